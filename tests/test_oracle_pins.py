@@ -1,0 +1,328 @@
+"""Pins of the oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the pin it is and the passage it follows.  The oracle is test
+infrastructure; these tests make sure a plausible mistake in it (a dropped term, a wrong
+sign or index, a transposed operand) fails somewhere.
+
+Parity status of the oracle's functions:
+  layer_response  pinned: paper's printed 3-layer densities (Sec. 2.1), homogeneous medium,
+                  two half-spaces closed form.
+  green_react     pinned: homogeneous medium (P6), two half-spaces images (P7), reciprocity (P8),
+                  finite differences of the field.
+  direct          pinned: equals the sum of green_react / closed forms; reciprocity of the
+                  assembled potential.
+  S_table         pinned: Sommerfeld identity closed forms for K=1,d=0 and K=2,d=1 in a
+                  homogeneous medium; Bessel three-term recurrence invariant; zero for rho=0,d>0.
+  image_z         pinned: the paper's printed example coordinates (Sec. 3.4).
+  tree/lists      pinned: brute force over integer box coordinates.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_01334_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper_sigma3(lr, d, eps, lam):
+    """The 3-layer reaction densities as printed in Sec. 2.1 (eqs. densitythreelayer1-3), with
+    d_0 = 0, exp(-d_1 lz_1) read literally (d_1 < 0), sigma_10^11's "lambda_1 lambda_1z" read as
+    eps_1 lambda_1z and sigma_11^21's "+eps_0 lambda_0z" read as "-eps_0 lambda_0z"."""
+    e0, e1, e2 = eps
+    l0, l1, l2 = np.sqrt(np.asarray(lam) ** 2 + lr * lr)
+    d1 = d[1]
+    ch, sh, ex = np.cosh(-d1 * l1), np.sinh(-d1 * l1), np.exp(-d1 * l1)
+    kap = e1 * l1 * (e0 * l0 + e2 * l2) * ch + (e1 ** 2 * l1 ** 2 + e0 * e2 * l0 * l2) * sh
+    S = {}
+    S[(0, 0, 1, 1)] = (e1 * l1 * (e0 * l0 - e2 * l2) * ch - (e1 ** 2 * l1 ** 2 - e0 * e2 * l0 * l2) * sh) / (e0 * kap)
+    S[(1, 0, 1, 1)] = e0 * l1 * (e1 * l1 - e2 * l2) / (e0 * kap)
+    S[(1, 0, 2, 1)] = e0 * l1 * (e1 * l1 + e2 * l2) * ex / (e0 * kap)
+    S[(2, 0, 2, 1)] = 2 * e0 * e1 * l1 * l2 / (e0 * kap)
+    S[(0, 1, 1, 1)] = e1 * l0 * (e1 * l1 - e2 * l2) / (e1 * kap)
+    S[(0, 1, 1, 2)] = e1 * l0 * (e1 * l1 + e2 * l2) * ex / (e1 * kap)
+    S[(1, 1, 1, 1)] = (e1 * l1 - e2 * l2) * (e1 * l1 + e0 * l0) * ex / (2 * e1 * kap)
+    S[(1, 1, 1, 2)] = (e1 * l1 - e2 * l2) * (e1 * l1 - e0 * l0) / (2 * e1 * kap)
+    S[(1, 1, 2, 1)] = (e1 * l1 - e2 * l2) * (e1 * l1 - e0 * l0) / (2 * e1 * kap)
+    S[(1, 1, 2, 2)] = (e1 * l1 + e2 * l2) * (e1 * l1 - e0 * l0) * ex / (2 * e1 * kap)
+    S[(2, 1, 2, 1)] = e1 * l2 * (e0 * l0 + e1 * l1) * ex / (e1 * kap)
+    S[(2, 1, 2, 2)] = e1 * l2 * (e1 * l1 - e0 * l0) / (e1 * kap)
+    S[(0, 2, 1, 2)] = 2 * e1 * l1 * e2 * l0 / (e2 * kap)
+    S[(1, 2, 2, 2)] = e2 * l1 * (e1 * l1 - e0 * l0) / (e2 * kap)
+    S[(1, 2, 1, 2)] = e2 * l1 * (e0 * l0 + e1 * l1) * ex / (e2 * kap)
+    S[(2, 2, 2, 2)] = (e1 * l1 * (e2 * l2 - e0 * l0) * ch - (e1 ** 2 * l1 ** 2 - e0 * e2 * l0 * l2) * sh) / (e2 * kap)
+    return S
+
+
+@pytest.mark.parametrize("medium", ["three_layer", "paper_three_layer"])
+@pytest.mark.parametrize("lr", [0.0, 0.37, 1.9, 7.5])
+def test_P1_three_layer_densities_match_paper(medium, lr):
+    m = inputs.MEDIA[medium]
+    md = oracle.Medium(**m)
+    for (l, lp, a, b), v in paper_sigma3(lr, m["d"], m["eps"], m["lam"]).items():
+        got = oracle.sigma(md, lr, l, lp, a, b)
+        assert abs(got - v) <= 1e-13 * max(1.0, abs(v)), (l, lp, a, b, got, v)
+
+
+def test_P1_printed_sigma11_21_sign_is_a_typo():
+    """Reciprocity fixes sigma_11^21 = sigma_11^12; the printed '+eps_0 lambda_0z' breaks it."""
+    m = inputs.MEDIA["three_layer"]
+    md = oracle.Medium(**m)
+    lr = 0.8
+    l0, l1, l2 = np.sqrt(np.asarray(m["lam"]) ** 2 + lr * lr)
+    e0, e1, e2 = m["eps"]
+    printed = paper_sigma3(lr, m["d"], m["eps"], m["lam"])[(1, 1, 2, 1)] / (e1 * l1 - e0 * l0) * (e1 * l1 + e0 * l0)
+    assert abs(oracle.sigma(md, lr, 1, 1, 2, 1) - printed) > 1e-3
+    assert abs(oracle.sigma(md, lr, 1, 1, 2, 1) - oracle.sigma(md, lr, 1, 1, 1, 2)) < 1e-15
+
+
+def free(r, rp, lam, eps):
+    R = np.linalg.norm(np.subtract(r, rp))
+    phi = np.exp(-lam * R) / (4 * np.pi * eps * R)
+    field = phi * (1 + lam * R) / R ** 2 * np.subtract(r, rp)
+    return phi, field
+
+
+def test_P6_homogeneous_medium():
+    """All layers share eps, lambda: same-layer reaction vanishes, cross-layer reaction is the
+    whole free-space kernel (Sec. 2.1 eq. layeredGreensfun)."""
+    md = oracle.Medium([0.0, -1.0], [3.0, 3.0, 3.0], [0.7, 0.7, 0.7])
+    r = np.array([0.1, 0.2, -0.4])
+    for rp, lp in [([0.3, -0.1, -0.7], 1), ([0.0, 0.1, 0.6], 0), ([-0.2, 0.4, -1.5], 2)]:
+        g, f = oracle.green_react(md, 1, r, lp, rp)
+        if lp == 1:
+            assert abs(g) < 1e-14 and np.abs(f).max() < 1e-13
+        else:
+            g0, f0 = free(r, rp, 0.7, 3.0)
+            assert abs(g - g0) < 1e-12 * abs(g0)
+            assert np.abs(f - f0).max() < 1e-11 * np.abs(f0).max()
+
+
+@pytest.mark.parametrize("lam", [0.7, 1e-8])
+def test_P7_two_half_spaces_image_charge(lam):
+    """Two half-spaces with equal lambda: reflected part R e^{-lam r*}/(4 pi eps0 r*) at the
+    mirror image, R = (eps0-eps1)/(eps0+eps1); transmitted 2 e^{-lam r}/(4 pi (eps0+eps1) r)."""
+    e0, e1 = 2.0, 7.0
+    md = oracle.Medium([0.0], [e0, e1], [lam, lam])
+    rp = np.array([0.1, -0.2, 0.35])
+    for r in ([0.4, 0.3, 0.6], [-0.3, 0.1, 0.15]):
+        mirror = rp * [1, 1, -1]
+        g, f = oracle.green_react(md, 0, r, 0, rp)
+        g0, f0 = free(r, mirror, lam, e0)
+        Rc = (e0 - e1) / (e0 + e1)
+        assert abs(g - Rc * g0) < 1e-11 * abs(g0)
+        assert np.abs(f - Rc * f0).max() < 1e-10 * np.abs(f0).max()
+    r = np.array([0.2, -0.5, -0.45])
+    g, f = oracle.green_react(md, 1, r, 0, rp)
+    g0, f0 = free(r, rp, lam, 1.0)
+    assert abs(g - 2 * g0 / (e0 + e1)) < 1e-11 * abs(g0)
+    assert np.abs(f - 2 * f0 / (e0 + e1)).max() < 1e-10 * np.abs(f0).max()
+
+
+def test_P7_unequal_lambda_limit_to_laplace():
+    """lambda_0 != lambda_1 -> 0 tends to the Laplace image formula."""
+    e0, e1 = 1.0, 4.0
+    rp = np.array([0.0, 0.0, 0.3])
+    r = np.array([0.2, 0.1, 0.5])
+    Rlap = (e0 - e1) / (e0 + e1) / (4 * np.pi * e0 * np.linalg.norm(r - rp * [1, 1, -1]))
+    errs = []
+    for s in (1e-2, 1e-3, 1e-4):
+        md = oracle.Medium([0.0], [e0, e1], [s, 2 * s])
+        g, _ = oracle.green_react(md, 0, r, 0, rp)
+        errs.append(abs(g - Rlap))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 1e-4 * abs(Rlap)
+
+
+@pytest.mark.parametrize("medium", ["three_layer", "four_layer"])
+def test_P8_reciprocity(medium):
+    m = inputs.MEDIA[medium]
+    md = oracle.Medium(**m)
+    rng = np.random.default_rng(5)
+    boxes = inputs.THREE_LAYER_BOXES if medium == "three_layer" else inputs.FOUR_LAYER_BOXES
+    for _ in range(6):
+        l, lp = rng.integers(0, md.L + 1, 2)
+        r = np.r_[rng.uniform(-0.5, 0.5, 2), rng.uniform(*boxes[l])]
+        rp = np.r_[rng.uniform(-0.5, 0.5, 2), rng.uniform(*boxes[lp])]
+        g1, _ = oracle.green_react(md, l, r, lp, rp)
+        g2, _ = oracle.green_react(md, lp, rp, l, r)
+        assert abs(g1 - g2) < 1e-12 * max(abs(g1), 1e-6), (l, lp, g1, g2)
+
+
+def test_field_is_minus_gradient():
+    md = oracle.Medium(**inputs.MEDIA["four_layer"])
+    r = np.array([0.1, -0.2, -1.3])
+    rp = np.array([-0.3, 0.25, -0.6])
+    g, f = oracle.green_react(md, 2, r, 1, rp)
+    h = 1e-5
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        gp, _ = oracle.green_react(md, 2, r + e, 1, rp)
+        gm, _ = oracle.green_react(md, 2, r - e, 1, rp)
+        assert abs(-(gp - gm) / (2 * h) - f[k]) < 1e-8 * np.abs(f).max()
+
+
+def test_direct_matches_pairwise_definition():
+    """The batched fixed-rule direct sum equals the per-pair adaptive definition."""
+    w = inputs.workload("three_layer", n=30, seed=11)
+    md = oracle.Medium(**w["medium"])
+    phi, field = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    for i in (0, 7, 29):
+        acc = 0.0
+        fac = np.zeros(3)
+        for j in range(30):
+            g, f = oracle.green_react(md, w["layer"][i], w["xyz"][i], w["layer"][j], w["xyz"][j])
+            acc += w["q"][j] * g
+            fac += w["q"][j] * f
+            if j != i and w["layer"][j] == w["layer"][i]:
+                lam, eps = md.lam[w["layer"][i]], md.eps[w["layer"][i]]
+                g0, f0 = free(w["xyz"][i], w["xyz"][j], lam, eps)
+                acc += w["q"][j] * g0
+                fac += w["q"][j] * f0
+        assert abs(phi[i] - acc) < 1e-11 * np.abs(phi).max()
+        assert np.abs(field[i] - fac).max() < 1e-10 * np.abs(field).max()
+
+
+def test_direct_reciprocity_of_assembled_potential():
+    """sum_i q'_i phi_i[q] = sum_i q_i phi_i[q'] (symmetric Green's function)."""
+    w = inputs.workload("four_layer", n=40, seed=3)
+    md = oracle.Medium(**w["medium"])
+    q2 = inputs.uniform(99, 40) - 0.5
+    p1, _ = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    p2, _ = oracle.direct(md, q2, w["xyz"], w["layer"])
+    a, b = np.dot(q2, p1), np.dot(w["q"], p2)
+    assert abs(a - b) < 1e-12 * max(abs(a), abs(b))
+
+
+def test_S_table_closed_forms_homogeneous():
+    """Homogeneous 2-half-space medium, cross-layer component (l=1 target, l'=0 source, a=2, b=1):
+    sigma = 1/eps, so S^1 S_{1 0,00} = e^{-lam R}/(eps R) (Sommerfeld identity, Sec. 3.2) and
+    S^2 S_{2 1,00} = h^2/sqrt(6) (rho/R)(1+lam R) e^{-lam R}/(eps R^2)."""
+    lam, eps = 0.6, 2.5
+    md = oracle.Medium([0.0], [eps, eps], [lam, lam])
+    h, rho, zt, zs = 0.7, 1.3, 0.4, 0.5
+    S = oracle.S_table(md, 1, 0, 2, 1, h, rho, zt, zs, 3)
+    R = np.hypot(rho, zt + zs)
+    v10 = h * np.exp(-lam * R) / (eps * R)
+    v21 = h * h / np.sqrt(6.0) * (rho / R) * (1 + lam * R) * np.exp(-lam * R) / (eps * R * R)
+    assert abs(S[1, 0, 0, 0] - v10) < 1e-12 * abs(v10)
+    assert abs(S[2, 1, 0, 0] - v21) < 1e-12 * abs(v21)
+
+
+def test_S_table_bessel_recurrence_and_rho_zero():
+    """The definition obeys the three-term recurrence of Sec. 3.5 (eq. recurrence1) exactly,
+    and vanishes for rho = 0, d > 0."""
+    md = oracle.Medium(**inputs.MEDIA["three_layer"])
+    h = 0.3
+    Kmax = 9
+    S = oracle.S_table(md, 1, 2, 1, 2, h, 2.2 * h, 1.5 * h, 0.5 * h, Kmax)
+    a = lambda n: np.sqrt(n * (n + 1.0))
+    rho = 2.2 * h
+    worst = 0.0
+    for d in range(1, Kmax - 1):
+        for K in range(d + 2, Kmax + 1):
+            rhs = 2 * d / a(K + d) * (h / rho) * S[K - 1, d] - a(K - d) / a(K + d) * S[K, d - 1]
+            scale = np.abs(S[K]).max()
+            worst = max(worst, np.abs(S[K, d + 1] - rhs).max() / scale)
+    assert worst < 1e-10
+    S0 = oracle.S_table(md, 1, 2, 1, 2, h, 0.0, 1.5 * h, 0.5 * h, 5)
+    assert np.abs(S0[:, 1:]).max() == 0.0 and np.abs(S0[3, 0]).max() > 0
+
+
+def test_image_coordinates_match_paper_example():
+    g = json.load(open(os.path.join(GOLD, "paper_me_example.json")))
+    md = oracle.Medium(g["d"], g["eps"], g["lam"])
+    zp = g["source"][2]
+    assert abs(oracle.image_z(md, 1, 1, 1, 1, zp) - g["image_11"][2]) < 1e-14
+    assert abs(oracle.image_z(md, 1, 2, 1, 2, zp) - g["image_22"][2]) < 1e-14
+    for key in ("11", "22"):
+        dist = np.linalg.norm(np.subtract(g["image_" + key], g["center_" + key]))
+        assert abs(dist - g["image_center_distance"]) < 5e-5
+
+
+def test_images_across_interface_from_targets():
+    """Images of group (l, a) lie beyond the interface from the targets (Sec. 3.3, Remark 1)."""
+    m = inputs.MEDIA["four_layer"]
+    md = oracle.Medium(**m)
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        l = int(rng.integers(0, 4))
+        lp = int(rng.integers(0, 4))
+        zp = rng.uniform(*inputs.FOUR_LAYER_BOXES[lp])
+        for a in (1, 2):
+            if (a == 1 and l == 3) or (a == 2 and l == 0):
+                continue
+            for b in (1, 2):
+                if (b == 1 and lp == 3) or (b == 2 and lp == 0):
+                    continue
+                zi = oracle.image_z(md, l, a, lp, b, zp)
+                if a == 1:
+                    assert zi < m["d"][l]
+                else:
+                    assert zi > m["d"][l - 1]
+
+
+def brute_lists(tcoords, scoords, lev, kind):
+    sset = {tuple(c): i for i, c in enumerate(scoords)}
+    out = []
+    for t in tcoords:
+        row = []
+        for dx in range(-3, 4):
+            for dy in range(-3, 4):
+                for dz in range(-3, 4):
+                    s = (t[0] + dx, t[1] + dy, t[2] + dz)
+                    if s not in sset:
+                        continue
+                    cheb = max(abs(dx), abs(dy), abs(dz))
+                    if kind == 1:
+                        ok = cheb <= 1
+                    else:
+                        ok = cheb >= 2 and all(abs((s[k] >> 1) - (t[k] >> 1)) <= 1 for k in range(3))
+                    if ok:
+                        row.append(sset[s])
+        out.append(row)
+    return out
+
+
+def coords_of(boxes):
+    out = []
+    for key in boxes:
+        key = int(key)
+        x = y = z = 0
+        for k in range(21):
+            z |= ((key >> (3 * k)) & 1) << k
+            y |= ((key >> (3 * k + 1)) & 1) << k
+            x |= ((key >> (3 * k + 2)) & 1) << k
+        out.append((x, y, z))
+    return out
+
+
+def test_tree_keys_and_lists_brute_force():
+    w = inputs.workload("three_layer", n=600, seed=7)
+    md = oracle.Medium(**w["medium"])
+    l, a, D = 1, 2, 4
+    root = oracle.tree_root(md, w["xyz"], w["layer"], l, a)
+    assert root[2] == md.d[0]
+    tk, tsrc, _ = oracle.tree_keys(md, w["xyz"], w["layer"], l, a, D, root, 0)
+    ik, isrc, ityp = oracle.tree_keys(md, w["xyz"], w["layer"], l, a, D, root, 1)
+    assert len(tk) == 200 and len(ik) == 200 + 2 * 200 + 200
+    # keys from an independent float computation of the cells
+    H = root[3]
+    for k, j in zip(tk[:50], tsrc[:50]):
+        c = [int(np.floor((w["xyz"][j][t] - (root[t] - H)) * ((1 << D) / (2 * H)))) for t in range(3)]
+        assert int(k) == int(oracle.morton(*c))
+    # targets below, images above the bisecting interface: z-cells on either side of 2^(D-1)
+    tz = [c[2] for c in coords_of(tk)]
+    iz = [c[2] for c in coords_of(ik)]
+    assert max(tz) < (1 << (D - 1)) <= min(iz)
+    for lev in (2, 3, 4):
+        tb = oracle.level_boxes(tk, D, lev)
+        sb = oracle.level_boxes(ik, D, lev)
+        for kind in (0, 1):
+            off, idx = oracle.lists(tb, sb, lev, kind)
+            ref = brute_lists(coords_of(tb), coords_of(sb), lev, kind)
+            got = [list(idx[off[t]:off[t + 1]]) for t in range(len(tb))]
+            assert got == ref
