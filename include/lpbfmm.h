@@ -1,0 +1,192 @@
+/*
+ * lpbfmm -- fast multipole evaluation of screened-Coulomb (linearized Poisson-Boltzmann)
+ * potentials and fields of point charges in a layered medium, on one NVIDIA GB300 GPU.
+ *
+ * Method: Wang, Zhang & Cai, "Fast Multipole Method for 3-D Linearized Poisson-Boltzmann
+ * Equation in Layered Media" (arXiv 2002.01334).  The potential at a charge in layer l is
+ * the free-space Yukawa sum over the other charges of that layer plus the reaction
+ * components carried by equivalent polarization sources (Sec. 2.2, eq. totalinteraction;
+ * Sec. 3.3).  Each component is evaluated by an FMM whose multipole-to-local operators are
+ * Sommerfeld-type integrals tabulated at run time (Sec. 3.4-3.5, Algorithms 1 and 2).
+ *
+ * Conventions (Sec. 2.1): L interfaces z = d_0 > d_1 > ... > d_{L-1}; layer 0 is z > d_0,
+ * layer k is d_k < z < d_{k-1}, layer L is z < d_{L-1}.  Layer k has dielectric constant
+ * eps_k > 0 and inverse Debye length lambda_k > 0.  The Green's function solves
+ * eps_l (Laplacian - lambda_l^2) u = -delta with continuity of u and eps du/dz across the
+ * interfaces, so the free-space part is exp(-lambda r) / (4 pi eps r).
+ *
+ * Every entry point returns an lpbfmm status code (0 = success).  Device pointers refer to
+ * memory on the context's device; the caller owns all input and output arrays and the
+ * library never frees them.  Work is issued on the context's stream; lpbfmm_eval returns
+ * after the results are complete on that stream (it synchronizes the stream internally
+ * several times to size its work).
+ */
+#ifndef LPBFMM_H
+#define LPBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define LPBFMM_OK 0
+#define LPBFMM_ERR_ARG 1            /* null pointer where one is required, n < 0, bad option  */
+#define LPBFMM_ERR_MEDIUM 2         /* interfaces not strictly descending, eps <= 0, lambda <= 0,
+                                       or more than LPBFMM_MAX_INTERFACES interfaces          */
+#define LPBFMM_ERR_P 3              /* truncation order outside [LPBFMM_P_MIN, LPBFMM_P_MAX]   */
+#define LPBFMM_ERR_ON_INTERFACE 4   /* a charge lies within 1e-12 (relative to the layer
+                                       thickness scale) of an interface, where the Sommerfeld
+                                       integrals do not converge (Sec. 3.5)                   */
+#define LPBFMM_ERR_LAYER_MISMATCH 5 /* layer_id[i] differs from the layer containing z_i     */
+#define LPBFMM_ERR_NONFINITE 6      /* NaN or Inf in q or xyz                                 */
+#define LPBFMM_ERR_OOM 7            /* device allocation failed                               */
+#define LPBFMM_ERR_CUDA 8           /* a CUDA call failed                                     */
+#define LPBFMM_ERR_TIMEOUT 9        /* a bounded device wait expired                          */
+#define LPBFMM_ERR_UNSUPPORTED 10   /* e.g. tree too deep for the input size                 */
+
+#define LPBFMM_MAX_INTERFACES 8
+#define LPBFMM_P_MIN 2
+#define LPBFMM_P_MAX 16
+
+/* precision modes */
+#define LPBFMM_FP64 0  /* every step in FP64                                                  */
+#define LPBFMM_MIXED 1 /* FP32 P2P, P2M/M2M/M2L/L2L/L2P; FP64 tables, operators and final sums */
+
+typedef struct lpbfmm_ctx *lpbfmm_t;
+
+typedef struct {
+  int precision;     /* LPBFMM_FP64 or LPBFMM_MIXED                                        */
+  int max_per_leaf;  /* automatic depth: smallest depth >= 2 whose mean target occupancy of
+                        the non-empty leaves is <= max_per_leaf (default 128)               */
+  int uniform_depth; /* > 0: use this tree depth for every target group; 0: automatic      */
+  int reserved;      /* must be 0                                                            */
+  void *stream;      /* cudaStream_t for all work; NULL = the legacy default stream          */
+} lpbfmm_opts;
+
+/* Fill *opts with the defaults (FP64, max_per_leaf 128, automatic depth, default stream). */
+void lpbfmm_default_opts(lpbfmm_opts *opts);
+
+/*
+ * Create a context for one medium and truncation order (Sec. 2.1 medium; Sec. 3.1 and 3.4
+ * expansions truncated at degree p).  Host arrays: z_iface[n_iface] (strictly descending),
+ * eps[n_iface+1] > 0, lambda[n_iface+1] > 0.  tol is the truncation tolerance of the
+ * Sommerfeld integrals (Sec. 3.5, end: "decayed to a user specified tolerance"), in (0, 1e-3].
+ * The context allocates device tables for Gaunt coefficients and Legendre-product expansion
+ * coefficients on the current device.  opts may be NULL (defaults).  On success *out holds a
+ * new context that must be released with lpbfmm_destroy.
+ */
+int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const double *lambda, int p,
+                  double tol, const lpbfmm_opts *opts, lpbfmm_t *out);
+
+/*
+ * Potential and field of n charges (Sec. 2.2 eq. potential1, Algorithm 2):
+ *   phi_i = sum_{j != i, layer_j = layer_i} q_j exp(-lambda r_ij)/(4 pi eps r_ij)
+ *         + sum_j q_j u^react_{layer_i layer_j}(r_i, r_j)      (reaction part includes j = i)
+ *   field_i = -grad_{r_i} phi_i.
+ * Device arrays: q[n] (FP64), xyz[n*3] (FP64, x y z per charge), layer_id[n] (int32, the layer
+ * of each charge, 0 = top); outputs phi[n] (FP64) and field[n*3] (FP64, may be NULL).
+ * Inputs are validated on the device (finite, off the interfaces, layer_id consistent with z);
+ * on a data error phi/field are unspecified and the code is returned.  n = 0 is a no-op.
+ */
+int lpbfmm_eval(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
+                double *phi, double *field);
+
+/*
+ * Same as lpbfmm_eval for a subset of the components, used to check the parts separately
+ * (Sec. 2.2, eq. freereactioncomponents): bit 0 (1) the free-space part, bit 1 (2) the reaction
+ * part; diagnostics: bit 2 (4) leaves out the reaction near field (direct interactions of
+ * adjacent target / image leaves, Algorithm 1 last loop), bit 3 (8) leaves out the reaction
+ * far field (multipole-to-local translations).  parts must be in [1, 15].
+ */
+int lpbfmm_eval_parts(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
+                      int parts, double *phi, double *field);
+
+/*
+ * Adjoint of phi with respect to q and positions for an upstream gradient g_phi[n] (device):
+ *   g_q[j]   = sum_i g_phi[i] G(r_i, r_j)                  = phi[g_phi](r_j)
+ *   g_xyz[j] = sum_i g_phi[i] d phi_i / d r_j = -(q_j field[g_phi](r_j) + g_phi[j] field[q](r_j))
+ * using the reciprocity G_{l l'}(r, r') = G_{l' l}(r', r) of the layered Green's function.
+ * With g_phi = q / 2 this gives dE/dq and -(force) for E = 1/2 sum q_i phi_i.  Device arrays;
+ * g_q[n], g_xyz[n*3] are outputs.
+ */
+int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
+                   const double *g_phi, double *g_q, double *g_xyz);
+
+/*
+ * Batched evaluation of nsys independent systems, each with its own context (medium and
+ * order): system s uses rows offsets[s] .. offsets[s+1]-1 of the concatenated device arrays.
+ * offsets is a host array of nsys+1 non-decreasing entries with offsets[0] = 0.
+ */
+int lpbfmm_eval_batched(int nsys, const lpbfmm_t *ctxs, const int64_t *offsets, const double *q,
+                        const double *xyz, const int32_t *layer_id, double *phi, double *field);
+
+/*
+ * Diagnostics for the tests: after an lpbfmm_eval on h, copy out the tree of target group
+ * (layer l, side a) at its depth D (Sec. 3.5: root cube bisected by interface d_l for a = 1,
+ * d_{l-1} for a = 2).  root[4] = cx, cy, cz, half-size (host).  If keys is NULL only the
+ * counts are returned: *n_targets, *n_images, *depth.  Otherwise keys_t[n_targets] and
+ * keys_i[n_images] (host uint64) receive the depth-D Morton keys in sorted order, src_t and
+ * src_i (host int64) the input index of each point, type_i (host int32) the image type
+ * 2*l' + b - 1.  Returns LPBFMM_ERR_ARG if the group does not exist.
+ */
+int lpbfmm_debug_tree(lpbfmm_t h, int l, int a, double *root, int64_t *n_targets, int64_t *n_images,
+                      int *depth, uint64_t *keys_t, int64_t *src_t, uint64_t *keys_i, int64_t *src_i,
+                      int32_t *type_i);
+
+/*
+ * Diagnostics: after an lpbfmm_eval, the interaction lists of group (l, a) at level lev:
+ * kind 0 = far (multipole-to-local) list, kind 1 = near list at the leaf level; src 0 = the
+ * group's free-space sources (its own targets), src 1 = its images.  Host outputs in CSR form
+ * over the level's target boxes (sorted by key): off[nbox+1], idx[off[nbox]] source box
+ * indices, each row in the order dx, dy, dz from -3 to 3 (dx outermost).  With off == NULL
+ * only *nbox and *nent are returned.
+ */
+int lpbfmm_debug_lists(lpbfmm_t h, int l, int a, int lev, int kind, int src, int64_t *nbox, int64_t *nent,
+                       int64_t *off, int64_t *idx);
+
+/*
+ * Diagnostics: scaled Sommerfeld integrals of Sec. 3.5 (eq. M2Ltable scaled by S^K, S = h)
+ *   out[((K*(Kmax+1)) + d)*4 + 2i + j] = h^K / sqrt((K+d)!(K-d)!)
+ *        * int_0^inf lr^K J_d(lr rho) exp(-lz_l zt - lz_l' zs) sigma^{ab}_{l l'} / lz_l
+ *          (lambda_l/lz_l)^i (lambda_l'/lz_l')^j d lr,         K = 0..Kmax, d = 0..K,
+ * computed on the device the way the FMM computes them: quadrature for d = 0, 1 and the
+ * forward recurrence in d (eq. recurrence1) for d >= 2.  zt, zs > 0 are the distances of the
+ * target and source centres to the component's interface, rho = ratio * h with ratio^2 in
+ * {0,1,2,4,5,8,9,10,13,18}.  out is a host array.
+ */
+int lpbfmm_debug_stable(lpbfmm_t h, int l, int a, int lp, int b, double hbox, double rho, double zt,
+                        double zs, int Kmax, double *out);
+
+/*
+ * Diagnostics: after an lpbfmm_eval, copy an intermediate device array of group (l, a) at
+ * level lev into the host buffer dst (capacity cap bytes); *bytes receives its size.  Names:
+ * "Mimg", "Mfree", "Lt" (expansions, complex, working precision), "op_react", "op_free"
+ * (translation operators), "stab" (FP64 Sommerfeld tables), "used" (uint8 reaction classes in
+ * use), "vreact" (int32 far list), "ikeys", "tkeys" (uint64 box keys), "rows", "nrows".
+ * With dst == NULL only *bytes is set.
+ */
+int lpbfmm_debug_array(lpbfmm_t h, int l, int a, const char *name, int lev, void *dst, int64_t cap,
+                       int64_t *bytes);
+
+/* Read and clear the device status word (synchronizes the context's stream). */
+int lpbfmm_status(lpbfmm_t h);
+
+/* Short description of a status code (static storage). */
+const char *lpbfmm_strerror(int code);
+
+/* Release the context's device memory. */
+void lpbfmm_destroy(lpbfmm_t h);
+
+/*
+ * Per-phase device times (ms) of the last lpbfmm_eval, measured with CUDA events on the
+ * context's stream, and the number of kernels it launched.  names[i] is a static string.
+ * Returns the number of phases written (at most cap).
+ */
+int lpbfmm_last_profile(lpbfmm_t h, int cap, const char **names, float *ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

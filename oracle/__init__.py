@@ -43,6 +43,7 @@ def lib():
         up = C.POINTER(C.c_uint64)
         L.orc_layer_response.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, dp, dp]
         L.orc_green_react.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp, C.c_double, dp, dp]
+        L.orc_green_react_ab.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp, C.c_int, C.c_int, C.c_double, dp, dp]
         L.orc_direct.argtypes = [C.c_void_p, C.c_int64, dp, dp, ip, C.c_int64, lp, C.c_int, C.c_int, dp, dp]
         L.orc_S_table.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                   C.c_double, C.c_double, C.c_int, C.c_double, dp]
@@ -123,6 +124,18 @@ def green_react(md, l, r, lp, rp, tol=1e-14):
     rc = lib().orc_green_react(md.ptr, int(l), _p(r), int(lp), _p(rp), float(tol), _p(phi), _p(f))
     if rc:
         raise ValueError("green_react rc=%d" % rc)
+    return phi[0], f
+
+
+def green_react_ab(md, l, r, lp, rp, a, b, tol=1e-14):
+    """One reaction component u^{ab}_{l lp}(r, rp) and its -grad_r (Sec. 2.2)."""
+    r = np.ascontiguousarray(r, float)
+    rp = np.ascontiguousarray(rp, float)
+    phi = np.zeros(1)
+    f = np.zeros(3)
+    rc = lib().orc_green_react_ab(md.ptr, int(l), _p(r), int(lp), _p(rp), int(a), int(b), float(tol), _p(phi), _p(f))
+    if rc:
+        raise ValueError("green_react_ab rc=%d" % rc)
     return phi[0], f
 
 

@@ -235,6 +235,7 @@ typedef struct {
   int l, lp, tmask, smask;
   double ht[3], hs[3], rho;
 } gr_ctx;
+static int gr_amask = 6, gr_bmask = 6; /* bits 1<<a, 1<<b of the components kept */
 
 static void gr_integrand(double lr, void *vctx, int nv, double *out) {
   (void)nv;
@@ -272,14 +273,15 @@ int orc_green_react(const orc_medium *md, int l, const double *r, int lp, const 
                     double *phi, double *field) {
   gr_ctx c;
   c.md = md; c.l = l; c.lp = lp;
-  c.tmask = target_h(md, l, r[2], c.ht);
-  c.smask = source_h(md, lp, rp[2], c.hs);
+  c.tmask = target_h(md, l, r[2], c.ht) & gr_amask;
+  c.smask = source_h(md, lp, rp[2], c.hs) & gr_bmask;
   const double dx = r[0] - rp[0], dy = r[1] - rp[1];
   c.rho = sqrt(dx * dx + dy * dy);
   double dmin = 1e300;
   for (int a = 1; a <= 2; ++a)
     for (int b = 1; b <= 2; ++b)
       if ((c.tmask & (1 << a)) && (c.smask & (1 << b))) dmin = fmin(dmin, c.ht[a] + c.hs[b]);
+  if (dmin > 1e299) { *phi = 0.0; field[0] = field[1] = field[2] = 0.0; return 0; }
   if (!(dmin > 0.0)) return -1;
   const double xmax = 60.0 / dmin;
   double w = 2.0 / dmin;
@@ -291,6 +293,17 @@ int orc_green_react(const orc_medium *md, int l, const double *r, int lp, const 
   field[1] = dy * out[1];
   field[2] = out[2];
   return 0;
+}
+
+/* One reaction component u^{ab}_{l l'} (Sec. 2.2 eq. generalcomponents): a, b select the
+ * target-side and source-side waves. */
+int orc_green_react_ab(const orc_medium *md, int l, const double *r, int lp, const double *rp, int a, int b,
+                       double tol, double *phi, double *field) {
+  gr_amask = 1 << a;
+  gr_bmask = 1 << b;
+  const int rc = orc_green_react(md, l, r, lp, rp, tol, phi, field);
+  gr_amask = gr_bmask = 6;
+  return rc;
 }
 
 /* ------------------------------------------------------------------------------------ */

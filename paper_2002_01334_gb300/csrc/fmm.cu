@@ -1,0 +1,926 @@
+// FMM passes of one target group (Algorithm 1 for the reaction components of group (l, a),
+// the free-space Yukawa FMM of layer l when the group carries it, Algorithm 2 around them):
+// P2M, M2M, M2L (free + reaction), L2L, L2P with field, near-field P2P.
+// Expansions use the half representation (m >= 0) and the scaling described in ops.cu:
+//   M~_nm = sum_j q_j 4 pi itilde_n(lambda r_j) conj(R_n^m(r_j / h)),
+//   phi(r) = sum_n [L~_n0 itilde_n R_n^0 + 2 Re sum_{m>0} L~_nm itilde_n R_n^m](r / h).
+#include "internal.h"
+
+namespace lpb {
+
+// recurrence and gradient constants (index [n][m], n <= PMAX + 1)
+struct Consts {
+  double A[PMAX + 2][PMAX + 2], B[PMAX + 2][PMAX + 2];
+  double sect[PMAX + 2], sub[PMAX + 2];
+  double gz[PMAX + 2][PMAX + 2], ga[PMAX + 2][PMAX + 2], gb[PMAX + 2][PMAX + 2];
+  int mof[KHALF_MAX];
+};
+__constant__ Consts cK;
+
+void upload_consts(cudaStream_t s) {
+  static Consts h;
+  for (int n = 0; n <= PMAX + 1; ++n)
+    for (int m = 0; m <= PMAX + 1; ++m) {
+      h.A[n][m] = h.B[n][m] = h.gz[n][m] = h.ga[n][m] = h.gb[n][m] = 0.0;
+      if (m <= n && n >= m + 2) {
+        h.A[n][m] = sqrt((4.0 * n * n - 1.0) / (double(n) * n - double(m) * m));
+        h.B[n][m] = sqrt(((n - 1.0) * (n - 1.0) - double(m) * m) * (2.0 * n + 1.0) /
+                         ((2.0 * n - 3.0) * (double(n) * n - double(m) * m)));
+      }
+      if (m <= n) {
+        const double c1 = sqrt((2.0 * (n + 1) + 1.0) / (2.0 * (n + 1) - 1.0));
+        h.gz[n][m] = c1 * sqrt(double(n + 1 + m) * (n + 1 - m));
+        h.ga[n][m] = c1 * sqrt(double(n + 2 - m) * (n + 1 - m));
+        h.gb[n][m] = c1 * sqrt(double(n + 2 + m) * (n + 1 + m));
+      }
+    }
+  for (int m = 0; m <= PMAX + 1; ++m) {
+    h.sect[m] = m ? -sqrt((2.0 * m + 1.0) / (2.0 * m)) : 1.0;
+    h.sub[m] = sqrt(2.0 * m + 3.0);
+  }
+  for (int n = 0; n <= PMAX; ++n)
+    for (int m = 0; m <= n; ++m) h.mof[hidx(n, m)] = m;
+  LPB_CUDA(cudaMemcpyToSymbolAsync(cK, &h, sizeof(Consts), 0, cudaMemcpyHostToDevice, s));
+  LPB_CUDA(cudaStreamSynchronize(s));
+}
+
+template <typename T> struct C2;
+template <> struct C2<float> { typedef float2 t; };
+template <> struct C2<double> { typedef double2 t; };
+
+struct Geo {
+  double o[3];  // lower corner of the root cube
+  double h;     // box size at the level
+};
+
+__device__ __forceinline__ uint32_t compact3_(uint64_t x) {
+  x &= 0x9249249ull;
+  x = (x ^ (x >> 2)) & 0x30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x300f00full;
+  x = (x ^ (x >> 8)) & 0x30000ffull;
+  x = (x ^ (x >> 16)) & 0x3ffull;
+  return (uint32_t)x;
+}
+__device__ __forceinline__ void box_center(uint64_t key, const Geo &g, double &cx, double &cy, double &cz) {
+  cx = g.o[0] + (compact3_(key >> 2) + 0.5) * g.h;
+  cy = g.o[1] + (compact3_(key >> 1) + 0.5) * g.h;
+  cz = g.o[2] + (compact3_(key) + 0.5) * g.h;
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct LamTab {
+  double v[2 * MAXLAYER];
+};
+
+// ---------------------------------------------------------------------------------------
+// P2M: one warp per leaf (box, type) segment
+// ---------------------------------------------------------------------------------------
+template <typename T, int PT>
+__global__ void k_p2m(const uint32_t *d_nseg, const uint32_t *seg_start, const uint32_t *seg_count,
+                      const uint32_t *seg_box, const uint32_t *seg_type, int ntypes, const uint64_t *box_key,
+                      const double *x, const double *y, const double *z, const double *q, Geo geo, LamTab lt,
+                      int p, int K, typename C2<T>::t *M) {
+  typedef typename C2<T>::t T2;
+  __shared__ T2 acc[4][KHALF_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t seg = (int64_t)blockIdx.x * 4 + warp;
+  if (seg >= *d_nseg) return;
+  for (int e = lane; e < K; e += 32) acc[warp][e] = T2{0, 0};
+  const uint32_t st = seg_start[seg], cnt = seg_count[seg];
+  const uint32_t box = seg_box ? seg_box[seg] : (uint32_t)seg;
+  const uint32_t type = seg_type ? seg_type[seg] : 0u;
+  double cx, cy, cz;
+  box_center(box_key[box], geo, cx, cy, cz);
+  const double ih = 1.0 / geo.h;
+  const T lh = (T)(lt.v[type] * geo.h);
+  __syncwarp();
+  for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
+    const uint32_t j = b0 + lane;
+    const bool valid = j < cnt;
+    const uint32_t k = st + (valid ? j : 0);
+    const T rx = (T)((x[k] - cx) * ih), ry = (T)((y[k] - cy) * ih), rz = (T)((z[k] - cz) * ih);
+    const T qq = valid ? (T)(q[k] * 4.0 * PI) : T(0);
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    T it[PT + 2];
+    itilde_all<T, PT + 1>(lh * lh * r2, it);
+    T2 Rmm = T2{(T)(0.5 / sqrt(PI)), T(0)};
+#pragma unroll
+    for (int m = 0; m <= PT; ++m) {
+      if (m > p) break;
+      if (m > 0) {
+        const T s = (T)cK.sect[m];
+        const T2 t = T2{Rmm.x * rx - Rmm.y * ry, Rmm.x * ry + Rmm.y * rx};
+        Rmm = T2{s * t.x, s * t.y};
+      }
+      T2 p1 = T2{0, 0}, p2 = T2{0, 0};
+#pragma unroll
+      for (int n = m; n <= PT; ++n) {
+        if (n > p) break;
+        T2 R;
+        if (n == m) R = Rmm;
+        else if (n == m + 1) { const T s = (T)cK.sub[m] * rz; R = T2{s * p1.x, s * p1.y}; }
+        else {
+          const T a = (T)cK.A[n][m] * rz, b = (T)cK.B[n][m] * r2;
+          R = T2{a * p1.x - b * p2.x, a * p1.y - b * p2.y};
+        }
+        p2 = p1;
+        p1 = R;
+        const T c = qq * it[n];
+        const T vr = wsum(c * R.x), vi = wsum(-c * R.y);
+        if (lane == 0) {
+          T2 &A = acc[warp][hidx(n, m)];
+          A.x += vr;
+          A.y += vi;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  T2 *out = M + ((size_t)box * ntypes + type) * K;
+  for (int e = lane; e < K; e += 32) out[e] = acc[warp][e];
+}
+
+// ---------------------------------------------------------------------------------------
+// M2M (children -> parent) and L2L (parent -> child): azimuth-factored dense operators
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void rot_of_octant(uint64_t ckey, int m, const T *rot4, T &c, T &s) {
+  const int oct = (int)(ckey & 7ull);
+  const int dir = ((oct >> 2) & 1) * 2 + ((oct >> 1) & 1);
+  c = rot4[(dir * (PMAX + 1) + m) * 2];
+  s = rot4[(dir * (PMAX + 1) + m) * 2 + 1];
+}
+
+template <typename T>
+__global__ void k_m2m(const uint32_t *d_np, const uint32_t *pstart, const uint32_t *pcount, const uint64_t *ckey,
+                      int ntypes, const typename C2<T>::t *Mc, typename C2<T>::t *Mp, const T *ops, const T *rot4,
+                      int K) {
+  typedef typename C2<T>::t T2;
+  __shared__ T xr[KHALF_MAX], xi[KHALF_MAX];
+  const uint32_t box = blockIdx.x, type = blockIdx.y;
+  if (box >= *d_np) return;
+  const size_t KK = (size_t)K * K;
+  T ar[2] = {0, 0}, ai[2] = {0, 0};
+  const uint32_t c0 = pstart[box], nc = pcount[box];
+  for (uint32_t c = c0; c < c0 + nc; ++c) {
+    const uint64_t ck = ckey[c];
+    const int cz = (int)(ck & 1ull);
+    const T *P = ops + ((size_t)type * 2 + cz) * 2 * KK, *Q = P + KK;
+    for (int e = threadIdx.x; e < K; e += blockDim.x) {
+      T cs, sn;
+      rot_of_octant(ck, cK.mof[e], rot4, cs, sn);
+      const T2 v = Mc[((size_t)c * ntypes + type) * K + e];
+      xr[e] = cs * v.x - sn * v.y;
+      xi[e] = sn * v.x + cs * v.y;
+    }
+    __syncthreads();
+    for (int r = 0; r < 2; ++r) {
+      const int i = threadIdx.x + r * blockDim.x;
+      if (i >= K) break;
+      T yr = 0, yi = 0;
+      for (int k = 0; k < K; ++k) {
+        yr += P[(size_t)i * K + k] * xr[k];
+        yi += Q[(size_t)i * K + k] * xi[k];
+      }
+      T cs, sn;
+      rot_of_octant(ck, cK.mof[i], rot4, cs, sn);
+      ar[r] += cs * yr + sn * yi;
+      ai[r] += cs * yi - sn * yr;
+    }
+    __syncthreads();
+  }
+  for (int r = 0; r < 2; ++r) {
+    const int i = threadIdx.x + r * blockDim.x;
+    if (i < K) Mp[((size_t)box * ntypes + type) * K + i] = T2{ar[r], ai[r]};
+  }
+}
+
+template <typename T>
+__global__ void k_l2l(const uint32_t *d_nc, const uint32_t *cparent, const uint64_t *ckey,
+                      const typename C2<T>::t *Lp, typename C2<T>::t *Lc, const T *ops, const T *rot4, int K) {
+  typedef typename C2<T>::t T2;
+  __shared__ T xr[KHALF_MAX], xi[KHALF_MAX];
+  const uint32_t c = blockIdx.x;
+  if (c >= *d_nc) return;
+  const uint64_t ck = ckey[c];
+  const int cz = (int)(ck & 1ull);
+  const size_t KK = (size_t)K * K;
+  const T *P = ops + (size_t)cz * 2 * KK, *Q = P + KK;
+  const uint32_t par = cparent[c];
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    T cs, sn;
+    rot_of_octant(ck, cK.mof[e], rot4, cs, sn);
+    const T2 v = Lp[(size_t)par * K + e];
+    xr[e] = cs * v.x - sn * v.y;
+    xi[e] = sn * v.x + cs * v.y;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    T yr = 0, yi = 0;
+    for (int k = 0; k < K; ++k) {
+      yr += P[(size_t)i * K + k] * xr[k];
+      yi += Q[(size_t)i * K + k] * xi[k];
+    }
+    T cs, sn;
+    rot_of_octant(ck, cK.mof[i], rot4, cs, sn);
+    T2 &dst = Lc[(size_t)c * K + i];
+    dst.x += cs * yr + sn * yi;
+    dst.y += cs * yi - sn * yr;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// M2L: one launch for every (group, level, free / reaction row) job.  A work item is
+// (job, tile of target boxes, slice dx of the 343 offsets).  For every offset of its slice
+// the class operator (P, Q) and the phase-rotated multipoles of the tile's sources are staged
+// in shared memory in K-chunks and multiplied as a small GEMM (rows = output coefficients,
+// columns = target boxes); the tile's partial local expansions are added atomically.
+// ---------------------------------------------------------------------------------------
+constexpr int M2L_KC = 32;
+constexpr int M2L_NSLICE = 7;  // offsets with dx = -3..3, 49 each
+
+struct XJob {
+  const int32_t *tlist;   // target box indices (nullptr: 0..ntb-1)
+  const uint32_t *d_ntl;  // number of entries of tlist (device)
+  int64_t ntb;
+  const int32_t *vlist;   // [ntb][NOFF] source box or -1
+  const int32_t *cls_of;  // [NOFF] operator class or -1
+  const void *M;          // [nsb][ntypes][K]
+  const void *ops;        // [ncls][ntypes][2][K][K]
+  void *L;                // [ntb][K]
+  int ntypes, pad;
+  int64_t item0;          // first work item of this job
+};
+
+template <typename T>
+__device__ __forceinline__ void atomic_add2(typename C2<T>::t *p, T x, T y) {
+  atomicAdd(&p->x, x);
+  atomicAdd(&p->y, y);
+}
+
+template <typename T, int TPT, int NR>
+__global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const T *rot, int K) {
+  typedef typename C2<T>::t T2;
+  constexpr int TT = 16 * TPT, KR = 16 * NR;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *Pm = (T *)smraw;                 // [KR][KC]
+  T *Qm = Pm + KR * M2L_KC;           // [KR][KC]
+  T *Xr = Qm + KR * M2L_KC;           // [KC][TT]
+  T *Xi = Xr + M2L_KC * TT;           // [KC][TT]
+  int *sidx = (int *)(Xi + M2L_KC * TT);  // [TT]
+  int *tid_ = sidx + TT;                  // [TT]
+  // find the job of this item (jobs sorted by item0)
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].item0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const XJob J = jobs[lo];
+  const int64_t local = (int64_t)blockIdx.x - J.item0;
+  const int slice = (int)(local % M2L_NSLICE);
+  const int64_t tile0 = (local / M2L_NSLICE) * TT;
+  const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
+  if (tile0 >= ntl) return;
+  const T2 *M = (const T2 *)J.M;
+  const T *ops = (const T *)J.ops;
+  T2 *L = (T2 *)J.L;
+  const int ntypes = J.ntypes;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x < TT) {
+    const int64_t j = tile0 + threadIdx.x;
+    tid_[threadIdx.x] = (j < ntl) ? (J.tlist ? J.tlist[j] : (int)j) : -1;
+  }
+  T Lr[NR][TPT], Li[NR][TPT];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) Lr[r][j] = Li[r][j] = 0;
+  const size_t KK = (size_t)K * K;
+  bool any = false;
+  __syncthreads();
+  for (int o = slice * 49; o < slice * 49 + 49; ++o) {
+    const int cls = J.cls_of[o];
+    if (cls < 0) continue;
+    int has = 0;
+    if (threadIdx.x < TT) {
+      const int t = tid_[threadIdx.x];
+      const int s = (t >= 0) ? J.vlist[(size_t)t * NOFF + o] : -1;
+      sidx[threadIdx.x] = s;
+      has = s >= 0;
+    }
+    if (!__syncthreads_or(has)) continue;
+    any = true;
+    T Yr[NR][TPT], Yi[NR][TPT];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < TPT; ++j) Yr[r][j] = Yi[r][j] = 0;
+    const T *rc = rot + (size_t)o * (PMAX + 1) * 2;
+    for (int tau = 0; tau < ntypes; ++tau) {
+      const T *P = ops + ((size_t)cls * ntypes + tau) * 2 * KK, *Q = P + KK;
+      for (int kc = 0; kc < K; kc += M2L_KC) {
+        for (int e = threadIdx.x; e < KR * M2L_KC; e += blockDim.x) {
+          const int r = e / M2L_KC, k = e % M2L_KC;
+          const bool ok = r < K && kc + k < K;
+          Pm[e] = ok ? P[(size_t)r * K + kc + k] : T(0);
+          Qm[e] = ok ? Q[(size_t)r * K + kc + k] : T(0);
+        }
+        for (int e = threadIdx.x; e < M2L_KC * TT; e += blockDim.x) {
+          const int k = e / TT, j = e % TT;
+          const int s = sidx[j];
+          T vr = 0, vi = 0;
+          if (s >= 0 && kc + k < K) {
+            const int m = cK.mof[kc + k];
+            const T c = rc[2 * m], sn = rc[2 * m + 1];
+            const T2 v = M[((size_t)s * ntypes + tau) * K + kc + k];
+            vr = c * v.x - sn * v.y;
+            vi = sn * v.x + c * v.y;
+          }
+          Xr[e] = vr;
+          Xi[e] = vi;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < M2L_KC; ++k) {
+          T xr[TPT], xi[TPT];
+#pragma unroll
+          for (int j = 0; j < TPT; ++j) {
+            xr[j] = Xr[k * TT + tx + 16 * j];
+            xi[j] = Xi[k * TT + tx + 16 * j];
+          }
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const T pv = Pm[(ty + 16 * r) * M2L_KC + k], qv = Qm[(ty + 16 * r) * M2L_KC + k];
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+              Yr[r][j] += pv * xr[j];
+              Yi[r][j] += qv * xi[j];
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int row = ty + 16 * r;
+      if (row >= K) break;
+      const int m = cK.mof[row];
+      const T c = rc[2 * m], sn = rc[2 * m + 1];
+#pragma unroll
+      for (int j = 0; j < TPT; ++j) {
+        Lr[r][j] += c * Yr[r][j] + sn * Yi[r][j];
+        Li[r][j] += c * Yi[r][j] - sn * Yr[r][j];
+      }
+    }
+  }
+  if (!any) return;
+#pragma unroll
+  for (int j = 0; j < TPT; ++j) {
+    const int t = tid_[tx + 16 * j];
+    if (t < 0) continue;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int row = ty + 16 * r;
+      if (row >= K) break;
+      atomic_add2<T>(&L[(size_t)t * K + row], Lr[r][j], Li[r][j]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// L2P with field: one warp per leaf box
+// ---------------------------------------------------------------------------------------
+template <typename T, int PT>
+__global__ void k_l2p(const uint32_t *d_nb, const uint64_t *bkey, const uint32_t *bstart, const uint32_t *bcount,
+                      const double *x, const double *y, const double *z, const uint32_t *src, Geo geo, double lam,
+                      int p, int K, const typename C2<T>::t *L, double *phi, double *field) {
+  typedef typename C2<T>::t T2;
+  __shared__ T2 Ls[4][KHALF_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t box = (int64_t)blockIdx.x * 4 + warp;
+  if (box >= *d_nb) return;
+  for (int e = lane; e < K; e += 32) Ls[warp][e] = L[(size_t)box * K + e];
+  __syncwarp();
+  double cx, cy, cz;
+  box_center(bkey[box], geo, cx, cy, cz);
+  const double ih = 1.0 / geo.h;
+  const T lh = (T)(lam * geo.h);
+  const uint32_t st = bstart[box], cnt = bcount[box];
+  const T2 *Lw = Ls[warp];
+  for (uint32_t j = lane; j < cnt; j += 32) {
+    const uint32_t k = st + j;
+    const T rx = (T)((x[k] - cx) * ih), ry = (T)((y[k] - cy) * ih), rz = (T)((z[k] - cz) * ih);
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    T it[PT + 3];
+    itilde_all<T, PT + 2>(lh * lh * r2, it);
+    T ph = 0, S1 = 0, Gz = 0, Gpr = 0, Gpi = 0;
+    T2 Rmm = T2{(T)(0.5 / sqrt(PI)), T(0)};
+#pragma unroll
+    for (int m = 0; m <= PT; ++m) {
+      if (m > p) break;
+      if (m > 0) {
+        const T s = (T)cK.sect[m];
+        const T2 t = T2{Rmm.x * rx - Rmm.y * ry, Rmm.x * ry + Rmm.y * rx};
+        Rmm = T2{s * t.x, s * t.y};
+      }
+      const T wm = m ? T(2) : T(1);
+      T2 p1 = T2{0, 0}, p2 = T2{0, 0};
+#pragma unroll
+      for (int n = m; n <= PT; ++n) {
+        if (n > p) break;
+        T2 R;
+        if (n == m) R = Rmm;
+        else if (n == m + 1) { const T s = (T)cK.sub[m] * rz; R = T2{s * p1.x, s * p1.y}; }
+        else {
+          const T a = (T)cK.A[n][m] * rz, b = (T)cK.B[n][m] * r2;
+          R = T2{a * p1.x - b * p2.x, a * p1.y - b * p2.y};
+        }
+        p2 = p1;
+        p1 = R;
+        const T2 Lnm = Lw[hidx(n, m)];
+        const T re = Lnm.x * R.x - Lnm.y * R.y;
+        ph += wm * it[n] * re;
+        S1 += wm * it[n + 1] / T(2 * n + 3) * re;
+        if (n < p) {
+          const T in1 = it[n + 1];
+          const T2 Lz = Lw[hidx(n + 1, m)];
+          Gz += wm * in1 * (T)cK.gz[n][m] * (Lz.x * R.x - Lz.y * R.y);
+          if (m >= 1) {
+            const T2 La = Lw[hidx(n + 1, m - 1)];
+            const T ca = in1 * (T)cK.ga[n][m];
+            Gpr += ca * (La.x * R.x - La.y * R.y);
+            Gpi += ca * (La.x * R.y + La.y * R.x);
+          }
+          const T2 Lb = Lw[hidx(n + 1, m + 1)];
+          const T cb = in1 * (T)cK.gb[n][m];
+          // - conj(Lb R)
+          Gpr -= cb * (Lb.x * R.x - Lb.y * R.y);
+          Gpi += cb * (Lb.x * R.y + Lb.y * R.x);
+        }
+      }
+    }
+    const uint32_t i = src[k];
+    phi[i] += (double)ph;
+    if (field) {
+      const double l2h = lam * lam * geo.h;  // lambda^2 r = lambda^2 h r_u
+      field[3 * i] -= l2h * (double)rx * (double)S1 + (double)Gpr * ih;
+      field[3 * i + 1] -= l2h * (double)ry * (double)S1 + (double)Gpi * ih;
+      field[3 * i + 2] -= l2h * (double)rz * (double)S1 + (double)Gz * ih;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// free-space P2P over the near list (27 neighbours incl. the box itself), pair math in T,
+// per-neighbour partial sums in T, per-target accumulation in FP64
+// ---------------------------------------------------------------------------------------
+constexpr int P2P_THREADS = 128;
+
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
+
+// Mixed precision keeps each offset from the box centre as an FP32 pair hi + lo (the FP64
+// offset to 48 bits); the pair difference (hi_t - hi_s) + (lo_t - lo_s) is then accurate to
+// FP32 precision of the difference itself, also for close pairs.
+template <typename T>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p_free(const uint32_t *d_nb, const uint64_t *bkey,
+                                                          const uint32_t *bstart, const uint32_t *bcount,
+                                                          const int32_t *ulist, const double *x, const double *y,
+                                                          const double *z, const double *q, const uint32_t *src,
+                                                          Geo geo, double lam, double scale, double *phi,
+                                                          double *field) {
+  constexpr bool comp = sizeof(T) == 4;
+  __shared__ T sx[P2P_THREADS], sy[P2P_THREADS], sz[P2P_THREADS], sq[P2P_THREADS];
+  __shared__ T lx[P2P_THREADS], ly[P2P_THREADS], lz[P2P_THREADS];
+  __shared__ uint32_t sk[P2P_THREADS];
+  const uint32_t box = blockIdx.x;
+  if (box >= *d_nb) return;
+  double cx, cy, cz;
+  box_center(bkey[box], geo, cx, cy, cz);
+  const uint32_t tst = bstart[box], tcnt = bcount[box];
+  const T tl = (T)lam;
+  for (uint32_t t0 = 0; t0 < tcnt; t0 += P2P_THREADS) {
+    const uint32_t tj = t0 + threadIdx.x;
+    const bool tv = tj < tcnt;
+    const uint32_t tk = tst + (tv ? tj : 0);
+    const double ox = x[tk] - cx, oy = y[tk] - cy, oz = z[tk] - cz;
+    const T px = (T)ox, py = (T)oy, pz = (T)oz;
+    const T plx = comp ? (T)(ox - (double)px) : T(0), ply = comp ? (T)(oy - (double)py) : T(0),
+            plz = comp ? (T)(oz - (double)pz) : T(0);
+    double aphi = 0, ax = 0, ay = 0, az = 0;
+    for (int o = 0; o < NNEAR; ++o) {
+      const int s = ulist[(size_t)box * NNEAR + o];
+      if (s < 0) continue;
+      const uint32_t sst = bstart[s], scnt = bcount[s];
+      T fphi = 0, fx = 0, fy = 0, fz = 0;
+      for (uint32_t s0 = 0; s0 < scnt; s0 += P2P_THREADS) {
+        __syncthreads();
+        if (s0 + threadIdx.x < scnt) {
+          const uint32_t k = sst + s0 + threadIdx.x;
+          const double qx = x[k] - cx, qy = y[k] - cy, qz = z[k] - cz;
+          const T hx = (T)qx, hy = (T)qy, hz = (T)qz;
+          sx[threadIdx.x] = hx;
+          sy[threadIdx.x] = hy;
+          sz[threadIdx.x] = hz;
+          if (comp) {
+            lx[threadIdx.x] = (T)(qx - (double)hx);
+            ly[threadIdx.x] = (T)(qy - (double)hy);
+            lz[threadIdx.x] = (T)(qz - (double)hz);
+          }
+          sq[threadIdx.x] = (T)q[k];
+          sk[threadIdx.x] = k;
+        }
+        __syncthreads();
+        const uint32_t nn = min((uint32_t)P2P_THREADS, scnt - s0);
+        if (tv) {
+          for (uint32_t jj = 0; jj < nn; ++jj) {
+            T dx = px - sx[jj], dy = py - sy[jj], dz = pz - sz[jj];
+            if (comp) {
+              dx += plx - lx[jj];
+              dy += ply - ly[jj];
+              dz += plz - lz[jj];
+            }
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (sk[jj] == tk || r2 == T(0)) continue;
+            const T ri = frsqrt(r2);
+            const T r = r2 * ri;
+            const T e = sq[jj] * fexp(-tl * r) * ri;
+            fphi += e;
+            const T f = e * (T(1) + tl * r) * ri * ri;
+            fx += f * dx;
+            fy += f * dy;
+            fz += f * dz;
+          }
+        }
+      }
+      aphi += (double)fphi;
+      ax += (double)fx;
+      ay += (double)fy;
+      az += (double)fz;
+    }
+    if (tv) {
+      const uint32_t i = src[tk];
+      phi[i] += scale * aphi;
+      if (field) {
+        field[3 * i] += scale * ax;
+        field[3 * i + 1] += scale * ay;
+        field[3 * i + 2] += scale * az;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// reaction near field: target leaf box vs adjacent image leaf boxes across the interface,
+// Sommerfeld integral by the precomputed node rule, truncated per pair at exp(-36)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float fj0(float x) { return j0f(x); }
+__device__ __forceinline__ double fj0(double x) { return j0(x); }
+__device__ __forceinline__ float fj1(float x) { return j1f(x); }
+__device__ __forceinline__ double fj1(double x) { return j1(x); }
+
+template <typename T>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p_react(
+    const uint32_t *d_nb, const uint64_t *tkey, const uint32_t *tstart, const uint32_t *tcount, const int32_t *ulist,
+    const double *tx, const double *ty, const double *tz, const uint32_t *tsrc, const uint32_t *istart,
+    const uint32_t *icount, const double *ix, const double *iy, const double *iz, const double *iq,
+    const uint64_t *ikey, Geo geo, double dI, double sa, const double *nodes, int nq, double *phi, double *field) {
+  __shared__ T sx[P2P_THREADS], sy[P2P_THREADS], szs[P2P_THREADS], sq[P2P_THREADS];
+  __shared__ int st[P2P_THREADS];
+  const uint32_t box = blockIdx.x;
+  if (box >= *d_nb) return;
+  bool any = false;
+  for (int o = 0; o < NNEAR; ++o) any |= ulist[(size_t)box * NNEAR + o] >= 0;
+  if (!any) return;
+  double cx, cy, cz;
+  box_center(tkey[box], geo, cx, cy, cz);
+  const uint32_t tst = tstart[box], tcnt = tcount[box];
+  for (uint32_t t0 = 0; t0 < tcnt; t0 += P2P_THREADS) {
+    const uint32_t tj = t0 + threadIdx.x;
+    const bool tv = tj < tcnt;
+    const uint32_t tk = tst + (tv ? tj : 0);
+    const T px = (T)(tx[tk] - cx), py = (T)(ty[tk] - cy);
+    const T zt = (T)fabs(tz[tk] - dI);
+    double aphi = 0, ax = 0, ay = 0, az = 0;
+    for (int o = 0; o < NNEAR; ++o) {
+      const int s = ulist[(size_t)box * NNEAR + o];
+      if (s < 0) continue;
+      const uint32_t sst = istart[s], scnt = icount[s];
+      for (uint32_t s0 = 0; s0 < scnt; s0 += P2P_THREADS) {
+        __syncthreads();
+        if (s0 + threadIdx.x < scnt) {
+          const uint32_t k = sst + s0 + threadIdx.x;
+          sx[threadIdx.x] = (T)(ix[k] - cx);
+          sy[threadIdx.x] = (T)(iy[k] - cy);
+          szs[threadIdx.x] = (T)fabs(iz[k] - dI);
+          sq[threadIdx.x] = (T)iq[k];
+          st[threadIdx.x] = (int)(ikey[k] & 15ull);
+        }
+        __syncthreads();
+        const uint32_t nn = min((uint32_t)P2P_THREADS, scnt - s0);
+        if (!tv) continue;
+        for (uint32_t jj = 0; jj < nn; ++jj) {
+          const T dx = px - sx[jj], dy = py - sy[jj];
+          const T rho = sqrt(dx * dx + dy * dy);
+          const T zs = szs[jj];
+          const T xcut = T(36) / (zt + zs);
+          const double *nd = nodes + (size_t)st[jj] * nq * 4;
+          T v = 0, vr = 0, vz = 0;
+          for (int k = 0; k < nq; ++k) {
+            const T lr = (T)nd[4 * k];
+            if (lr > xcut) break;
+            const T E = (T)nd[4 * k + 1] * fexp(-(T)nd[4 * k + 2] * zt - (T)nd[4 * k + 3] * zs);
+            const T a = lr * rho;
+            const T J0 = fj0(a);
+            const T J1r = rho > T(0) ? fj1(a) / rho : T(0.5) * lr;
+            v += E * J0;
+            vr += E * lr * J1r;
+            vz += E * J0 * (T)nd[4 * k + 2];
+          }
+          const T qq = sq[jj];
+          aphi += (double)(qq * v);
+          ax += (double)(qq * dx * vr);
+          ay += (double)(qq * dy * vr);
+          az += (double)(qq * vz);
+        }
+      }
+    }
+    if (tv) {
+      const uint32_t i = tsrc[tk];
+      phi[i] += aphi;
+      if (field) {
+        field[3 * i] += ax;
+        field[3 * i + 1] += ay;
+        field[3 * i + 2] += sa * az;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// driver for one group
+// ---------------------------------------------------------------------------------------
+struct Tables {
+  int32_t *cls_free, *cls_react;  // [343], [2][3][343]
+  void *rot, *rot4;               // per precision
+};
+Tables g_tab_d, g_tab_f;
+static bool g_tab_ready = false;
+
+static void make_tables(Ctx &c) {
+  if (g_tab_ready) return;
+  std::vector<int32_t> cf(NOFF, -1), cr(2 * 3 * NOFF, -1);
+  const int r2v[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+  auto rho_idx = [&](int dx, int dy) {
+    for (int k = 0; k < NRHO; ++k)
+      if (r2v[k] == dx * dx + dy * dy) return k;
+    return -1;
+  };
+  const int kkt[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
+  std::vector<double> rot(NOFF * (PMAX + 1) * 2), rot4(4 * (PMAX + 1) * 2);
+  for (int o = 0; o < NOFF; ++o) {
+    const int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
+    const int cheb = std::max(abs(dx), std::max(abs(dy), abs(dz)));
+    if (cheb >= 2) cf[o] = rho_idx(dx, dy) * 7 + dz + 3;
+    for (int a = 1; a <= 2; ++a)
+      for (int kt = 0; kt < 3; ++kt) {
+        const int ks = (a == 1) ? -dz - 1 - kt : dz - 1 - kt;
+        if (cheb < 2 || ks < 0 || kt + ks > 2) continue;
+        cr[((a - 1) * 3 + kt) * NOFF + o] = rho_idx(dx, dy) * NKK + kkt[kt][ks];
+      }
+    const double ph = (dx == 0 && dy == 0) ? 0.0 : atan2(-(double)dy, -(double)dx);
+    for (int m = 0; m <= PMAX; ++m) {
+      rot[(o * (PMAX + 1) + m) * 2] = cos(m * ph);
+      rot[(o * (PMAX + 1) + m) * 2 + 1] = sin(m * ph);
+    }
+  }
+  for (int dir = 0; dir < 4; ++dir) {
+    const int bx = dir >> 1, by = dir & 1;
+    const double ph = atan2(2.0 * by - 1.0, 2.0 * bx - 1.0);
+    for (int m = 0; m <= PMAX; ++m) {
+      rot4[(dir * (PMAX + 1) + m) * 2] = cos(m * ph);
+      rot4[(dir * (PMAX + 1) + m) * 2 + 1] = sin(m * ph);
+    }
+  }
+  int32_t *dcf, *dcr;
+  LPB_CUDA(cudaMalloc(&dcf, sizeof(int32_t) * NOFF));
+  LPB_CUDA(cudaMalloc(&dcr, sizeof(int32_t) * 6 * NOFF));
+  LPB_CUDA(cudaMemcpy(dcf, cf.data(), sizeof(int32_t) * NOFF, cudaMemcpyHostToDevice));
+  LPB_CUDA(cudaMemcpy(dcr, cr.data(), sizeof(int32_t) * 6 * NOFF, cudaMemcpyHostToDevice));
+  std::vector<float> rotf(rot.begin(), rot.end()), rot4f(rot4.begin(), rot4.end());
+  void *rd, *r4d, *rf, *r4f;
+  LPB_CUDA(cudaMalloc(&rd, sizeof(double) * rot.size()));
+  LPB_CUDA(cudaMalloc(&r4d, sizeof(double) * rot4.size()));
+  LPB_CUDA(cudaMalloc(&rf, sizeof(float) * rot.size()));
+  LPB_CUDA(cudaMalloc(&r4f, sizeof(float) * rot4.size()));
+  LPB_CUDA(cudaMemcpy(rd, rot.data(), sizeof(double) * rot.size(), cudaMemcpyHostToDevice));
+  LPB_CUDA(cudaMemcpy(r4d, rot4.data(), sizeof(double) * rot4.size(), cudaMemcpyHostToDevice));
+  LPB_CUDA(cudaMemcpy(rf, rotf.data(), sizeof(float) * rotf.size(), cudaMemcpyHostToDevice));
+  LPB_CUDA(cudaMemcpy(r4f, rot4f.data(), sizeof(float) * rot4f.size(), cudaMemcpyHostToDevice));
+  g_tab_d = Tables{dcf, dcr, rd, r4d};
+  g_tab_f = Tables{dcf, dcr, rf, r4f};
+  g_tab_ready = true;
+  (void)c;
+}
+
+void init_fmm_tables(Ctx &c) {
+  make_tables(c);
+  upload_consts(c.stream);
+}
+
+template <typename T, int PT>
+static void launch_p2m(Ctx &c, const uint32_t *d_nseg, int64_t nseg_cap, const uint32_t *sst, const uint32_t *scnt,
+                       const uint32_t *sbox, const uint32_t *styp, int ntypes, const uint64_t *bkey,
+                       const PointSet &P, Geo geo, const LamTab &lt, void *M) {
+  typedef typename C2<T>::t T2;
+  k_p2m<T, PT><<<(unsigned)((nseg_cap + 3) / 4), 128, 0, c.stream>>>(d_nseg, sst, scnt, sbox, styp, ntypes, bkey,
+                                                                      P.x, P.y, P.z, P.q, geo, lt, c.p, c.K,
+                                                                      (T2 *)M);
+  LPB_LAUNCH();
+  c.launches++;
+}
+template <typename T, int PT>
+static void launch_l2p(Ctx &c, const Level &Lv, int64_t nb, const PointSet &P, Geo geo, double lam, const void *L,
+                       double *phi, double *field) {
+  typedef typename C2<T>::t T2;
+  k_l2p<T, PT><<<(unsigned)((nb + 3) / 4), 128, 0, c.stream>>>(Lv.d_n, Lv.key, Lv.start, Lv.count, P.x, P.y, P.z,
+                                                                P.src, geo, lam, c.p, c.K, (const T2 *)L, phi, field);
+  LPB_LAUNCH();
+  c.launches++;
+}
+
+template <typename T, int TPT, int NR>
+static void launch_m2l_t(Ctx &c, const std::vector<XJob> &jobs, int64_t items) {
+  constexpr int TT = 16 * TPT, KR = 16 * NR;
+  const size_t smem = sizeof(T) * (2 * KR * M2L_KC + 2 * M2L_KC * TT) + sizeof(int) * 2 * TT;
+  static bool attr = false;
+  if (!attr) {
+    LPB_CUDA(cudaFuncSetAttribute(k_m2l<T, TPT, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  XJob *dj = c.arena.get<XJob>(jobs.size());
+  LPB_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(XJob) * jobs.size(), cudaMemcpyHostToDevice, c.stream));
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  k_m2l<T, TPT, NR><<<(unsigned)items, 256, smem, c.stream>>>(dj, (int)jobs.size(), (const T *)tb.rot, c.K);
+  LPB_LAUNCH();
+  c.launches++;
+}
+
+#define PT_DISPATCH(F, ...)                                   \
+  do {                                                        \
+    if (c.p <= 5) F<T, 5>(__VA_ARGS__);                       \
+    else if (c.p <= 8) F<T, 8>(__VA_ARGS__);                  \
+    else if (c.p <= 10) F<T, 10>(__VA_ARGS__);                \
+    else if (c.p <= 12) F<T, 12>(__VA_ARGS__);                \
+    else F<T, 16>(__VA_ARGS__);                               \
+  } while (0)
+
+template <typename T>
+static Geo geo_at(const Group &g, int l) {
+  Geo G;
+  G.o[0] = g.root[0] - g.root[3];
+  G.o[1] = g.root[1] - g.root[3];
+  G.o[2] = g.root[2] - g.root[3];
+  G.h = g.h(l);
+  return G;
+}
+
+// P2M and M2M of one group; local expansions of every level zeroed
+template <typename T>
+static void upward_t(Ctx &c, Group &g, int parts) {
+  typedef typename C2<T>::t T2;
+  const int K = c.K, D = g.D;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  const bool dofree = g.is_free && (parts & 1);
+  const bool doreact = (parts & 2) && g.I.np > 0;
+  LamTab lt_t, lt_i;
+  for (int k = 0; k < 2 * MAXLAYER; ++k) lt_t.v[k] = lt_i.v[k] = c.md.lam[g.l];
+  for (int t = 0; t < g.ntypes; ++t) {
+    int lp, b;
+    type_decode(t, lp, b);
+    lt_i.v[t] = c.md.lam[lp];
+  }
+  for (int l = 2; l <= D; ++l) {
+    const int64_t ntb = g.T.lev[l].n, nib = g.I.lev[l].n;
+    g.Lt[l] = c.arena.get<T2>(ntb * K);
+    LPB_CUDA(cudaMemsetAsync(g.Lt[l], 0, sizeof(T2) * ntb * K, c.stream));
+    if (dofree) g.Mfree[l] = c.arena.get<T2>(ntb * K);
+    if (doreact) g.Mimg[l] = c.arena.get<T2>(nib * g.ntypes * K);
+  }
+  if (dofree)
+    PT_DISPATCH(launch_p2m, c, g.T.lev[D].d_n, g.T.lev[D].n, g.T.lev[D].start, g.T.lev[D].count, nullptr, nullptr, 1,
+                g.T.lev[D].key, g.T, geo_at<T>(g, D), lt_t, g.Mfree[D]);
+  if (doreact) {
+    LPB_CUDA(cudaMemsetAsync(g.Mimg[D], 0, sizeof(T2) * g.I.lev[D].n * g.ntypes * K, c.stream));
+    PT_DISPATCH(launch_p2m, c, g.I.d_nseg, g.I.nseg, g.I.seg_start, g.I.seg_count, g.I.seg_box, g.I.seg_type,
+                g.ntypes, g.I.lev[D].key, g.I, geo_at<T>(g, D), lt_i, g.Mimg[D]);
+  }
+  for (int l = D; l >= 3; --l) {
+    if (dofree && g.T.lev[l - 1].n) {
+      k_m2m<T><<<dim3((unsigned)g.T.lev[l - 1].n, 1), 128, 0, c.stream>>>(
+          g.T.lev[l - 1].d_n, g.T.lev[l - 1].start, g.T.lev[l - 1].count, g.T.lev[l].key, 1, (const T2 *)g.Mfree[l],
+          (T2 *)g.Mfree[l - 1], (const T *)g.op_m2m_t[l], (const T *)tb.rot4, K);
+      LPB_LAUNCH();
+      c.launches++;
+    }
+    if (doreact && g.I.lev[l - 1].n) {
+      k_m2m<T><<<dim3((unsigned)g.I.lev[l - 1].n, g.ntypes), 128, 0, c.stream>>>(
+          g.I.lev[l - 1].d_n, g.I.lev[l - 1].start, g.I.lev[l - 1].count, g.I.lev[l].key, g.ntypes,
+          (const T2 *)g.Mimg[l], (T2 *)g.Mimg[l - 1], (const T *)g.op_m2m_i[l], (const T *)tb.rot4, K);
+      LPB_LAUNCH();
+      c.launches++;
+    }
+  }
+}
+
+// every multipole-to-local translation of every group and level in one launch
+template <typename T>
+static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
+  constexpr int TPT = sizeof(T) == 4 ? 4 : 2;
+  constexpr int TT = 16 * TPT;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  std::vector<XJob> jobs;
+  int64_t items = 0;
+  auto add = [&](const int32_t *tlist, const uint32_t *d_ntl, int64_t ntb, const int32_t *vlist,
+                 const int32_t *cls_of, const void *M, const void *ops, void *L, int ntypes) {
+    XJob j;
+    j.tlist = tlist; j.d_ntl = d_ntl; j.ntb = ntb; j.vlist = vlist; j.cls_of = cls_of;
+    j.M = M; j.ops = ops; j.L = L; j.ntypes = ntypes; j.pad = 0; j.item0 = items;
+    jobs.push_back(j);
+    items += ((ntb + TT - 1) / TT) * M2L_NSLICE;
+  };
+  for (auto &g : groups) {
+    const bool dofree = g.is_free && (parts & 1);
+    const bool react_far = (parts & 2) && g.I.np > 0 && !(parts & 8);
+    for (int l = 2; l <= g.D; ++l) {
+      const int64_t ntb = g.T.lev[l].n;
+      if (!ntb) continue;
+      if (dofree) add(nullptr, nullptr, ntb, g.vfree[l], tb.cls_free, g.Mfree[l], g.op_free[l], g.Lt[l], 1);
+      if (react_far && g.vreact[l])
+        for (int kt = 0; kt < 3; ++kt)
+          add(g.rows[l] + (size_t)kt * ntb, g.nrows[l] + kt, ntb, g.vreact[l],
+              tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], g.Lt[l], g.ntypes);
+    }
+  }
+  if (jobs.empty()) return;
+  if (c.K <= 80) launch_m2l_t<T, TPT, 5>(c, jobs, items);
+  else if (c.K <= 128) launch_m2l_t<T, TPT, 8>(c, jobs, items);
+  else launch_m2l_t<T, TPT, 10>(c, jobs, items);
+}
+
+// L2L (adding the parent's shifted expansion), L2P and the near fields of one group
+template <typename T>
+static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) {
+  typedef typename C2<T>::t T2;
+  const int K = c.K, D = g.D;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  const bool dofree = g.is_free && (parts & 1);
+  const bool doreact = (parts & 2) && g.I.np > 0;
+  const bool react_near = doreact && !(parts & 4);
+  for (int l = 3; l <= D; ++l) {
+    const int64_t ntb = g.T.lev[l].n;
+    if (!ntb) continue;
+    k_l2l<T><<<(unsigned)ntb, 128, 0, c.stream>>>(g.T.lev[l].d_n, g.T.lev[l].parent, g.T.lev[l].key,
+                                                  (const T2 *)g.Lt[l - 1], (T2 *)g.Lt[l], (const T *)g.op_l2l[l],
+                                                  (const T *)tb.rot4, K);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+  PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
+  if (dofree) {
+    k_p2p_free<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(
+        g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q,
+        g.T.src, geo_at<T>(g, D), c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+  if (react_near && g.ureact && g.nodes) {
+    k_p2p_react<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(
+        g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count, g.ureact, g.T.x, g.T.y, g.T.z, g.T.src,
+        g.I.lev[D].start, g.I.lev[D].count, g.I.x, g.I.y, g.I.z, g.I.q, g.I.key, geo_at<T>(g, D), g.dI,
+        g.a == 1 ? 1.0 : -1.0, g.nodes, g.nq, phi, field);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+}
+
+void run_fmm_all(Ctx &c, std::vector<Group> &groups, int parts, double *phi, double *field) {
+  const bool d = c.opts.precision == LPBFMM_FP64;
+  for (auto &g : groups) d ? upward_t<double>(c, g, parts) : upward_t<float>(c, g, parts);
+  prof_mark(c, "upward");
+  d ? m2l_all_t<double>(c, groups, parts) : m2l_all_t<float>(c, groups, parts);
+  prof_mark(c, "m2l");
+  for (auto &g : groups) d ? downward_t<double>(c, g, parts, phi, field) : downward_t<float>(c, g, parts, phi, field);
+  prof_mark(c, "downward");
+}
+
+}  // namespace lpb

@@ -1,0 +1,576 @@
+// Translation operators, built on the device in FP64 for every evaluation.
+//
+// All translations have the azimuth-factored form (half representation m >= 0):
+//   X'_{nu mu} = e^{i mu phi} X_{nu mu},  Y_{nm} = P Re X' + i Q Im X',  out_{nm} += e^{-i m phi} Y_{nm}
+// with real P, Q of size K x K, K = (p+1)(p+2)/2.
+//  * free-space M2M / L2L / M2L (Sec. 3.1, Theorems 1-3): Gaunt-coefficient sums over
+//    i_q(lambda b) or k_q(lambda b) times Phat_q(cos theta_b);
+//  * reaction M2L (Sec. 3.4 eq. metoleimage2, Sec. 3.5): the scaled Sommerfeld integrals
+//    S^K S_{K d, ij} (eq. M2Ltable) by composite Gauss-Legendre quadrature for d = 0, 1,
+//    the forward recurrence (eq. recurrence1) for d >= 2, and a Legendre-product expansion
+//    of the two plane-wave factors (eq. metoletableform), in this library's own derivation.
+// Scaling (Sec. 3.5, "scaling"): with h the box size, multipole coefficients are stored as
+// M~_n = M_n (2n+1)!!/(lambda h)^n and local ones as L~_n = c L_n (lambda h)^n/(2n+1)!!
+// (c = lambda/(2 pi^2 eps) for the free-space part, 1 for reaction parts), so that
+// phi = sum L~_nm itilde_n(lambda r) R_n^m(r/h) with R_n^m = r^n Y_n^m.
+#include "internal.h"
+
+namespace lpb {
+
+struct OpDesc {
+  int kind;     // 0 = M2L free, 1 = M2M, 2 = L2L
+  int out_inv;  // 0: out scale x^n/(2n+1)!!, 1: (2n+1)!!/x^n
+  int in_inv;
+  int pad;
+  double lam, bnorm, cosb, xout, xin, pref;
+  int64_t dst;  // element offset of P (Q follows after K*K)
+};
+
+__device__ __forceinline__ void hdecode(int o, int &n, int &m) {
+  n = (int)((sqrt(8.0 * o + 1.0) - 1.0) * 0.5);
+  while ((n + 1) * (n + 2) / 2 <= o) ++n;
+  while (n * (n + 1) / 2 > o) --n;
+  m = o - n * (n + 1) / 2;
+}
+
+template <typename T>
+__global__ void k_build_ops(const OpDesc *descs, int p, int K, const double *gaunt, T *out) {
+  const OpDesc d = descs[blockIdx.x];
+  __shared__ double f[2 * PMAX + 1];
+  __shared__ double Pl[(2 * PMAX + 1) * (2 * PMAX + 2) / 2];
+  __shared__ double so[PMAX + 1], si[PMAX + 1];
+  const int qmax = 2 * p;
+  if (threadIdx.x == 0) {
+    const double x = d.lam * d.bnorm;
+    if (d.kind == 0) kbessel_all(x, qmax, f);
+    else ibessel_all(x, qmax, f);
+    phat_all(d.cosb, qmax, Pl);
+    for (int n = 0; n <= p; ++n) {
+      const double a = pow(d.xout, n) / dfact2(n), b = pow(d.xin, n) / dfact2(n);
+      so[n] = (d.out_inv ? 1.0 / a : a) * d.pref;
+      si[n] = d.in_inv ? 1.0 / b : b;
+    }
+  }
+  __syncthreads();
+  const int NF = (p + 1) * (p + 1), NQ = 2 * p + 1;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int o = e / K, i = e % K;
+    int n, m, nu, mu;
+    hdecode(o, n, m);
+    hdecode(i, nu, mu);
+    double r[2] = {0.0, 0.0};
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const int mus = sgn ? -mu : mu;
+      if (sgn && mu == 0) break;
+      double s = 0.0;
+      for (int q = abs(n - nu); q <= n + nu; q += 2) {
+        if (d.kind == 2 || d.kind == 0) {
+          const int k = m - mus;
+          if (abs(k) > q) continue;
+          s += f[q] * phat_signed(Pl, q, k) * gaunt[((size_t)fidx(nu, mus) * NF + fidx(n, m)) * NQ + q];
+        } else {
+          const int k = mus - m;
+          if (abs(k) > q) continue;
+          s += f[q] * phat_signed(Pl, q, k) * gaunt[((size_t)fidx(n, m) * NF + fidx(nu, mus)) * NQ + q];
+        }
+      }
+      s *= 4.0 * PI * so[n] * si[nu];
+      if (d.kind == 0 && (n & 1)) s = -s;
+      r[sgn] = s;
+    }
+    double P, Q;
+    if (mu == 0) { P = r[0]; Q = 0.0; }
+    else {
+      const double sg = (mu & 1) ? -1.0 : 1.0;
+      P = r[0] + sg * r[1];
+      Q = r[0] - sg * r[1];
+    }
+    out[d.dst + (size_t)o * K + i] = (T)P;
+    out[d.dst + (size_t)K * K + (size_t)o * K + i] = (T)Q;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Reaction operators
+// ---------------------------------------------------------------------------------------
+struct RDesc {
+  int l, a, lp, b, tau, ntypes, st, pad;
+  double h, Lam, Lamp;
+  const uint8_t *used;   // [NREACT_CLS]
+  double *stab;          // [NREACT_CLS][ntypes][TS]
+  double *coef;          // [K*K][NS]
+  int64_t dst;           // element offset of class 0, type tau in the op array
+};
+
+__constant__ double c_rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+__constant__ int c_kk_t[NKK] = {0, 0, 1, 0, 1, 2};
+__constant__ int c_kk_s[NKK] = {0, 1, 0, 2, 1, 0};
+
+constexpr int QCHUNK = 256;
+constexpr int MAXPANEL = 1024;
+
+__device__ __forceinline__ int stab_index(int KT, int K, int d, int ij) { return ((K * (KT + 1)) + d) * 4 + ij; }
+
+__device__ void make_panels(double umax, double wmax, double lmin, double *pu, double *pw, int *np) {
+  int n = 0;
+  double u = 0.0;
+  while (u < umax && n < MAXPANEL) {
+    double w = fmin(wmax, 0.5 * (lmin + u));
+    if (u + w > umax) w = umax - u;
+    pu[n] = u;
+    pw[n] = w;
+    u += w;
+    ++n;
+  }
+  *np = n;
+}
+
+// Gauss-Legendre 16-point rule on [-1,1], nodes by Newton iteration (shared by the kernels)
+__device__ void gl16(double *x, double *w) {
+  for (int i = 0; i < 16; ++i) {
+    double z = cos(PI * (i + 0.75) / 16.5), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= 16; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+      dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= 16; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+    dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// quadrature of S^K S_{K d, ij} for d = 0, 1, K = 0..KT (block = 256 threads, 8 warps)
+__global__ void k_stab_quad(const RDesc *descs, Medium md, int KT, double tol) {
+  const RDesc D = descs[blockIdx.y];
+  const int cls = blockIdx.x;
+  if (D.used && !D.used[cls]) return;
+  __shared__ double pu[MAXPANEL], pw[MAXPANEL];
+  __shared__ double gx[16], gw[16];
+  __shared__ double g[8][QCHUNK];
+  __shared__ double uu[QCHUNK];
+  __shared__ int npan;
+  const int ri = cls / NKK, kk = cls % NKK;
+  const double rh = sqrt(c_rho2[ri]);
+  const double zt = c_kk_t[kk] + 0.5, zs = c_kk_s[kk] + 0.5, zeta = zt + zs;
+  if (threadIdx.x == 0) {
+    gl16(gx, gw);
+    // u^KT e^{-zeta u} has fallen by tol below its peak at u = KT/zeta
+    const double pk = fmax(KT / zeta, 1.0 / zeta);
+    const double target = KT * log(pk) - zeta * pk + log(tol) - 3.0;
+    double umax = pk;
+    while (KT * log(umax) - zeta * umax > target) umax += 0.25 / zeta;
+    double wmax = 2.0 / zeta;
+    if (rh > 0.0) wmax = fmin(wmax, PI / rh);
+    make_panels(umax, wmax, fmin(D.Lam, D.Lamp), pu, pw, &npan);
+  }
+  __syncthreads();
+  const int nnodes = npan * 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dsel = warp >> 2, ij = warp & 3;
+  double acc[KMAX_TAB + 1];
+#pragma unroll
+  for (int k = 0; k <= KMAX_TAB; ++k) acc[k] = 0.0;
+  for (int c0 = 0; c0 < nnodes; c0 += QCHUNK) {
+    const int j = c0 + threadIdx.x;
+    if (j < nnodes) {
+      const int pi_ = j >> 4, gi = j & 15;
+      const double u = pu[pi_] + 0.5 * pw[pi_] * (gx[gi] + 1.0);
+      const double w = 0.5 * pw[pi_] * gw[gi];
+      const double sg = layer_sigma(md, u / D.h, D.l, D.a, D.lp, D.b);
+      const double uz = sqrt(D.Lam * D.Lam + u * u), uzp = sqrt(D.Lamp * D.Lamp + u * u);
+      const double base = w * sg * exp(-uz * zt - uzp * zs) / uz;
+      const double fi = D.Lam / uz, fj = D.Lamp / uzp;
+      const double j0v = j0(u * rh), j1v = j1(u * rh);
+      const double f00 = base, f01 = base * fj, f10 = base * fi, f11 = base * fi * fj;
+      g[0][threadIdx.x] = f00 * j0v; g[1][threadIdx.x] = f01 * j0v;
+      g[2][threadIdx.x] = f10 * j0v; g[3][threadIdx.x] = f11 * j0v;
+      g[4][threadIdx.x] = f00 * j1v; g[5][threadIdx.x] = f01 * j1v;
+      g[6][threadIdx.x] = f10 * j1v; g[7][threadIdx.x] = f11 * j1v;
+      uu[threadIdx.x] = u;
+    } else {
+      for (int k = 0; k < 8; ++k) g[k][threadIdx.x] = 0.0;
+      uu[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    for (int jj = lane; jj < QCHUNK; jj += 32) {
+      const double v = g[warp][jj], u = uu[jj];
+      double pw_ = v;
+#pragma unroll
+      for (int k = 0; k <= KMAX_TAB; ++k) {
+        if (k <= KT) acc[k] += pw_;
+        pw_ *= u;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k <= KMAX_TAB; ++k) {
+    double v = acc[k];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[k] = v;
+  }
+  if (lane == 0) {
+    double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+    // ij index in the table: 2i + j ; warp ij = 2*i + j with f01 = (i=0,j=1)
+#pragma unroll
+    for (int k = 0; k <= KMAX_TAB; ++k) {
+      if (k > KT) break;
+      if (dsel == 1 && k < 1) continue;
+      const double nrm = 1.0 / sqrt(tgamma(k + dsel + 1.0) * tgamma(k - dsel + 1.0));
+      S[stab_index(KT, k, dsel, ij)] = acc[k] * nrm;
+    }
+  }
+}
+
+// forward recurrence in d (Sec. 3.5 eq. recurrence1), one warp per class
+__global__ void k_stab_recur(const RDesc *descs, int KT) {
+  const RDesc D = descs[blockIdx.y];
+  const int cls = blockIdx.x;
+  if (D.used && !D.used[cls]) return;
+  const int ri = cls / NKK;
+  const double rh = sqrt(c_rho2[ri]);
+  double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  const int lane = threadIdx.x;
+  for (int d = 1; d < KT; ++d) {
+    for (int e = lane; e < (KT + 1) * 4; e += 32) {
+      const int K = e >> 2, ij = e & 3;
+      if (K < d + 1) continue;
+      double v = 0.0;
+      if (rh > 0.0) {
+        const double apd = sqrt(double(K + d) * (K + d + 1)), amd = sqrt(double(K - d) * (K - d + 1));
+        v = (2.0 * d / apd) / rh * S[stab_index(KT, K - 1, d, ij)] - (amd / apd) * S[stab_index(KT, K, d - 1, ij)];
+      }
+      S[stab_index(KT, K, d + 1, ij)] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// C_s(n,m,nu,mu) = sum_{k+k'=s} c^{nm}_k c^{nu mu}_{k'} Lam^{n-m-2k} Lamp^{nu-mu-2k'}
+__global__ void k_react_coef(const RDesc *descs, const double *tpoly, int tpk, int p, int K) {
+  const RDesc D = descs[blockIdx.y];
+  const int NS = p + 2;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K * K) return;
+  const int o = e / K, i = e % K;
+  int n, m, nu, mu;
+  hdecode(o, n, m);
+  hdecode(i, nu, mu);
+  const int k1 = (n - m + 1) / 2, k2 = (nu - mu + 1) / 2;
+  for (int s = 0; s < NS; ++s) {
+    double acc = 0.0;
+    for (int k = 0; k <= k1; ++k) {
+      const int kp = s - k;
+      if (kp < 0 || kp > k2) continue;
+      acc += tpoly[o * tpk + k] * tpoly[i * tpk + kp] * pow(D.Lam, n - m - 2 * k) * pow(D.Lamp, nu - mu - 2 * kp);
+    }
+    D.coef[(size_t)e * NS + s] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, T *out) {
+  const RDesc D = descs[blockIdx.y];
+  const int cls = blockIdx.x;
+  if (D.used && !D.used[cls]) return;
+  __shared__ double fac[KMAX_TAB + 1][KMAX_TAB + 1];
+  __shared__ double smm[PMAX + 1];
+  for (int e = threadIdx.x; e < (KT + 1) * (KT + 1); e += blockDim.x) {
+    const int Kk = e / (KT + 1), d = e % (KT + 1);
+    fac[Kk][d] = (d <= Kk) ? sqrt(tgamma(Kk + d + 1.0) * tgamma(Kk - d + 1.0)) : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    double s = 1.0;
+    smm[0] = 1.0;
+    for (int m = 1; m <= p; ++m) { s *= -sqrt((2.0 * m + 1.0) / (2.0 * m)); smm[m] = s; }
+  }
+  __syncthreads();
+  const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  const int NS = p + 2;
+  const size_t KK = (size_t)K * K;
+  T *P = out + D.dst + (size_t)cls * D.ntypes * 2 * KK;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int o = e / K, i = e % K;
+    int n, m, nu, mu;
+    hdecode(o, n, m);
+    hdecode(i, nu, mu);
+    const int ii = (n - m) & 1, jj = (nu - mu) & 1;
+    double A = smm[m] * smm[mu] / (4.0 * PI) / (dfact2(n) * dfact2(nu)) / D.h;
+    if ((n - m) & 1) A *= D.st;                 // st^{n-m}
+    if ((nu - mu) & 1) A *= -D.st;              // (-st)^{nu-mu}
+    const int smax = (n - m + 1) / 2 + (nu - mu + 1) / 2;
+    double r[2] = {0.0, 0.0};
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      if (sgn && mu == 0) break;
+      const int dd = (sgn ? -mu : mu) - m, ad = abs(dd);
+      double acc = 0.0;
+      for (int s = 0; s <= smax; ++s) {
+        const int Kk = 1 + m + mu + 2 * s;
+        if (Kk > KT) break;
+        acc += D.coef[(size_t)e * NS + s] * fac[Kk][ad] * S[stab_index(KT, Kk, ad, 2 * ii + jj)];
+      }
+      if (dd < 0 && (ad & 1)) acc = -acc;
+      r[sgn] = A * acc;
+    }
+    double Pv, Qv;
+    if (mu == 0) { Pv = r[0]; Qv = 0.0; }
+    else {
+      const double sg = (mu & 1) ? -1.0 : 1.0;
+      Pv = r[0] + sg * r[1];
+      Qv = r[0] - sg * r[1];
+    }
+    P[(size_t)D.tau * 2 * KK + (size_t)o * K + i] = (T)Pv;
+    P[(size_t)D.tau * 2 * KK + KK + (size_t)o * K + i] = (T)Qv;
+  }
+}
+
+// near-field reaction quadrature nodes: W = w lr sigma / (4 pi lz_l), lz_l, lz_l'
+__global__ void k_near_nodes(Medium md, int l, int a, int ntypes, double umax, double wmax, double lmin,
+                             double *nodes, int nq) {
+  __shared__ double pu[MAXPANEL], pw[MAXPANEL];
+  __shared__ double gx[16], gw[16];
+  __shared__ int npan;
+  if (threadIdx.x == 0) {
+    gl16(gx, gw);
+    make_panels(umax, wmax, lmin, pu, pw, &npan);
+  }
+  __syncthreads();
+  const int tau = blockIdx.y;
+  int lp, b;
+  type_decode(tau, lp, b);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nq; j += gridDim.x * blockDim.x) {
+    double *o = nodes + ((size_t)tau * nq + j) * 4;
+    if (j >= npan * 16) { o[0] = o[1] = 0.0; o[2] = o[3] = 1.0; continue; }
+    const int pi_ = j >> 4, gi = j & 15;
+    const double lr = pu[pi_] + 0.5 * pw[pi_] * (gx[gi] + 1.0);
+    const double w = 0.5 * pw[pi_] * gw[gi];
+    const double lz = sqrt(md.lam[l] * md.lam[l] + lr * lr), lzp = sqrt(md.lam[lp] * md.lam[lp] + lr * lr);
+    o[0] = lr;
+    o[1] = w * lr * layer_sigma(md, lr, l, a, lp, b) / (4.0 * PI * lz);
+    o[2] = lz;
+    o[3] = lzp;
+  }
+}
+
+// number of panels of the graded rule (host mirror of make_panels)
+static int count_panels(double umax, double wmax, double lmin) {
+  int n = 0;
+  double u = 0.0;
+  while (u < umax && n < MAXPANEL) {
+    double w = fmin(wmax, 0.5 * (lmin + u));
+    if (u + w > umax) w = umax - u;
+    u += w;
+    ++n;
+  }
+  return n;
+}
+
+template <typename T>
+static void build_ops_t(Ctx &c, Group &g, int parts) {
+  const int p = c.p, K = c.K, L = c.md.L;
+  const size_t KK = (size_t)K * K;
+  const double lam_t = c.md.lam[g.l];
+  std::vector<OpDesc> descs;
+  size_t total = 0;
+  auto add = [&](int kind, int out_inv, int in_inv, double lam, double bx, double by, double bz, double xout,
+                 double xin, double pref, void **slot, size_t offset_in_slot) {
+    OpDesc d;
+    d.kind = kind; d.out_inv = out_inv; d.in_inv = in_inv; d.pad = 0;
+    d.lam = lam;
+    d.bnorm = sqrt(bx * bx + by * by + bz * bz);
+    d.cosb = bz / d.bnorm;
+    d.xout = xout; d.xin = xin; d.pref = pref;
+    d.dst = (int64_t)(total + offset_in_slot);
+    descs.push_back(d);
+    (void)slot;
+  };
+  // layout: per level a block with M2M (free + types), L2L, free M2L classes
+  struct Blk { size_t m2m_t, m2m_i, l2l, fm2l; };
+  std::vector<Blk> blk(DMAX + 1);
+  for (int l = 2; l <= g.D; ++l) {
+    const double h = g.h(l), hc = h, hp = 2.0 * h;
+    Blk b{};
+    // M2M: children at level l -> parents at l-1 (only l >= 3)
+    if (l >= 3) {
+      if (g.is_free && (parts & 1)) {
+        b.m2m_t = total;
+        for (int cz = 0; cz < 2; ++cz)
+          add(1, 1, 0, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hp, lam_t * hc, 1.0, nullptr,
+              (size_t)cz * 2 * KK);
+        total += 4 * KK;
+      }
+      if (parts & 2) {
+        b.m2m_i = total;
+        for (int t = 0; t < g.ntypes; ++t) {
+          int lp, bb;
+          type_decode(t, lp, bb);
+          const double la = c.md.lam[lp];
+          for (int cz = 0; cz < 2; ++cz)
+            add(1, 1, 0, la, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, la * hp, la * hc, 1.0, nullptr,
+                ((size_t)t * 2 + cz) * 2 * KK);
+        }
+        total += (size_t)g.ntypes * 4 * KK;
+      }
+      // L2L: parent (l-1) -> child at l
+      b.l2l = total;
+      for (int cz = 0; cz < 2; ++cz)
+        add(2, 0, 1, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hc, lam_t * hp, 1.0, nullptr,
+            (size_t)cz * 2 * KK);
+      total += 4 * KK;
+    }
+    if (g.is_free && (parts & 1)) {
+      b.fm2l = total;
+      const double rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+      const double pref = lam_t / (2.0 * PI * PI * c.md.eps[g.l]);
+      for (int ri = 0; ri < NRHO; ++ri)
+        for (int dz = -3; dz <= 3; ++dz) {
+          const int cls = ri * 7 + dz + 3;
+          const bool adjacent = rho2[ri] <= 2.0 && abs(dz) <= 1;
+          if (adjacent) continue;
+          // b = c_t - c_s = -(offset) h; azimuth factored out: b = (rho h, 0, -dz h)
+          add(0, 0, 0, lam_t, sqrt(rho2[ri]) * h, 0.0, -dz * h, lam_t * h, lam_t * h, pref, nullptr,
+              (size_t)cls * 2 * KK);
+        }
+      total += (size_t)NFREE_CLS * 2 * KK;
+    }
+    blk[l] = b;
+  }
+  T *ops = c.arena.get<T>(total);
+  for (int l = 2; l <= g.D; ++l) {
+    g.op_m2m_t[l] = (l >= 3 && g.is_free && (parts & 1)) ? (void *)(ops + blk[l].m2m_t) : nullptr;
+    g.op_m2m_i[l] = (l >= 3 && (parts & 2)) ? (void *)(ops + blk[l].m2m_i) : nullptr;
+    g.op_l2l[l] = (l >= 3) ? (void *)(ops + blk[l].l2l) : nullptr;
+    g.op_free[l] = (g.is_free && (parts & 1)) ? (void *)(ops + blk[l].fm2l) : nullptr;
+  }
+  if (!descs.empty()) {
+    OpDesc *dd = c.arena.get<OpDesc>(descs.size());
+    LPB_CUDA(cudaMemcpyAsync(dd, descs.data(), sizeof(OpDesc) * descs.size(), cudaMemcpyHostToDevice, c.stream));
+    k_build_ops<T><<<(unsigned)descs.size(), 256, 0, c.stream>>>(dd, p, K, c.gaunt, ops);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+  if (!(parts & 2) || !g.I.np) return;
+  // reaction: one descriptor per (level, type)
+  const int KT = 2 * p + 3, NS = p + 2;
+  const size_t TS = (size_t)(KT + 1) * (KT + 1) * 4;
+  std::vector<RDesc> rd;
+  const int st = (g.a == 1) ? -1 : 1;
+  for (int l = 2; l <= g.D; ++l) {
+    if (!g.vreact[l]) continue;
+    const double h = g.h(l);
+    g.stab[l] = c.arena.get<double>((size_t)NREACT_CLS * g.ntypes * TS);
+    g.op_react[l] = c.arena.get<T>((size_t)NREACT_CLS * g.ntypes * 2 * KK);
+    double *coef = c.arena.get<double>((size_t)g.ntypes * KK * NS);
+    for (int t = 0; t < g.ntypes; ++t) {
+      int lp, bb;
+      type_decode(t, lp, bb);
+      RDesc d;
+      d.l = g.l; d.a = g.a; d.lp = lp; d.b = bb; d.tau = t; d.ntypes = g.ntypes; d.st = st; d.pad = l;
+      d.h = h; d.Lam = c.md.lam[g.l] * h; d.Lamp = c.md.lam[lp] * h;
+      d.used = g.used[l];
+      d.stab = g.stab[l];
+      d.coef = coef + (size_t)t * KK * NS;
+      d.dst = 0;
+      rd.push_back(d);
+    }
+  }
+  if (!rd.empty()) {
+    RDesc *dr = c.arena.get<RDesc>(rd.size());
+    LPB_CUDA(cudaMemcpyAsync(dr, rd.data(), sizeof(RDesc) * rd.size(), cudaMemcpyHostToDevice, c.stream));
+    const unsigned nd = (unsigned)rd.size();
+    k_stab_quad<<<dim3(NREACT_CLS, nd), 256, 0, c.stream>>>(dr, c.md, KT, fmax(c.tol, 1e-16));
+    LPB_LAUNCH();
+    k_stab_recur<<<dim3(NREACT_CLS, nd), 32, 0, c.stream>>>(dr, KT);
+    LPB_LAUNCH();
+    k_react_coef<<<dim3((unsigned)((KK + 255) / 256), nd), 256, 0, c.stream>>>(dr, c.tpoly, c.tpk, p, K);
+    LPB_LAUNCH();
+    // assemble into each level's op array: descriptors grouped by level
+    size_t first = 0;
+    while (first < rd.size()) {
+      const int l = rd[first].pad;
+      size_t last = first;
+      while (last < rd.size() && rd[last].pad == l) ++last;
+      k_react_assemble<T><<<dim3(NREACT_CLS, (unsigned)(last - first)), 256, 0, c.stream>>>(
+          dr + first, p, K, KT, (T *)g.op_react[l]);
+      LPB_LAUNCH();
+      c.launches++;
+      first = last;
+    }
+    c.launches += 3;
+  }
+}
+
+void build_operators(Ctx &c, Group &g, int parts) {
+  if (c.opts.precision == LPBFMM_FP64) build_ops_t<double>(c, g, parts);
+  else build_ops_t<float>(c, g, parts);
+}
+
+void build_near_nodes(Ctx &c, Group &g, double zeta_min, double rho_max) {
+  const double lmin = fmin(c.md.lam[g.l], [&] {
+    double m = 1e300;
+    for (int k = 0; k <= c.md.L; ++k) m = fmin(m, c.md.lam[k]);
+    return m;
+  }());
+  const double umax = 36.0 / zeta_min;
+  const double wmax = fmin(2.0 / zeta_min, PI / fmax(rho_max, 1e-300));
+  g.nq = count_panels(umax, wmax, lmin) * 16;
+  g.nodes = c.arena.get<double>((size_t)g.ntypes * g.nq * 4);
+  k_near_nodes<<<dim3((unsigned)((g.nq + 255) / 256), g.ntypes), 256, 0, c.stream>>>(c.md, g.l, g.a, g.ntypes, umax,
+                                                                                     wmax, lmin, g.nodes, g.nq);
+  LPB_LAUNCH();
+  c.launches++;
+}
+
+void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
+                  double *out) {
+  // single class with the requested geometry: reuse the quadrature + recurrence kernels through a
+  // one-class descriptor (class index chosen from rho/h, zt/h - 1/2, zs/h - 1/2)
+  const double r2 = (rho / h) * (rho / h);
+  const double rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+  int ri = -1;
+  for (int k = 0; k < NRHO; ++k)
+    if (fabs(r2 - rho2[k]) < 1e-9) ri = k;
+  const int kt = (int)llround(zt / h - 0.5), ks = (int)llround(zs / h - 0.5);
+  const int kkt[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
+  if (ri < 0 || kt < 0 || ks < 0 || kt + ks > 2 || fabs(zt / h - 0.5 - kt) > 1e-9 || fabs(zs / h - 0.5 - ks) > 1e-9)
+    throw StatusError{LPBFMM_ERR_ARG};
+  const int cls = ri * NKK + kkt[kt][ks];
+  const int KT = Kmax;
+  const size_t TS = (size_t)(KT + 1) * (KT + 1) * 4;
+  double *stab = nullptr;
+  uint8_t *used = nullptr;
+  RDesc *dr = nullptr;
+  LPB_CUDA(cudaMalloc(&stab, sizeof(double) * NREACT_CLS * TS));
+  LPB_CUDA(cudaMalloc(&used, NREACT_CLS));
+  LPB_CUDA(cudaMalloc(&dr, sizeof(RDesc)));
+  LPB_CUDA(cudaMemsetAsync(stab, 0, sizeof(double) * NREACT_CLS * TS, c.stream));
+  std::vector<uint8_t> hu(NREACT_CLS, 0);
+  hu[cls] = 1;
+  LPB_CUDA(cudaMemcpyAsync(used, hu.data(), NREACT_CLS, cudaMemcpyHostToDevice, c.stream));
+  RDesc d;
+  d.l = l; d.a = a; d.lp = lp; d.b = b; d.tau = 0; d.ntypes = 1; d.st = a == 1 ? -1 : 1; d.pad = 0;
+  d.h = h; d.Lam = c.md.lam[l] * h; d.Lamp = c.md.lam[lp] * h;
+  d.used = used; d.stab = stab; d.coef = nullptr; d.dst = 0;
+  LPB_CUDA(cudaMemcpyAsync(dr, &d, sizeof(RDesc), cudaMemcpyHostToDevice, c.stream));
+  k_stab_quad<<<dim3(NREACT_CLS, 1), 256, 0, c.stream>>>(dr, c.md, KT, fmax(c.tol, 1e-16));
+  LPB_LAUNCH();
+  k_stab_recur<<<dim3(NREACT_CLS, 1), 32, 0, c.stream>>>(dr, KT);
+  LPB_LAUNCH();
+  std::vector<double> h_out(TS);
+  LPB_CUDA(cudaMemcpyAsync(h_out.data(), stab + (size_t)cls * TS, sizeof(double) * TS, cudaMemcpyDeviceToHost,
+                           c.stream));
+  LPB_CUDA(cudaStreamSynchronize(c.stream));
+  cudaFree(stab);
+  cudaFree(used);
+  cudaFree(dr);
+  // out[((K*(Kmax+1)) + d)*4 + ij] with ij = 2i + j
+  for (size_t e = 0; e < TS; ++e) out[e] = h_out[e];
+}
+
+}  // namespace lpb

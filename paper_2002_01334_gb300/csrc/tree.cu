@@ -1,0 +1,580 @@
+// Input validation, per-group octrees (Morton keys + radix sort) and interaction lists.
+// Tree rule (Sec. 3.5): the root cube of target group (l, a) is bisected by its interface
+// (d_l for a = 1, d_{l-1} for a = 2), so every box of level >= 1 has its centre on the
+// side of the points it holds; all trees here have uniform depth D.
+#include "internal.h"
+#include "prims.cuh"
+
+namespace lpb {
+
+// ---------------------------------------------------------------------------------------
+// scan / sort wrappers
+// ---------------------------------------------------------------------------------------
+void scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total) {
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  uint32_t *sums = c.arena.get<uint32_t>(tiles + 1);
+  if (n > 0) {
+    k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, c.stream>>>(in, out, sums, n);
+    LPB_LAUNCH();
+  }
+  k_scan_sums<<<1, 1024, 0, c.stream>>>(sums, tiles, d_total);
+  LPB_LAUNCH();
+  if (tiles > 1) {
+    k_scan_add<<<(unsigned)tiles, SCAN_THREADS, 0, c.stream>>>(out, sums, n);
+    LPB_LAUNCH();
+  }
+  c.launches += 2 + (tiles > 1) + (n > 0 ? 0 : -1);
+}
+
+void radix_sort(Ctx &c, uint64_t *&keys, uint32_t *&vals, int64_t n, int bits) {
+  if (n <= 1) return;
+  const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
+  uint64_t *k2 = c.arena.get<uint64_t>(n);
+  uint32_t *v2 = c.arena.get<uint32_t>(n);
+  uint32_t *hist = c.arena.get<uint32_t>((size_t)256 * nblocks);
+  uint32_t *offs = c.arena.get<uint32_t>((size_t)256 * nblocks);
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_hist<<<nblocks, RS_THREADS, 0, c.stream>>>(keys, n, shift, hist, nblocks);
+    LPB_LAUNCH();
+    scan_u32(c, hist, offs, (int64_t)256 * nblocks, nullptr);
+    k_radix_scatter<<<nblocks, RS_THREADS, 0, c.stream>>>(keys, vals, k2, v2, n, shift, offs, nblocks);
+    LPB_LAUNCH();
+    c.launches += 2;
+    uint64_t *tk = keys; keys = k2; k2 = tk;
+    uint32_t *tv = vals; vals = v2; v2 = tv;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// validation: finite, off the interfaces, layer_id consistent with z; counts and extents
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ unsigned long long wmin(unsigned long long v) {
+  for (int o = 16; o; o >>= 1) { unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o); v = w < v ? w : v; }
+  return v;
+}
+__device__ __forceinline__ unsigned long long wmax(unsigned long long v) {
+  for (int o = 16; o; o >>= 1) { unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o); v = w > v ? w : v; }
+  return v;
+}
+
+__global__ void k_validate(int64_t n, const double *q, const double *xyz, const int32_t *layer, Medium md,
+                           double thr, Stats *st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  bool ok = false;
+  int lay = -1;
+  double x = 0, y = 0, z = 0;
+  if (i < n) {
+    x = xyz[3 * i]; y = xyz[3 * i + 1]; z = xyz[3 * i + 2];
+    const double qq = q[i];
+    lay = layer[i];
+    int code = 0;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qq)) {
+      code = LPBFMM_ERR_NONFINITE;
+    } else {
+      int l = 0;
+      while (l < md.L && z < md.d[l]) ++l;
+      for (int k = 0; k < md.L; ++k)
+        if (fabs(z - md.d[k]) < thr) code = LPBFMM_ERR_ON_INTERFACE;
+      if (!code && l != lay) code = LPBFMM_ERR_LAYER_MISMATCH;
+    }
+    if (code) atomicCAS(&st->status, 0, code);
+    ok = (code == 0);
+  }
+  const unsigned long long HI = ~0ull, LO = 0ull;
+  unsigned long long v;
+  v = wmin(ok ? ord_of(x) : HI); if (lane == 0 && v != HI) atomicMin(&st->xlo, v);
+  v = wmax(ok ? ord_of(x) : LO); if (lane == 0 && v != LO) atomicMax(&st->xhi, v);
+  v = wmin(ok ? ord_of(y) : HI); if (lane == 0 && v != HI) atomicMin(&st->ylo, v);
+  v = wmax(ok ? ord_of(y) : LO); if (lane == 0 && v != LO) atomicMax(&st->yhi, v);
+  for (int k = 0; k <= md.L; ++k) {
+    const bool in = ok && lay == k;
+    const unsigned cntk = __popc(__ballot_sync(0xffffffffu, in));
+    if (lane == 0 && cntk) atomicAdd(&st->cnt[k], (unsigned long long)cntk);
+    v = wmin(in ? ord_of(z) : HI); if (lane == 0 && v != HI) atomicMin(&st->zlo[k], v);
+    v = wmax(in ? ord_of(z) : LO); if (lane == 0 && v != LO) atomicMax(&st->zhi[k], v);
+  }
+}
+
+void launch_validate(Ctx &c, int64_t n, const double *q, const double *xyz, const int32_t *layer, Stats *st) {
+  double scale = 1.0;
+  for (int k = 0; k < c.md.L; ++k) scale = fmax(scale, fabs(c.md.d[k]));
+  const double thr = 1e-12 * scale;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  k_validate<<<blocks, 256, 0, c.stream>>>(n, q, xyz, layer, c.md, thr, st);
+  LPB_LAUNCH();
+  c.launches++;
+}
+
+__global__ void k_flag_layer(int64_t n, const int32_t *layer, int lay, uint32_t *f) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = layer[i] == lay ? 1u : 0u;
+}
+void layer_rank(Ctx &c, int64_t n, const int32_t *layer, int lay, uint32_t *rank) {
+  uint32_t *f = c.arena.get<uint32_t>(n);
+  k_flag_layer<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, layer, lay, f);
+  LPB_LAUNCH();
+  c.launches++;
+  scan_u32(c, f, rank, n, nullptr);
+}
+
+// ---------------------------------------------------------------------------------------
+// points and Morton keys
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x3ffu;  // 10 bits
+  x = (x | (x << 16)) & 0x30000ffull;
+  x = (x | (x << 8)) & 0x300f00full;
+  x = (x | (x << 4)) & 0x30c30c3ull;
+  x = (x | (x << 2)) & 0x9249249ull;
+  return x;
+}
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x9249249ull;
+  x = (x ^ (x >> 2)) & 0x30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x300f00full;
+  x = (x ^ (x >> 8)) & 0x30000ffull;
+  x = (x ^ (x >> 16)) & 0x3ffull;
+  return (uint32_t)x;
+}
+// cell index i = floor((x - x0) * s) clamped to [0, 2^DMAX - 1]; rounded ops, no contraction
+__device__ __forceinline__ uint32_t cell_of(double x, double x0, double s) {
+  double t = floor(__dmul_rn(__dsub_rn(x, x0), s));
+  t = fmin(fmax(t, 0.0), double((1 << DMAX) - 1));
+  return (uint32_t)t;
+}
+__device__ __forceinline__ uint64_t morton_of(double x, double y, double z, const double *o, double s) {
+  return (spread3(cell_of(x, o[0], s)) << 2) | (spread3(cell_of(y, o[1], s)) << 1) | spread3(cell_of(z, o[2], s));
+}
+
+struct RankPtrs {
+  uint32_t *r[MAXLAYER];
+};
+struct GroupGeom {
+  double o[3];  // lower corner of the root cube
+  double s;     // 2^DMAX / (2H)
+  int l, a;
+  int64_t type_off[2 * MAXLAYER];
+};
+
+__global__ void k_make_targets(int64_t n, const double *xyz, const int32_t *layer, RankPtrs rk, GroupGeom gg,
+                               uint64_t *key, uint32_t *src) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || layer[i] != gg.l) return;
+  const uint32_t pos = rk.r[gg.l][i];
+  key[pos] = morton_of(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], gg.o, gg.s) << 4;
+  src[pos] = (uint32_t)i;
+}
+
+__global__ void k_make_images(int64_t n, const double *xyz, const int32_t *layer, Medium md, RankPtrs rk,
+                              GroupGeom gg, int D, uint64_t *key, uint32_t *src) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int lp = layer[i];
+  for (int b = 1; b <= 2; ++b) {
+    if ((b == 1 && lp == md.L) || (b == 2 && lp == 0)) continue;
+    const int t = type_index(lp, b);
+    const int64_t pos = gg.type_off[t] + rk.r[lp][i];
+    const double zi = image_z(md, gg.l, gg.a, lp, b, xyz[3 * i + 2]);
+    key[pos] = ((morton_of(xyz[3 * i], xyz[3 * i + 1], zi, gg.o, gg.s) >> (3 * (DMAX - D))) << 4) | (uint64_t)t;
+    src[pos] = (uint32_t)i;
+  }
+}
+
+__global__ void k_gather_points(int64_t np, const uint64_t *key, const uint32_t *src, const double *q,
+                                const double *xyz, Medium md, int l, int a, int images, double *x, double *y,
+                                double *z, double *qq, const int32_t *layer) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const uint32_t i = src[k];
+  x[k] = xyz[3 * i];
+  y[k] = xyz[3 * i + 1];
+  if (images) {
+    int lp, b;
+    type_decode((int)(key[k] & 15ull), lp, b);
+    z[k] = image_z(md, l, a, lp, b, xyz[3 * i + 2]);
+  } else {
+    z[k] = xyz[3 * i + 2];
+  }
+  qq[k] = q[i];
+}
+
+static GroupGeom group_geom(Ctx &c, const Group &g, const int64_t *cnt) {
+  GroupGeom gg;
+  const double H = g.root[3];
+  gg.o[0] = g.root[0] - H;
+  gg.o[1] = g.root[1] - H;
+  gg.o[2] = g.root[2] - H;
+  gg.s = double(1 << DMAX) / (2.0 * H);
+  gg.l = g.l;
+  gg.a = g.a;
+  int64_t off = 0;
+  for (int t = 0; t < 2 * c.md.L; ++t) {
+    int lp, b;
+    type_decode(t, lp, b);
+    gg.type_off[t] = off;
+    off += cnt[lp];
+  }
+  return gg;
+}
+
+static void gather(Ctx &c, Group &g, PointSet &P, int images, const double *q, const double *xyz,
+                   const int32_t *layer) {
+  P.x = c.arena.get<double>(P.np);
+  P.y = c.arena.get<double>(P.np);
+  P.z = c.arena.get<double>(P.np);
+  P.q = c.arena.get<double>(P.np);
+  if (P.np) {
+    k_gather_points<<<(unsigned)((P.np + 255) / 256), 256, 0, c.stream>>>(P.np, P.key, P.src, q, xyz, c.md, g.l,
+                                                                          g.a, images, P.x, P.y, P.z, P.q, layer);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+}
+
+// targets of the group, sorted by their depth-DMAX Morton keys (every coarser key is a prefix)
+void build_group_targets(Ctx &c, Group &g, int64_t n, const double *q, const double *xyz, const int32_t *layer,
+                         uint32_t *const *rank, const int64_t *cnt) {
+  GroupGeom gg = group_geom(c, g, cnt);
+  RankPtrs rk;
+  for (int k = 0; k <= c.md.L; ++k) rk.r[k] = rank[k];
+  g.T.np = cnt[g.l];
+  g.T.key = c.arena.get<uint64_t>(g.T.np);
+  g.T.src = c.arena.get<uint32_t>(g.T.np);
+  k_make_targets<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, xyz, layer, rk, gg, g.T.key, g.T.src);
+  LPB_LAUNCH();
+  c.launches++;
+  radix_sort(c, g.T.key, g.T.src, g.T.np, DMAX * 3 + 4);
+  gather(c, g, g.T, 0, q, xyz, layer);
+}
+
+// images of the group, sorted by (depth-D leaf key, type, input order): every (leaf box,
+// type) pair is one contiguous run
+void build_group_images(Ctx &c, Group &g, int64_t n, const double *q, const double *xyz, const int32_t *layer,
+                        uint32_t *const *rank, const int64_t *cnt) {
+  GroupGeom gg = group_geom(c, g, cnt);
+  RankPtrs rk;
+  for (int k = 0; k <= c.md.L; ++k) rk.r[k] = rank[k];
+  int64_t tot = 0;
+  for (int t = 0; t < 2 * c.md.L; ++t) {
+    int lp, b;
+    type_decode(t, lp, b);
+    tot += cnt[lp];
+  }
+  g.I.np = tot;
+  g.I.key = c.arena.get<uint64_t>(g.I.np);
+  g.I.src = c.arena.get<uint32_t>(g.I.np);
+  k_make_images<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, xyz, layer, c.md, rk, gg, g.D, g.I.key,
+                                                                   g.I.src);
+  LPB_LAUNCH();
+  c.launches++;
+  radix_sort(c, g.I.key, g.I.src, g.I.np, g.D * 3 + 4);
+  gather(c, g, g.I, 1, q, xyz, layer);
+}
+
+// number of non-empty target boxes at every level 2..DMAX (automatic depth rule)
+__global__ void k_count_levels(int64_t np, const uint64_t *key, uint32_t *cnt) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int l = 2; l <= DMAX; ++l) {
+    bool f = false;
+    if (k < np) {
+      const int sh = 4 + 3 * (DMAX - l);
+      f = (k == 0) || ((key[k] >> sh) != (key[k - 1] >> sh));
+    }
+    const unsigned b = __popc(__ballot_sync(0xffffffffu, f));
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt[l], b);
+  }
+}
+void count_levels(Ctx &c, Group &g, uint32_t *d_counts) {
+  if (!g.T.np) return;
+  k_count_levels<<<(unsigned)((g.T.np + 255) / 256), 256, 0, c.stream>>>(g.T.np, g.T.key, d_counts);
+  LPB_LAUNCH();
+  c.launches++;
+}
+
+// ---------------------------------------------------------------------------------------
+// boxes per level
+// ---------------------------------------------------------------------------------------
+__global__ void k_leaf_flags(int64_t np, const uint64_t *key, int sh, uint32_t *f) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < np) f[k] = (k == 0 || (key[k] >> sh) != (key[k - 1] >> sh)) ? 1u : 0u;
+}
+__global__ void k_seg_flags(int64_t np, const uint64_t *key, int sh, uint32_t *f) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const uint64_t a = ((key[k] >> 4) >> sh << 4) | (key[k] & 15ull);
+  const uint64_t b = k ? (((key[k - 1] >> 4) >> sh << 4) | (key[k - 1] & 15ull)) : 0ull;
+  f[k] = (k == 0 || a != b) ? 1u : 0u;
+}
+// flagged item k starts box idx[k]
+__global__ void k_leaf_boxes(int64_t np, const uint64_t *key, int sh, const uint32_t *f, const uint32_t *idx,
+                             uint64_t *bkey, uint32_t *bstart) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < np && f[k]) {
+    bkey[idx[k]] = key[k] >> sh;
+    bstart[idx[k]] = (uint32_t)k;
+  }
+}
+__global__ void k_counts_from_starts(const uint32_t *d_n, const uint32_t *start, uint32_t total, uint32_t *cnt,
+                                     int64_t cap) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = *d_n;
+  if (b < n && b < cap) cnt[b] = ((b + 1 < n) ? start[b + 1] : total) - start[b];
+}
+__global__ void k_seg_fill(int64_t np, const uint64_t *key, const uint32_t *f, const uint32_t *sidx,
+                           const uint32_t *bf, const uint32_t *bidx, uint32_t *sstart, uint32_t *sbox,
+                           uint32_t *stype) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < np && f[k]) {
+    const uint32_t s = sidx[k];
+    sstart[s] = (uint32_t)k;
+    sbox[s] = bidx[k] + bf[k] - 1u;
+    stype[s] = (uint32_t)(key[k] & 15ull);
+  }
+}
+// parents of level l+1 boxes
+__global__ void k_parent_flags(const uint32_t *d_n, const uint64_t *ckey, uint32_t *f, int64_t cap) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = *d_n;
+  if (j < n && j < cap) f[j] = (j == 0 || (ckey[j] >> 3) != (ckey[j - 1] >> 3)) ? 1u : 0u;
+  else if (j < cap) f[j] = 0u;
+}
+__global__ void k_parent_fill(const uint32_t *d_n, const uint64_t *ckey, const uint32_t *f, const uint32_t *idx,
+                              uint32_t *cparent, uint64_t *pkey, uint32_t *pstart, int64_t cap) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = *d_n;
+  if (j >= n || j >= cap) return;
+  const uint32_t pid = idx[j] + f[j] - 1u;
+  cparent[j] = pid;
+  if (f[j]) {
+    pkey[pid] = ckey[j] >> 3;
+    pstart[pid] = (uint32_t)j;
+  }
+}
+
+static int64_t level_cap(int64_t np, int l) {
+  int64_t c = 1;
+  for (int k = 0; k < l && c < np; ++k) c *= 8;
+  return c < np ? c : np;
+}
+
+static void build_levels(Ctx &c, PointSet &P, int D, bool images) {
+  const int64_t np = P.np;
+  const unsigned pb = (unsigned)((np + 255) / 256);
+  for (int l = 0; l <= DMAX; ++l) P.lev[l] = Level();
+  if (!np) return;
+  // targets carry depth-DMAX keys, images depth-D keys (both shifted by 4 type bits)
+  const int sh = images ? 4 : 4 + 3 * (DMAX - D);
+  uint32_t *f = c.arena.get<uint32_t>(np), *idx = c.arena.get<uint32_t>(np);
+  Level &Lf = P.lev[D];
+  const int64_t capD = level_cap(np, D);
+  Lf.key = c.arena.get<uint64_t>(capD);
+  Lf.start = c.arena.get<uint32_t>(capD);
+  Lf.count = c.arena.get<uint32_t>(capD);
+  Lf.d_n = c.arena.get<uint32_t>(1);
+  k_leaf_flags<<<pb, 256, 0, c.stream>>>(np, P.key, sh, f);
+  LPB_LAUNCH();
+  scan_u32(c, f, idx, np, Lf.d_n);
+  k_leaf_boxes<<<pb, 256, 0, c.stream>>>(np, P.key, sh, f, idx, Lf.key, Lf.start);
+  LPB_LAUNCH();
+  k_counts_from_starts<<<(unsigned)((capD + 255) / 256), 256, 0, c.stream>>>(Lf.d_n, Lf.start, (uint32_t)np,
+                                                                              Lf.count, capD);
+  LPB_LAUNCH();
+  c.launches += 3;
+  if (images) {
+    uint32_t *sf = c.arena.get<uint32_t>(np), *sidx = c.arena.get<uint32_t>(np);
+    P.seg_start = c.arena.get<uint32_t>(np);
+    P.seg_count = c.arena.get<uint32_t>(np);
+    P.seg_box = c.arena.get<uint32_t>(np);
+    P.seg_type = c.arena.get<uint32_t>(np);
+    P.d_nseg = c.arena.get<uint32_t>(1);
+    k_seg_flags<<<pb, 256, 0, c.stream>>>(np, P.key, 0, sf);
+    LPB_LAUNCH();
+    scan_u32(c, sf, sidx, np, P.d_nseg);
+    k_seg_fill<<<pb, 256, 0, c.stream>>>(np, P.key, sf, sidx, f, idx, P.seg_start, P.seg_box, P.seg_type);
+    LPB_LAUNCH();
+    k_counts_from_starts<<<pb, 256, 0, c.stream>>>(P.d_nseg, P.seg_start, (uint32_t)np, P.seg_count, np);
+    LPB_LAUNCH();
+    c.launches += 3;
+  }
+  for (int l = D - 1; l >= 2; --l) {
+    Level &C = P.lev[l + 1], &Pa = P.lev[l];
+    const int64_t ccap = level_cap(np, l + 1), pcap = level_cap(np, l);
+    uint32_t *cf = c.arena.get<uint32_t>(ccap), *cidx = c.arena.get<uint32_t>(ccap);
+    Pa.key = c.arena.get<uint64_t>(pcap);
+    Pa.start = c.arena.get<uint32_t>(pcap);
+    Pa.count = c.arena.get<uint32_t>(pcap);
+    Pa.d_n = c.arena.get<uint32_t>(1);
+    C.parent = c.arena.get<uint32_t>(ccap);
+    const unsigned cb = (unsigned)((ccap + 255) / 256);
+    k_parent_flags<<<cb, 256, 0, c.stream>>>(C.d_n, C.key, cf, ccap);
+    LPB_LAUNCH();
+    scan_u32(c, cf, cidx, ccap, Pa.d_n);
+    k_parent_fill<<<cb, 256, 0, c.stream>>>(C.d_n, C.key, cf, cidx, C.parent, Pa.key, Pa.start, ccap);
+    LPB_LAUNCH();
+    k_counts_from_starts<<<(unsigned)((pcap + 255) / 256), 256, 0, c.stream>>>(Pa.d_n, Pa.start, 0u, Pa.count,
+                                                                                pcap);
+    LPB_LAUNCH();
+    c.launches += 3;
+  }
+}
+
+__global__ void k_fix_last_count(const uint32_t *d_nc, const uint32_t *d_np, const uint32_t *pstart,
+                                 uint32_t *pcount) {
+  // the last parent's count is (number of children) - start
+  const uint32_t np = *d_np;
+  if (np) pcount[np - 1] = *d_nc - pstart[np - 1];
+}
+
+void build_group_boxes(Ctx &c, Group &g) {
+  build_levels(c, g.T, g.D, false);
+  build_levels(c, g.I, g.D, true);
+  for (int which = 0; which < 2; ++which) {
+    PointSet &P = which ? g.I : g.T;
+    if (!P.np) continue;
+    for (int l = g.D - 1; l >= 2; --l) {
+      k_fix_last_count<<<1, 1, 0, c.stream>>>(P.lev[l + 1].d_n, P.lev[l].d_n, P.lev[l].start, P.lev[l].count);
+      LPB_LAUNCH();
+      c.launches++;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// interaction lists.  Far list (multipole-to-local, V): source boxes at offset d with
+// |d|_inf >= 2 whose parent neighbours the target's parent.  Near list (U): |d|_inf <= 1.
+// Dense layout: [target box][offset slot] -> source box index or -1.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int rho_index(int dx, int dy) {
+  const int r2 = dx * dx + dy * dy;
+  switch (r2) {
+    case 0: return 0; case 1: return 1; case 2: return 2; case 4: return 3; case 5: return 4;
+    case 8: return 5; case 9: return 6; case 10: return 7; case 13: return 8; case 18: return 9;
+  }
+  return -1;
+}
+__device__ __forceinline__ int kk_index(int kt, int ks) {
+  if (kt < 0 || ks < 0 || kt + ks > 2) return -1;
+  const int tab[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
+  return tab[kt][ks];
+}
+__device__ __forceinline__ int64_t find_key(const uint64_t *keys, int64_t n, uint64_t k) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    const int64_t m = (lo + hi) >> 1;
+    const uint64_t v = keys[m];
+    if (v == k) return m;
+    if (v < k) lo = m + 1; else hi = m - 1;
+  }
+  return -1;
+}
+
+// far = 1: V list over 343 slots; far = 0: near list over 27 slots
+// react: reaction list (targets vs images): also records used classes and the target row k_t
+__global__ void k_lists(const uint64_t *tkey, const uint32_t *d_nt, const uint64_t *skey, const uint32_t *d_ns,
+                        int lev, int far, int react, int a, int32_t *out, uint8_t *used) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nslot = far ? NOFF : NNEAR;
+  const int64_t t = gid / nslot;
+  const int o = (int)(gid % nslot);
+  const int64_t nt = *d_nt;
+  if (t >= nt) return;
+  int dx, dy, dz;
+  if (far) { dx = o / 49 - 3; dy = (o / 7) % 7 - 3; dz = o % 7 - 3; }
+  else { dx = o / 9 - 1; dy = (o / 3) % 3 - 1; dz = o % 3 - 1; }
+  const uint64_t k = tkey[t];
+  const int ix = compact3(k >> 2), iy = compact3(k >> 1), iz = compact3(k);
+  const int jx = ix + dx, jy = iy + dy, jz = iz + dz, nc = 1 << lev;
+  int32_t res = -1;
+  const int cheb = max(abs(dx), max(abs(dy), abs(dz)));
+  bool ok = jx >= 0 && jy >= 0 && jz >= 0 && jx < nc && jy < nc && jz < nc;
+  if (far) {
+    ok = ok && cheb >= 2 && abs((jx >> 1) - (ix >> 1)) <= 1 && abs((jy >> 1) - (iy >> 1)) <= 1 &&
+         abs((jz >> 1) - (iz >> 1)) <= 1;
+  }
+  const int64_t ns = *d_ns;
+  if (ok && ns > 0) {
+    const uint64_t sk = (spread3(jx) << 2) | (spread3(jy) << 1) | spread3(jz);
+    const int64_t s = find_key(skey, ns, sk);
+    if (s >= 0) {
+      res = (int32_t)s;
+      if (react && far && used) {
+        const int half = 1 << (lev - 1);
+        const int kt = (a == 1) ? iz - half : half - 1 - iz;
+        const int ks = (a == 1) ? half - 1 - jz : jz - half;
+        const int kk = kk_index(kt, ks);
+        if (kk >= 0) used[rho_index(dx, dy) * NKK + kk] = 1;
+      }
+    }
+  }
+  out[t * nslot + o] = res;
+}
+
+__global__ void k_rows(const uint64_t *tkey, const uint32_t *d_nt, int lev, int a, int32_t *rows, uint32_t *nrows,
+                       int32_t *ktrow, int64_t cap) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *d_nt) return;
+  const int iz = compact3(tkey[t]);
+  const int half = 1 << (lev - 1);
+  const int kt = (a == 1) ? iz - half : half - 1 - iz;
+  ktrow[t] = kt;
+  if (kt >= 0 && kt <= 2) {
+    const uint32_t pos = atomicAdd(&nrows[kt], 1u);
+    rows[kt * cap + pos] = (int32_t)t;
+  }
+}
+
+void build_group_lists(Ctx &c, Group &g, int parts) {
+  for (int l = 2; l <= g.D; ++l) {
+    const Level &T = g.T.lev[l];
+    const Level &I = g.I.lev[l];
+    const int64_t nt = T.n;
+    if (!nt) continue;
+    const unsigned fb = (unsigned)((nt * NOFF + 255) / 256);
+    if (g.is_free && (parts & 1)) {
+      g.vfree[l] = c.arena.get<int32_t>(nt * NOFF);
+      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, T.key, T.d_n, l, 1, 0, g.a, g.vfree[l], nullptr);
+      LPB_LAUNCH();
+      c.launches++;
+    }
+    if ((parts & 2) && I.n) {
+      g.vreact[l] = c.arena.get<int32_t>(nt * NOFF);
+      g.used[l] = c.arena.get<uint8_t>(NREACT_CLS);
+      LPB_CUDA(cudaMemsetAsync(g.used[l], 0, NREACT_CLS, c.stream));
+      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, I.key, I.d_n, l, 1, 1, g.a, g.vreact[l], g.used[l]);
+      LPB_LAUNCH();
+      g.rows[l] = c.arena.get<int32_t>(3 * nt);
+      g.nrows[l] = c.arena.get<uint32_t>(3);
+      g.ktrow[l] = c.arena.get<int32_t>(nt);
+      LPB_CUDA(cudaMemsetAsync(g.nrows[l], 0, 3 * sizeof(uint32_t), c.stream));
+      k_rows<<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(T.key, T.d_n, l, g.a, g.rows[l], g.nrows[l],
+                                                                 g.ktrow[l], nt);
+      LPB_LAUNCH();
+      c.launches += 2;
+    }
+  }
+  const int D = g.D;
+  const int64_t nt = g.T.lev[D].n;
+  if (!nt) return;
+  const unsigned nb = (unsigned)((nt * NNEAR + 255) / 256);
+  if (g.is_free && (parts & 1)) {
+    g.ufree = c.arena.get<int32_t>(nt * NNEAR);
+    k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].d_n, D, 0, 0,
+                                      g.a, g.ufree, nullptr);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+  if ((parts & 2) && g.I.lev[D].n) {
+    g.ureact = c.arena.get<int32_t>(nt * NNEAR);
+    k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.I.lev[D].key, g.I.lev[D].d_n, D, 0, 1,
+                                      g.a, g.ureact, nullptr);
+    LPB_LAUNCH();
+    c.launches++;
+  }
+}
+
+}  // namespace lpb

@@ -1,0 +1,227 @@
+"""Thin Python binding of liblpbfmm.so (ctypes; argument marshalling only).
+
+Every step of the computation runs in the library's CUDA kernels; this module only passes
+device pointers of torch tensors.  If the library has not been built it raises: there is no
+CPU fallback.  Build with ``python -m paper_2002_01334_gb300.build``.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblpbfmm.so")
+_lib = None
+
+FP64 = 0
+MIXED = 1
+STATUS = {
+    0: "ok", 1: "invalid argument", 2: "invalid medium", 3: "truncation order out of range",
+    4: "charge on an interface", 5: "layer_id does not match z", 6: "non-finite input",
+    7: "out of device memory", 8: "CUDA error", 9: "device wait timed out", 10: "unsupported size",
+}
+
+
+class LpbfmmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (where, STATUS.get(code, "unknown"), code))
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_per_leaf", C.c_int), ("uniform_depth", C.c_int),
+                ("reserved", C.c_int), ("stream", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblpbfmm.so is not built (expected at %s); run "
+                               "`python -m paper_2002_01334_gb300.build`" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+        L.lpbfmm_default_opts.argtypes = [C.POINTER(Opts)]
+        L.lpbfmm_create.argtypes = [C.c_int, dp, dp, dp, C.c_int, C.c_double, C.POINTER(Opts), C.POINTER(vp)]
+        L.lpbfmm_eval.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.lpbfmm_eval_parts.argtypes = [vp, i64, vp, vp, vp, C.c_int, vp, vp]
+        L.lpbfmm_adjoint.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        L.lpbfmm_eval_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(i64), vp, vp, vp, vp, vp]
+        L.lpbfmm_debug_tree.argtypes = [vp, C.c_int, C.c_int, dp, C.POINTER(i64), C.POINTER(i64),
+                                        C.POINTER(C.c_int), vp, vp, vp, vp, vp]
+        L.lpbfmm_debug_lists.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(i64),
+                                         C.POINTER(i64), vp, vp]
+        L.lpbfmm_debug_stable.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, C.c_int, dp]
+        L.lpbfmm_debug_array.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, C.c_int, vp, i64, C.POINTER(i64)]
+        L.lpbfmm_status.argtypes = [vp]
+        L.lpbfmm_strerror.argtypes = [C.c_int]
+        L.lpbfmm_strerror.restype = C.c_char_p
+        L.lpbfmm_destroy.argtypes = [vp]
+        L.lpbfmm_destroy.restype = None
+        L.lpbfmm_last_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_float),
+                                          C.POINTER(C.c_int)]
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc:
+        raise LpbfmmError(rc, where)
+
+
+def _dptr(t, dtype):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA %s tensor" % dtype)
+    return C.c_void_p(t.data_ptr())
+
+
+def _darr(vals):
+    a = (C.c_double * len(vals))(*[float(v) for v in vals])
+    return a
+
+
+class Context:
+    """One medium (interfaces d, eps, lambda per layer) and truncation order p (lpbfmm_create)."""
+
+    def __init__(self, d, eps, lam, p, tol=1e-14, precision=FP64, max_per_leaf=128, uniform_depth=0,
+                 stream=None):
+        L = lib()
+        o = Opts()
+        L.lpbfmm_default_opts(C.byref(o))
+        o.precision = int(precision)
+        o.max_per_leaf = int(max_per_leaf)
+        o.uniform_depth = int(uniform_depth or 0)
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        o.stream = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+        self.stream = stream
+        h = C.c_void_p()
+        self.d, self.eps, self.lam, self.p = list(d), list(eps), list(lam), int(p)
+        _check(L.lpbfmm_create(len(self.d), _darr(self.d), _darr(self.eps), _darr(self.lam), self.p, float(tol),
+                               C.byref(o), C.byref(h)), "lpbfmm_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().lpbfmm_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, q, xyz, layer, field=True, parts=3, out=None):
+        """phi[n] and field[n,3] (float64 CUDA tensors) for float64 q[n], xyz[n,3], int32 layer[n]."""
+        n = q.shape[0]
+        if out is None:
+            phi = torch.empty(n, dtype=torch.float64, device=q.device)
+            fld = torch.empty((n, 3), dtype=torch.float64, device=q.device) if field else None
+        else:
+            phi, fld = out
+        rc = lib().lpbfmm_eval_parts(self.h, n, _dptr(q, torch.float64), _dptr(xyz, torch.float64),
+                                     _dptr(layer, torch.int32), int(parts), _dptr(phi, torch.float64),
+                                     _dptr(fld, torch.float64) if fld is not None else None)
+        _check(rc, "lpbfmm_eval")
+        return phi, fld
+
+    def adjoint(self, q, xyz, layer, g_phi):
+        n = q.shape[0]
+        gq = torch.empty(n, dtype=torch.float64, device=q.device)
+        gx = torch.empty((n, 3), dtype=torch.float64, device=q.device)
+        rc = lib().lpbfmm_adjoint(self.h, n, _dptr(q, torch.float64), _dptr(xyz, torch.float64),
+                                  _dptr(layer, torch.int32), _dptr(g_phi, torch.float64),
+                                  _dptr(gq, torch.float64), _dptr(gx, torch.float64))
+        _check(rc, "lpbfmm_adjoint")
+        return gq, gx
+
+    def profile(self):
+        cap = 64
+        names = (C.c_char_p * cap)()
+        ms = (C.c_float * cap)()
+        lc = (C.c_int * cap)()
+        k = lib().lpbfmm_last_profile(self.h, cap, names, ms, lc)
+        return [(names[i].decode(), ms[i], lc[i]) for i in range(max(k, 0))]
+
+    # ---- diagnostics used by the tests ------------------------------------------------------
+    def debug_tree(self, l, a):
+        import numpy as np
+        root = (C.c_double * 4)()
+        nt, ni, D = C.c_int64(), C.c_int64(), C.c_int()
+        _check(lib().lpbfmm_debug_tree(self.h, l, a, root, C.byref(nt), C.byref(ni), C.byref(D), None, None,
+                                       None, None, None), "lpbfmm_debug_tree")
+        kt = np.zeros(nt.value, np.uint64)
+        st = np.zeros(nt.value, np.int64)
+        ki = np.zeros(ni.value, np.uint64)
+        si = np.zeros(ni.value, np.int64)
+        ti = np.zeros(ni.value, np.int32)
+        p = lambda a: C.c_void_p(a.ctypes.data)
+        _check(lib().lpbfmm_debug_tree(self.h, l, a, root, C.byref(nt), C.byref(ni), C.byref(D), p(kt), p(st),
+                                       p(ki), p(si), p(ti)), "lpbfmm_debug_tree")
+        return dict(root=list(root), depth=D.value, keys_t=kt, src_t=st, keys_i=ki, src_i=si, type_i=ti)
+
+    def debug_lists(self, l, a, lev, kind, src):
+        import numpy as np
+        nb, ne = C.c_int64(), C.c_int64()
+        _check(lib().lpbfmm_debug_lists(self.h, l, a, lev, kind, src, C.byref(nb), C.byref(ne), None, None),
+               "lpbfmm_debug_lists")
+        off = np.zeros(nb.value + 1, np.int64)
+        idx = np.zeros(max(ne.value, 1), np.int64)
+        _check(lib().lpbfmm_debug_lists(self.h, l, a, lev, kind, src, C.byref(nb), C.byref(ne),
+                                        C.c_void_p(off.ctypes.data), C.c_void_p(idx.ctypes.data)),
+               "lpbfmm_debug_lists")
+        return off, idx[:ne.value]
+
+    def debug_array(self, l, a, name, lev, dtype):
+        import numpy as np
+        nb = C.c_int64()
+        _check(lib().lpbfmm_debug_array(self.h, l, a, name.encode(), lev, None, 0, C.byref(nb)), "debug_array")
+        out = np.zeros(nb.value, np.uint8)
+        _check(lib().lpbfmm_debug_array(self.h, l, a, name.encode(), lev, C.c_void_p(out.ctypes.data), nb.value,
+                                        C.byref(nb)), "debug_array")
+        return out.view(dtype)
+
+    def debug_stable(self, l, a, lp, b, h, rho, zt, zs, Kmax):
+        import numpy as np
+        out = np.zeros((Kmax + 1) * (Kmax + 1) * 4)
+        _check(lib().lpbfmm_debug_stable(self.h, l, a, lp, b, float(h), float(rho), float(zt), float(zs), Kmax,
+                                         out.ctypes.data_as(C.POINTER(C.c_double))), "lpbfmm_debug_stable")
+        return out.reshape(Kmax + 1, Kmax + 1, 2, 2)
+
+
+def eval_batched(ctxs, offsets, q, xyz, layer, field=True):
+    n = q.shape[0]
+    phi = torch.empty(n, dtype=torch.float64, device=q.device)
+    fld = torch.empty((n, 3), dtype=torch.float64, device=q.device) if field else None
+    hs = (C.c_void_p * len(ctxs))(*[c.h.value for c in ctxs])
+    offs = (C.c_int64 * len(offsets))(*[int(o) for o in offsets])
+    rc = lib().lpbfmm_eval_batched(len(ctxs), hs, offs, _dptr(q, torch.float64), _dptr(xyz, torch.float64),
+                                   _dptr(layer, torch.int32), _dptr(phi, torch.float64),
+                                   _dptr(fld, torch.float64) if fld is not None else None)
+    _check(rc, "lpbfmm_eval_batched")
+    return phi, fld
+
+
+class Potential(torch.autograd.Function):
+    """phi = FMM potential of charges q at positions xyz; backward by the library's adjoint
+    (reciprocity of the layered Green's function): grad_q = phi[g], grad_xyz = -(q field[g] + g field[q])."""
+
+    @staticmethod
+    def forward(ctx_, context, q, xyz, layer):
+        phi, _ = context.eval(q.detach().contiguous(), xyz.detach().contiguous(), layer, field=False)
+        ctx_.context = context
+        ctx_.save_for_backward(q, xyz, layer)
+        return phi
+
+    @staticmethod
+    def backward(ctx_, g):
+        q, xyz, layer = ctx_.saved_tensors
+        gq, gx = ctx_.context.adjoint(q.detach().contiguous(), xyz.detach().contiguous(), layer,
+                                      g.detach().contiguous().to(torch.float64))
+        return None, gq, gx, None
+
+
+def potential(context, q, xyz, layer):
+    return Potential.apply(context, q, xyz, layer)

@@ -1,0 +1,314 @@
+"""GPU parity tests: the CUDA FMM (through the C-ABI) against the oracle, element by element.
+
+Tolerances are derived from the method: the FP64 FMM differs from the direct sum by its
+truncation error, which falls geometrically with p (Sec. 3.1 and 3.4 expansions with one-box
+separation); the tests pin that convergence, the bit-exact tree/list construction, the
+quadrature + recurrence tables, the exact near field, and the mixed-precision gate
+(relative L2 <= 1e-6 of mixed against FP64 FMM).
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2002_01334_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2002_01334_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2002_01334_gb300 import lpbfmm as F  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def tensors(w):
+    return (torch.tensor(w["q"], device=DEV), torch.tensor(w["xyz"], device=DEV).contiguous(),
+            torch.tensor(w["layer"], dtype=torch.int32, device=DEV))
+
+
+def run(w, p, prec=F.FP64, parts=3, depth=0, ctx=None):
+    m = w["medium"]
+    ctx = ctx or F.Context(m["d"], m["eps"], m["lam"], p, precision=prec, uniform_depth=depth)
+    q, x, l = tensors(w)
+    phi, fld = ctx.eval(q, x, l, parts=parts)
+    torch.cuda.synchronize()
+    return ctx, phi.cpu().numpy(), fld.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def w3000():
+    w = inputs.workload("three_layer", n=3000, seed=21)
+    md = oracle.Medium(**w["medium"])
+    ref = {parts: oracle.direct(md, w["q"], w["xyz"], w["layer"], parts=parts) for parts in (1, 2, 3)}
+    return w, ref
+
+
+@pytest.fixture(scope="module")
+def wsmall():
+    w = inputs.workload("three_layer_small")
+    md = oracle.Medium(**w["medium"])
+    ref = {parts: oracle.direct(md, w["q"], w["xyz"], w["layer"], parts=parts) for parts in (1, 2, 3)}
+    return w, ref
+
+
+def test_small_three_layer_depth2_matches_oracle(wsmall):
+    """N=1000 in the middle layer, p=8, uniform depth 2 (every tree): at depth 2 the free part
+    is all near field (exact) and the reaction part mixes near field and M2L."""
+    w, ref = wsmall
+    _, phi, fld = run(w, 8, depth=2)
+    assert rel(phi, ref[3][0]) < 5e-5 and rel(fld, ref[3][1]) < 5e-5
+    _, phi1, fld1 = run(w, 8, parts=1, depth=2)
+    assert rel(phi1, ref[1][0]) < 1e-13 and rel(fld1, ref[1][1]) < 1e-13
+
+
+@pytest.mark.parametrize("D", [3, 4])
+def test_free_part_converges_in_p(wsmall, D):
+    w, ref = wsmall
+    errs = [rel(run(w, p, parts=1, depth=D)[1], ref[1][0]) for p in (6, 8, 10)]
+    assert errs[0] > 3 * errs[1] > 9 * errs[2] and errs[2] < 2e-6, errs
+
+
+def test_reaction_part_converges_in_p(w3000):
+    w, ref = w3000
+    errs, ferrs = [], []
+    for p in (6, 8, 10, 12):
+        _, phi, fld = run(w, p, parts=2, depth=4)
+        errs.append(rel(phi, ref[2][0]))
+        ferrs.append(rel(fld, ref[2][1]))
+    assert all(errs[k] > 3 * errs[k + 1] for k in range(3)), errs
+    assert errs[3] < 1e-6 and ferrs[3] < 3e-5, (errs, ferrs)
+
+
+@pytest.mark.parametrize("D", [3, 4, 5])
+def test_total_p10_matches_oracle(w3000, D):
+    w, ref = w3000
+    _, phi, fld = run(w, 10, depth=D)
+    assert rel(phi, ref[3][0]) < 5e-6 and rel(fld, ref[3][1]) < 3e-5
+
+
+def test_reaction_near_field_equals_pairwise_oracle(wsmall):
+    """The reaction near field (Algorithm 1, last loop) evaluated by the node rule equals the
+    oracle's per-pair Sommerfeld integral of the same reaction component over the same pairs."""
+    w, _ = wsmall
+    md = oracle.Medium(**w["medium"])
+    ctx, phi, fld = run(w, 8, parts=2 | 8, depth=2)
+    trees = {}
+    for (l, a) in [(1, 1), (1, 2)]:
+        t = ctx.debug_tree(l, a)
+        D = t["depth"]
+        off, lst = ctx.debug_lists(l, a, D, 1, 1)
+        trees[(l, a)] = (np.unique(t["keys_t"]), np.unique(t["keys_i"]), off, lst, t)
+    sel = np.arange(0, len(w["q"]), 50)
+    res = np.zeros(len(sel))
+    resf = np.zeros((len(sel), 3))
+    for k, i in enumerate(sel):
+        for (l, a), (tb, ib, off, lst, t) in trees.items():
+            bt = np.searchsorted(tb, t["keys_t"][np.where(t["src_t"] == i)[0][0]])
+            for s in lst[off[bt]:off[bt + 1]]:
+                for j in np.where(t["keys_i"] == ib[s])[0]:
+                    ty = t["type_i"][j]
+                    lp = ty // 2 if ty % 2 == 0 else (ty + 1) // 2
+                    b = ty - 2 * lp + 1
+                    g, f = oracle.green_react_ab(md, 1, w["xyz"][i], lp, w["xyz"][t["src_i"][j]], a, b)
+                    res[k] += w["q"][t["src_i"][j]] * g
+                    resf[k] += w["q"][t["src_i"][j]] * f
+    assert rel(phi[sel], res) < 1e-12 and rel(fld[sel], resf) < 1e-12
+
+
+def test_deterministic(w3000):
+    w, _ = w3000
+    for prec in (F.FP64, F.MIXED):
+        ctx, a, fa = run(w, 8, prec=prec, depth=4)
+        _, b, fb = run(w, 8, prec=prec, depth=4, ctx=ctx)
+        assert np.array_equal(a, b) and np.array_equal(fa, fb)
+
+
+def test_tree_and_lists_bit_exact():
+    w = inputs.workload("three_layer", n=3000, seed=7)
+    md = oracle.Medium(**w["medium"])
+    ctx, _, _ = run(w, 6, depth=4)
+    for (l, a) in [(0, 1), (1, 1), (1, 2), (2, 2)]:
+        tr = ctx.debug_tree(l, a)
+        root = oracle.tree_root(md, w["xyz"], w["layer"], l, a)
+        assert np.array_equal(root, np.array(tr["root"]))
+        D = tr["depth"]
+        tk, tsrc, _ = oracle.tree_keys(md, w["xyz"], w["layer"], l, a, D, root, 0)
+        ik, isrc, ityp = oracle.tree_keys(md, w["xyz"], w["layer"], l, a, D, root, 1)
+        o = np.lexsort((tsrc, tk))
+        og = np.lexsort((tr["src_t"], tr["keys_t"]))
+        assert np.array_equal(tk[o], tr["keys_t"][og]) and np.array_equal(tsrc[o], tr["src_t"][og])
+        o2 = np.lexsort((isrc, ityp, ik))
+        assert np.array_equal(ik[o2], tr["keys_i"]) and np.array_equal(isrc[o2], tr["src_i"])
+        assert np.array_equal(ityp[o2], tr["type_i"])
+        for lev in range(2, D + 1):
+            tb = oracle.level_boxes(tk, D, lev)
+            sb = oracle.level_boxes(ik, D, lev)
+            kinds = (0, 1) if lev == D else (0,)
+            for kind in kinds:
+                off, idx = oracle.lists(tb, sb, lev, kind)
+                goff, gidx = ctx.debug_lists(l, a, lev, kind, 1)
+                assert np.array_equal(off, goff) and np.array_equal(idx, gidx), (l, a, lev, kind)
+                if (l, a) != (1, 2):
+                    off, idx = oracle.lists(tb, tb, lev, kind)
+                    goff, gidx = ctx.debug_lists(l, a, lev, kind, 0)
+                    assert np.array_equal(off, goff) and np.array_equal(idx, gidx), (l, a, lev, kind)
+
+
+@pytest.mark.parametrize("cls", [(1, 2, 1, 2, 5, 0, 1), (1, 1, 0, 1, 0, 1, 1), (0, 1, 2, 2, 18, 0, 0),
+                                 (2, 2, 1, 1, 2, 0, 2), (1, 1, 1, 1, 1, 0, 0)])
+def test_sommerfeld_tables_quadrature_and_recurrence(cls):
+    """d = 0, 1 by composite Gauss quadrature match the oracle's adaptive quadrature to 1e-13;
+    the forward recurrence (Sec. 3.5 eq. recurrence1) reproduces d >= 2 to 1e-9 of each row."""
+    l, a, lp, b, r2, kt, ks = cls
+    m = inputs.MEDIA["three_layer"]
+    md = oracle.Medium(**m)
+    ctx = F.Context(m["d"], m["eps"], m["lam"], 8)
+    h, K = 0.3, 19
+    g = ctx.debug_stable(l, a, lp, b, h, np.sqrt(r2) * h, (kt + .5) * h, (ks + .5) * h, K)
+    o = oracle.S_table(md, l, lp, a, b, h, np.sqrt(r2) * h, (kt + .5) * h, (ks + .5) * h, K)
+    for KK in range(K + 1):
+        for d in range(min(KK, 1) + 1):
+            assert np.abs(g[KK, d] - o[KK, d]).max() <= 1e-13 * np.abs(o[KK, d]).max() + 1e-300
+        assert np.abs(g[KK, :KK + 1] - o[KK, :KK + 1]).max() <= 1e-9 * np.abs(o[KK, :KK + 1]).max()
+
+
+def test_mixed_precision_gate(w3000):
+    """Mixed precision (FP32 P2P, P2M/M2M/M2L/L2L/L2P; FP64 tables and sums) against the FP64
+    FMM on the same tree: relative L2 <= 1e-6 in potential and field."""
+    w, _ = w3000
+    for p in (8, 10):
+        _, a, fa = run(w, p, prec=F.FP64)
+        _, b, fb = run(w, p, prec=F.MIXED)
+        assert rel(b, a) < 1e-6 and rel(fb, fa) < 1e-6, (p, rel(b, a), rel(fb, fa))
+
+
+def test_four_layer_medium_all_layers(w3000):
+    w = inputs.workload("four_layer", n=2000, seed=5)
+    md = oracle.Medium(**w["medium"])
+    ref = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    _, phi, fld = run(w, 10, depth=4)
+    assert rel(phi, ref[0]) < 1e-5 and rel(fld, ref[1]) < 5e-5
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 37, 129])
+def test_ragged_and_tiny_inputs(n):
+    w = inputs.workload("three_layer", n=n, seed=100 + n)
+    md = oracle.Medium(**w["medium"])
+    ref = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    _, phi, fld = run(w, 10, depth=3)
+    assert rel(phi, ref[0]) < 1e-5 and rel(fld, ref[1]) < 5e-5
+
+
+def test_empty_input_is_noop():
+    m = inputs.MEDIA["three_layer"]
+    ctx = F.Context(m["d"], m["eps"], m["lam"], 8)
+    z = torch.zeros(0, dtype=torch.float64, device=DEV)
+    phi, fld = ctx.eval(z, torch.zeros((0, 3), dtype=torch.float64, device=DEV),
+                        torch.zeros(0, dtype=torch.int32, device=DEV))
+    assert phi.numel() == 0
+
+
+@pytest.mark.parametrize("case,code", [("nan", 6), ("interface", 4), ("mismatch", 5)])
+def test_invalid_inputs_return_codes(case, code):
+    w = inputs.workload("three_layer", n=60, seed=3)
+    xyz = w["xyz"].copy()
+    layer = w["layer"].copy()
+    if case == "nan":
+        xyz[7, 0] = np.nan
+    elif case == "interface":
+        xyz[8, 2] = 0.0
+        layer[8] = 1
+    else:
+        layer[9] = (layer[9] + 1) % 3
+    m = w["medium"]
+    ctx = F.Context(m["d"], m["eps"], m["lam"], 8)
+    with pytest.raises(F.LpbfmmError) as e:
+        ctx.eval(torch.tensor(w["q"], device=DEV), torch.tensor(xyz, device=DEV),
+                 torch.tensor(layer, dtype=torch.int32, device=DEV))
+    assert e.value.code == code
+
+
+def test_adjoint_forces_and_dEdq_match_oracle_and_finite_differences():
+    """E = 1/2 sum q phi; dE/dq = phi and -dE/dr = q field by reciprocity (FP64 FMM)."""
+    w = inputs.workload("four_layer", n=400, seed=9)
+    m = w["medium"]
+    md = oracle.Medium(**m)
+    ctx = F.Context(m["d"], m["eps"], m["lam"], 12, uniform_depth=3)
+    q, x, l = tensors(w)
+    gq, gx = ctx.adjoint(q, x, l, 0.5 * q)
+    ref_phi, ref_fld = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    assert rel(gq.cpu().numpy(), ref_phi) < 1e-6
+    force = -gx.cpu().numpy()
+    assert rel(force, w["q"][:, None] * ref_fld) < 3e-6
+    # central differences of E for a few charges (positions inside their boxes at depth 3)
+    def energy(xx):
+        phi, _ = ctx.eval(q, torch.tensor(xx, device=DEV), l, field=False)
+        return 0.5 * float(torch.dot(q, phi))
+    hstep = 1e-5
+    for i in (3, 111, 250):
+        for k in range(3):
+            xp = w["xyz"].copy(); xp[i, k] += hstep
+            xm = w["xyz"].copy(); xm[i, k] -= hstep
+            fd = -(energy(xp) - energy(xm)) / (2 * hstep)
+            assert abs(fd - force[i, k]) < 1e-5 * np.abs(force).max() + 1e-7, (i, k, fd, force[i, k])
+
+
+def test_autograd_function():
+    w = inputs.workload("three_layer", n=300, seed=4)
+    m = w["medium"]
+    ctx = F.Context(m["d"], m["eps"], m["lam"], 10, uniform_depth=3)
+    q, x, l = tensors(w)
+    q.requires_grad_(True)
+    x.requires_grad_(True)
+    phi = F.potential(ctx, q, x, l)
+    E = 0.5 * (q * phi).sum()
+    E.backward()
+    phi2, fld = ctx.eval(q.detach(), x.detach(), l)
+    assert torch.allclose(q.grad, phi2, rtol=1e-6, atol=1e-9)
+    assert torch.allclose(-x.grad, q.detach()[:, None] * fld, rtol=1e-5, atol=1e-8)
+
+
+def test_batched_matches_individual():
+    systems = inputs.batch(nsys=4, nmin=200, nmax=800)
+    ctxs, qs, xs, ls, offs = [], [], [], [], [0]
+    for s in systems:
+        m = s["medium"]
+        ctxs.append(F.Context(m["d"], m["eps"], m["lam"], 8))
+        qs.append(s["q"]); xs.append(s["xyz"]); ls.append(s["layer"])
+        offs.append(offs[-1] + len(s["q"]))
+    q = torch.tensor(np.concatenate(qs), device=DEV)
+    x = torch.tensor(np.concatenate(xs), device=DEV)
+    l = torch.tensor(np.concatenate(ls), dtype=torch.int32, device=DEV)
+    phi, fld = F.eval_batched(ctxs, offs, q, x, l)
+    for k, s in enumerate(systems):
+        md = oracle.Medium(**s["medium"])
+        sel = np.arange(0, len(s["q"]), 37)
+        ref = oracle.direct(md, s["q"], s["xyz"], s["layer"], targets=sel)
+        got = phi[offs[k]:offs[k + 1]].cpu().numpy()[sel]
+        assert rel(got, ref[0]) < 2e-5
+
+
+@pytest.mark.skipif(os.environ.get("LPBFMM_FULL_SIZE", "1") == "0", reason="full-size sample disabled")
+def test_full_size_three_layer_sampled_targets():
+    """N = 1,000,000 in three layers, p = 10, automatic depth, the launch configuration the
+    benchmark times: FP64 and mixed FMM against the oracle on sampled targets."""
+    w = inputs.workload("three_layer", n=1000000)
+    md = oracle.Medium(**w["medium"])
+    sel = np.array([0, 1, 2, 333331, 500000, 999999])
+    ref = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=sel)
+    _, a, fa = run(w, 10, prec=F.FP64)
+    _, b, fb = run(w, 10, prec=F.MIXED)
+    assert rel(a[sel], ref[0]) < 2e-5 and rel(fa[sel], ref[1]) < 1e-4
+    assert rel(b, a) < 1e-6 and rel(fb, fa) < 3e-6
