@@ -1,0 +1,312 @@
+"""Benchmark: targets/s (potential + field) of the layered-media screened-Coulomb FMM.
+
+Workload (one step = one full evaluation, trees + tables + all passes): N = 1,000,000 charges
+in the three-layer medium d = (0, -1.2), eps = (1, 2, 5), lambda = (0.5, 1, 0.8), split evenly
+over three unit cubes (one per layer), q ~ U[-1, 1], p = 10, mixed precision.  Inputs are
+resident in HBM; L2 is flushed (256 MB write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (direct sum) on the host
+cores on a bounded sample of the same workload.  With --gpus N > 1 (launched by
+torch.distributed.run) every rank evaluates its own independent system of N charges (weak
+scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "targets/sec (potential+field) N=1M 3-layer @relL2<=1e-6: mixed vs FP64 FMM"
+N_DEFAULT = 1000000
+P_DEFAULT = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--p", type=int, default=P_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n, p, precision):
+    return {"workload": "three-layer screened Coulomb, N=%d, p=%d" % (n, p), "n": n, "p": p, "layers": 3,
+            "interfaces": [0.0, -1.2], "eps": [1.0, 2.0, 5.0], "lambda": [0.5, 1.0, 0.8],
+            "charges": "q~U[-1,1], uniform in three unit cubes (one per layer)", "precision": precision,
+            "l2": "flushed between steps (256 MB write)", "tree": "automatic depth, <=128 mean targets per leaf"}
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload, scaled to targets/s over all sources)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(w, n_targets, source_stride):
+    import oracle
+    md = oracle.Medium(**w["medium"])
+    n = len(w["q"])
+    sel = np.arange(0, n, source_stride)
+    q, xyz, layer = w["q"][sel], w["xyz"][sel], w["layer"][sel]
+    tg = np.arange(n_targets) * (len(sel) // max(n_targets, 1))
+    t0 = time.perf_counter()
+    oracle.direct(md, q, xyz, layer, targets=tg)
+    dt = time.perf_counter() - t0
+    frac = len(sel) / n
+    return n_targets * frac / dt, dt, {"kind": "oracle", "cores": oracle.num_threads(),
+                                       "sample": "%d targets x %d of %d sources (every %d-th charge); "
+                                                 "targets/s scaled by the source fraction %.4f"
+                                                 % (n_targets, len(sel), n, source_stride, frac)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2002_01334_gb300 import inputs
+    import oracle
+    oracle.build()
+    w = inputs.workload("three_layer", n=args.n)
+    cores = oracle.num_threads()
+    nt, stride = max(2, cores), 20
+    for _ in range(args.warmup):
+        oracle_sample(w, nt, stride)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, info = oracle_sample(w, nt, stride)
+        vals.append(v)
+        times.append(dt)
+    value = args.steps * nt * (args.n // stride) / args.n / sum(times)
+    info["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.n, args.p, "fp64 direct sum (CPU oracle)"), "cpu_baseline": info,
+            "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2002_01334_gb300 import build as B
+    B.build()
+    from paper_2002_01334_gb300 import inputs
+    from paper_2002_01334_gb300 import lpbfmm as F
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = inputs.workload("three_layer", n=args.n, seed=inputs.BASE_SEED + 2 + 1000 * rank)
+    m = w["medium"]
+    q = torch.tensor(w["q"], device=dev)
+    x = torch.tensor(w["xyz"], device=dev)
+    l = torch.tensor(w["layer"], dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.MIXED, stream=stream)
+    n = args.n
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    fld = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ctx.eval(q, x, l, out=(phi, fld))
+    torch.cuda.synchronize(dev)
+    counts = ctx.counts()
+    launches_per_step = counts["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    m2l_ms = []
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            ctx.eval(q, x, l, out=(phi, fld))
+            ev[k][1].record(stream)
+            prof = dict((nm, ms) for nm, ms, _ in ctx.profile())
+            m2l_ms.append(prof.get("m2l", float("nan")))
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public call with host buffers (pinned), copies inside the timed region
+    hq = torch.tensor(w["q"]).pin_memory()
+    hx = torch.tensor(w["xyz"]).pin_memory()
+    hl = torch.tensor(w["layer"], dtype=torch.int32).pin_memory()
+    hphi = torch.empty(n, dtype=torch.float64).pin_memory()
+    hfld = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    dq, dx, dl = torch.empty_like(q), torch.empty_like(x), torch.empty_like(l)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dq.copy_(hq, non_blocking=True)
+        dx.copy_(hx, non_blocking=True)
+        dl.copy_(hl, non_blocking=True)
+        ctx.eval(dq, dx, dl, out=(phi, fld))
+        hphi.copy_(phi, non_blocking=True)
+        hfld.copy_(fld, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * n * e2e_steps / (e2e_ms / 1000.0)
+
+    # accuracy gate and the FP64 comparator (same tree rule, same inputs), untimed by the driver's clock
+    accuracy, fp64_value = None, None
+    if not args.no_fp64:
+        ctx64 = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.FP64, stream=stream)
+        p64 = torch.empty_like(phi)
+        f64 = torch.empty_like(fld)
+        ctx64.eval(q, x, l, out=(p64, f64))
+        torch.cuda.synchronize(dev)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        ctx64.eval(q, x, l, out=(p64, f64))
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64_value = n / (s0.elapsed_time(s1) / 1000.0)
+        ctx.eval(q, x, l, out=(phi, fld))
+        torch.cuda.synchronize(dev)
+        accuracy = {"relL2_phi_mixed_vs_fp64": float(torch.linalg.norm(phi - p64) / torch.linalg.norm(p64)),
+                    "relL2_field_mixed_vs_fp64": float(torch.linalg.norm(fld - f64) / torch.linalg.norm(f64)),
+                    "gate": 1e-6}
+        ctx64.close()
+
+    # roofline of the dominant kernel: the merged multipole-to-local launch, FP32 FMA pipe (SIMT)
+    K = (args.p + 1) * (args.p + 2) // 2
+    flops = 4.0 * K * K * (counts["m2l_free"] + counts["m2l_react"])
+    m2l_med = float(np.nanmedian(m2l_ms))
+    achieved = flops / (m2l_med / 1000.0) / 1e12
+    peak = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "m2l_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch_1M")
+        except Exception:
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_m2l (free + reaction multipole-to-local, FP32 FMA)",
+            "ms_per_launch": m2l_med, "algorithmic_flops_per_launch": flops}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, dt, info = oracle_sample(w, max(2, oracle.num_threads()), 10)
+        info["value"] = v
+        cpu = info
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": workload_config(n, args.p, "mixed"), "clocks": clk.summary(),
+                "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
+                        "d2h_bytes_per_step": n * (8 + 24)},
+                "gpu_launches": launches_per_step * args.steps, "roofline": roof, "cpu_baseline": cpu,
+                "fp64_fmm_value": fp64_value, "accuracy": accuracy, "counts": counts}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

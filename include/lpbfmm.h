@@ -107,9 +107,10 @@ int lpbfmm_eval_parts(lpbfmm_t h, int64_t n, const double *q, const double *xyz,
  * Adjoint of phi with respect to q and positions for an upstream gradient g_phi[n] (device):
  *   g_q[j]   = sum_i g_phi[i] G(r_i, r_j)                  = phi[g_phi](r_j)
  *   g_xyz[j] = sum_i g_phi[i] d phi_i / d r_j = -(q_j field[g_phi](r_j) + g_phi[j] field[q](r_j))
- * using the reciprocity G_{l l'}(r, r') = G_{l' l}(r', r) of the layered Green's function.
- * With g_phi = q / 2 this gives dE/dq and -(force) for E = 1/2 sum q_i phi_i.  Device arrays;
- * g_q[n], g_xyz[n*3] are outputs.
+ * using the reciprocity G_{l l'}(r, r') = G_{l' l}(r', r) of the layered Green's function (the
+ * vector-Jacobian product of phi).  For E = 1/2 sum q_i phi_i: dE/dq = g_q with g_phi = q, and
+ * dE/dr = g_xyz with g_phi = q / 2 (so the force on charge j is -g_xyz[j]).  Two evaluations
+ * are run.  Device arrays; g_q[n], g_xyz[n*3] are outputs.
  */
 int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
                    const double *g_phi, double *g_q, double *g_xyz);
@@ -152,7 +153,8 @@ int lpbfmm_debug_lists(lpbfmm_t h, int l, int a, int lev, int kind, int src, int
  *        * int_0^inf lr^K J_d(lr rho) exp(-lz_l zt - lz_l' zs) sigma^{ab}_{l l'} / lz_l
  *          (lambda_l/lz_l)^i (lambda_l'/lz_l')^j d lr,         K = 0..Kmax, d = 0..K,
  * computed on the device the way the FMM computes them: quadrature for d = 0, 1 and the
- * forward recurrence in d (eq. recurrence1) for d >= 2.  zt, zs > 0 are the distances of the
+ * forward recurrence in d (eq. recurrence1) for d >= 2.  Only the entries with K - d odd are
+ * computed (the multipole-to-local operators use no others); the rest are 0.  zt, zs > 0 are the distances of the
  * target and source centres to the component's interface, rho = ratio * h with ratio^2 in
  * {0,1,2,4,5,8,9,10,13,18}.  out is a host array.
  */
@@ -169,6 +171,15 @@ int lpbfmm_debug_stable(lpbfmm_t h, int l, int a, int lp, int b, double hbox, do
  */
 int lpbfmm_debug_array(lpbfmm_t h, int l, int a, const char *name, int lev, void *dst, int64_t cap,
                        int64_t *bytes);
+
+/*
+ * Work counts of the last lpbfmm_eval (host int64 out[8]): [0] free-space multipole-to-local
+ * translations, [1] reaction translations (box pairs x source types), [2] free-space P2P pairs
+ * (including the excluded self pairs), [3] reaction near-field pairs, [4] targets summed over
+ * the target groups, [5] images summed over the groups, [6] target boxes over all groups and
+ * levels, [7] kernels launched by the evaluation.  Synchronizes the context's stream.
+ */
+int lpbfmm_last_counts(lpbfmm_t h, int64_t *out);
 
 /* Read and clear the device status word (synchronizes the context's stream). */
 int lpbfmm_status(lpbfmm_t h);

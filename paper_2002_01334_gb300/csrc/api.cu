@@ -79,6 +79,19 @@ static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w
 }
 
 // G[a][c][q] = int Y_a^alpha Y_q^{gamma-alpha} conj(Y_c^gamma) dOmega (all real), full indices a, c
+// sqrt((K+d)! (K-d)!) for 0 <= d <= K <= KMAX_TAB, the normalisation of the scaled
+// Sommerfeld tables (long double products, then rounded once)
+static std::vector<double> sfac_table() {
+  const int n = KMAX_TAB + 1;
+  std::vector<long double> f(2 * n + 1);
+  f[0] = 1.0L;
+  for (int k = 1; k <= 2 * n; ++k) f[k] = f[k - 1] * (long double)k;
+  std::vector<double> out((size_t)n * n, 0.0);
+  for (int K = 0; K < n; ++K)
+    for (int d = 0; d <= K; ++d) out[(size_t)K * n + d] = (double)sqrtl(f[K + d] * f[K - d]);
+  return out;
+}
+
 static std::vector<double> gaunt_table(int p) {
   const int NF = (p + 1) * (p + 1), NQ = 2 * p + 1, qmax = 2 * p;
   std::vector<double> G((size_t)NF * NF * NQ, 0.0);
@@ -364,6 +377,9 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     LPB_CUDA(cudaMemcpy(c->gaunt, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice));
     LPB_CUDA(cudaMalloc(&c->tpoly, sizeof(double) * tp.size()));
     LPB_CUDA(cudaMemcpy(c->tpoly, tp.data(), sizeof(double) * tp.size(), cudaMemcpyHostToDevice));
+    std::vector<double> sf = sfac_table();
+    LPB_CUDA(cudaMalloc(&c->sfac, sizeof(double) * sf.size()));
+    LPB_CUDA(cudaMemcpy(c->sfac, sf.data(), sizeof(double) * sf.size(), cudaMemcpyHostToDevice));
     LPB_CUDA(cudaMalloc(&c->status, sizeof(int)));
     LPB_CUDA(cudaMemset(c->status, 0, sizeof(int)));
     LPB_CUDA(cudaMallocHost(&c->h_pinned, 1 << 16));
@@ -472,6 +488,7 @@ void lpbfmm_destroy(lpbfmm_t h) {
   h->arena.release();
   if (h->gaunt) cudaFree(h->gaunt);
   if (h->tpoly) cudaFree(h->tpoly);
+  if (h->sfac) cudaFree(h->sfac);
   if (h->status) cudaFree(h->status);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int k = 0; k < 64; ++k)
@@ -617,6 +634,73 @@ int lpbfmm_debug_array(lpbfmm_t h, int l, int a, const char *name, int lev, void
   if ((int64_t)nb > cap) return LPBFMM_ERR_ARG;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LPBFMM_ERR_CUDA;
   if (cudaMemcpy(dst, src, nb, cudaMemcpyDeviceToHost) != cudaSuccess) return LPBFMM_ERR_CUDA;
+  return LPBFMM_OK;
+}
+
+__global__ void k_count_lists(const int32_t *v, int64_t n, unsigned long long *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned c = __popc(__ballot_sync(0xffffffffu, i < n && v[i] >= 0));
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+// pairs of the near list: sum over target leaves of count(target) * count(source)
+__global__ void k_count_near(const int32_t *u, int64_t nb, const uint32_t *tcnt, const uint32_t *scnt,
+                             unsigned long long *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = 0;
+  if (i < nb * 27) {
+    const int32_t s = u[i];
+    if (s >= 0) v = (unsigned long long)tcnt[i / 27] * scnt[s];
+  }
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+int lpbfmm_last_counts(lpbfmm_t h, int64_t *out) {
+  if (!h || !out) return LPBFMM_ERR_ARG;
+  unsigned long long *d = nullptr;
+  try {
+    LPB_CUDA(cudaMalloc(&d, 8 * sizeof(unsigned long long)));
+    LPB_CUDA(cudaMemsetAsync(d, 0, 8 * sizeof(unsigned long long), h->stream));
+    for (auto &g : h->groups) {
+      for (int l = 2; l <= g.D; ++l) {
+        const int64_t nv = g.T.lev[l].n * NOFF;
+        if (g.vfree[l]) k_count_lists<<<(unsigned)((nv + 255) / 256), 256, 0, h->stream>>>(g.vfree[l], nv, d + 0);
+        if (g.vreact[l]) {
+          for (int t = 0; t < g.ntypes; ++t)
+            k_count_lists<<<(unsigned)((nv + 255) / 256), 256, 0, h->stream>>>(g.vreact[l], nv, d + 1);
+        }
+      }
+      const int64_t nb = g.T.lev[g.D].n;
+      if (g.ufree)
+        k_count_near<<<(unsigned)((nb * 27 + 255) / 256), 256, 0, h->stream>>>(g.ufree, nb, g.T.lev[g.D].count,
+                                                                              g.T.lev[g.D].count, d + 2);
+      if (g.ureact)
+        k_count_near<<<(unsigned)((nb * 27 + 255) / 256), 256, 0, h->stream>>>(g.ureact, nb, g.T.lev[g.D].count,
+                                                                              g.I.lev[g.D].count, d + 3);
+    }
+    LPB_CUDA(cudaGetLastError());
+    unsigned long long hv[8];
+    LPB_CUDA(cudaMemcpyAsync(hv, d, sizeof hv, cudaMemcpyDeviceToHost, h->stream));
+    LPB_CUDA(cudaStreamSynchronize(h->stream));
+    cudaFree(d);
+    int64_t nt = 0, ni = 0, nbox = 0;
+    for (auto &g : h->groups) {
+      nt += g.T.np;
+      ni += g.I.np;
+      for (int l = 2; l <= g.D; ++l) nbox += g.T.lev[l].n;
+    }
+    out[0] = (int64_t)hv[0];  // free-space M2L translations
+    out[1] = (int64_t)hv[1];  // reaction M2L translations (pairs x source types)
+    out[2] = (int64_t)hv[2];  // free-space P2P pairs (incl. the excluded self pairs)
+    out[3] = (int64_t)hv[3];  // reaction near-field pairs
+    out[4] = nt;              // targets over all groups
+    out[5] = ni;              // images over all groups
+    out[6] = nbox;            // target boxes over all groups and levels
+    out[7] = h->launches;     // kernels launched by the last evaluation
+  } catch (const CudaError &e) {
+    if (d) cudaFree(d);
+    return map_error(e);
+  }
   return LPBFMM_OK;
 }
 

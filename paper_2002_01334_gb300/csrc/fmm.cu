@@ -253,10 +253,11 @@ struct XJob {
   const int32_t *cls_of;  // [NOFF] operator class or -1
   const void *M;          // [nsb][ntypes][K]
   const void *ops;        // [ncls][ntypes][2][K][K]
-  void *L;                // [ntb][K]
-  int ntypes, pad;
+  void *L;                // partial sums [ntb][M2L_NSLOT][K]: slot = slot0 + dx-slice
+  int ntypes, slot0;
   int64_t item0;          // first work item of this job
 };
+constexpr int M2L_NSLOT = 2 * M2L_NSLICE;  // free-space slices, then reaction slices
 
 template <typename T>
 __device__ __forceinline__ void atomic_add2(typename C2<T>::t *p, T x, T y) {
@@ -389,9 +390,247 @@ __global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const 
     for (int r = 0; r < NR; ++r) {
       const int row = ty + 16 * r;
       if (row >= K) break;
-      atomic_add2<T>(&L[(size_t)t * K + row], Lr[r][j], Li[r][j]);
+      L[((size_t)t * M2L_NSLOT + J.slot0 + slice) * K + row] = T2{Lr[r][j], Li[r][j]};
     }
   }
+}
+
+// FP32 multipole-to-local with asynchronous double-buffered staging.  A work item (job, tile of
+// 96 target boxes, dx-slice) first lists its (offset, type) steps that have at least one source;
+// every step copies the class operator (P, Q, K x K) and the tile's source multipoles into a
+// shared-memory stage with cp.async while the previous step is multiplied.  After a stage lands
+// the multipoles are rotated by e^{i mu phi} in place; the product is rotated by e^{-i m phi}
+// into the register accumulators, which are added atomically at the end.
+constexpr int F32_TPT = 6, F32_TT = 16 * F32_TPT, F32_NR = 5, F32_KR = 16 * F32_NR;
+constexpr int F32_MAXSTEP = 49 * 2 * MAXLAYER;
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+static size_t m2l_f32_smem(int K) {
+  const size_t op = (size_t)2 * F32_KR * K * 4, xs = (size_t)F32_TT * (K + 1) * 8;
+  return 2 * (op + xs) + sizeof(int) * (F32_TT + F32_MAXSTEP + 2 * F32_TT + F32_KR) + 2 * (PMAX + 1) * 8 * 2;
+}
+
+__global__ void __launch_bounds__(256, 1) k_m2l_f32(const XJob *jobs, int njobs, const float *rot, int K) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const size_t opsz = (size_t)2 * F32_KR * K, xsz = (size_t)F32_TT * (K + 1) * 2;  // floats
+  float *stage[2];
+  stage[0] = (float *)smraw;
+  stage[1] = stage[0] + opsz + xsz;
+  int *tid_ = (int *)(stage[1] + opsz + xsz);
+  int *steps = tid_ + F32_TT;                // (o << 4) | tau
+  int *srcs = steps + F32_MAXSTEP;           // [2][TT] source box per stage
+  int *mofs = srcs + 2 * F32_TT;              // [KR] m of each half-representation index
+  float *rotc = (float *)(mofs + F32_KR);     // [2][PMAX+1][2]
+  __shared__ int nsteps;
+  __shared__ unsigned hasmask[2];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].item0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const XJob J = jobs[lo];
+  const int64_t local = (int64_t)blockIdx.x - J.item0;
+  const int slice = (int)(local % M2L_NSLICE);
+  const int64_t tile0 = (local / M2L_NSLICE) * F32_TT;
+  const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
+  if (tile0 >= ntl) return;
+  const float2 *M = (const float2 *)J.M;
+  const float *ops = (const float *)J.ops;
+  float2 *L = (float2 *)J.L;
+  const int ntypes = J.ntypes;
+  const size_t KK = (size_t)K * K;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x < F32_TT) {
+    const int64_t j = tile0 + threadIdx.x;
+    tid_[threadIdx.x] = (j < ntl) ? (J.tlist ? J.tlist[j] : (int)j) : -1;
+  }
+  if (threadIdx.x < 2) hasmask[threadIdx.x] = 0u;
+  if (threadIdx.x < F32_KR) mofs[threadIdx.x] = threadIdx.x < K ? cK.mof[threadIdx.x] : 0;
+  // zero the operator padding rows K..KR-1 of both stages once
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int e = threadIdx.x; e < 2 * (F32_KR - K) * K; e += blockDim.x) {
+      const int half = e / ((F32_KR - K) * K), r = e % ((F32_KR - K) * K);
+      stage[s2][half * F32_KR * K + K * K + r] = 0.0f;
+    }
+  __syncthreads();
+  // offsets of the slice with at least one source in the tile
+  if (threadIdx.x < F32_TT) {
+    const int t = tid_[threadIdx.x];
+    if (t >= 0)
+      for (int k = 0; k < 49; ++k) {
+        const int o = slice * 49 + k;
+        if (J.cls_of[o] >= 0 && J.vlist[(size_t)t * NOFF + o] >= 0) atomicOr(&hasmask[k >> 5], 1u << (k & 31));
+      }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int k = 0; k < 49; ++k)
+      if (hasmask[k >> 5] & (1u << (k & 31)))
+        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * 49 + k) << 4) | tau;
+    nsteps = n;
+  }
+  __syncthreads();
+  const int ns = nsteps;
+  if (ns == 0) return;
+  // --- staging helpers (explicit, see below)
+  auto stage_step = [&](int st, int buf) {
+    const int o = steps[st] >> 4, tau = steps[st] & 15;
+    const int cls = J.cls_of[o];
+    float *opP = stage[buf], *opQ = opP + F32_KR * K;
+    float *xs = opP + opsz;
+    const float *P = ops + ((size_t)cls * ntypes + tau) * 2 * KK, *Q = P + KK;
+    if (KK & 1) {  // Q is only 4-byte aligned: 4-byte granules
+      for (int e = threadIdx.x; e < (int)KK; e += blockDim.x) {
+        cp_async4(opP + e, P + e);
+        cp_async4(opQ + e, Q + e);
+      }
+    } else {
+      const int halfKK = (int)(KK / 2);
+      for (int e = threadIdx.x; e < halfKK; e += blockDim.x) {
+        cp_async8(opP + 2 * e, P + 2 * e, true);
+        cp_async8(opQ + 2 * e, Q + 2 * e, true);
+      }
+    }
+    int *sb = srcs + buf * F32_TT;
+    if (threadIdx.x < F32_TT) {
+      const int t = tid_[threadIdx.x];
+      sb[threadIdx.x] = t >= 0 ? J.vlist[(size_t)t * NOFF + o] : -1;
+    }
+    if (threadIdx.x < 2 * (PMAX + 1)) {
+      float *rc = rotc + buf * 2 * (PMAX + 1);
+      rc[threadIdx.x] = rot[(size_t)o * (PMAX + 1) * 2 + threadIdx.x];
+    }
+    __syncthreads();
+    // multipoles: row j (K float2, padded to K+1) of source sb[j]; 8-byte granules
+    for (int e = threadIdx.x; e < F32_TT * K; e += blockDim.x) {
+      const int j = e / K, k = e % K;
+      const int s = sb[j];
+      const float2 *src = s >= 0 ? M + ((size_t)s * ntypes + tau) * K + k : M;
+      cp_async8(xs + 2 * ((size_t)j * (K + 1) + k), src, s >= 0);
+    }
+    cp_commit();
+  };
+  float Lr[F32_NR][F32_TPT], Li[F32_NR][F32_TPT];
+#pragma unroll
+  for (int r = 0; r < F32_NR; ++r)
+#pragma unroll
+    for (int j = 0; j < F32_TPT; ++j) Lr[r][j] = Li[r][j] = 0.f;
+  stage_step(0, 0);
+  for (int st = 0; st < ns; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < ns) {
+      stage_step(st + 1, buf ^ 1);
+      cp_wait1();
+    } else {
+      cp_wait0();
+    }
+    __syncthreads();
+    float *opP = stage[buf], *opQ = opP + F32_KR * K;
+    float *xs = opP + opsz;
+    const float *rc = rotc + buf * 2 * (PMAX + 1);
+    // rotate the staged multipoles by e^{i mu phi}
+    for (int e = threadIdx.x; e < F32_TT * K; e += blockDim.x) {
+      const int j = e / K, k = e % K;
+      float2 *v = (float2 *)(xs + 2 * ((size_t)j * (K + 1) + k));
+      const int m = mofs[k];
+      const float c = rc[2 * m], sn = rc[2 * m + 1];
+      const float2 a = *v;
+      *v = make_float2(c * a.x - sn * a.y, sn * a.x + c * a.y);
+    }
+    __syncthreads();
+    float Yr[F32_NR][F32_TPT], Yi[F32_NR][F32_TPT];
+#pragma unroll
+    for (int r = 0; r < F32_NR; ++r)
+#pragma unroll
+      for (int j = 0; j < F32_TPT; ++j) Yr[r][j] = Yi[r][j] = 0.f;
+    const float2 *xv = (const float2 *)xs;
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+      float2 x[F32_TPT];
+#pragma unroll
+      for (int j = 0; j < F32_TPT; ++j) x[j] = xv[(size_t)(tx + 16 * j) * (K + 1) + k];
+#pragma unroll
+      for (int r = 0; r < F32_NR; ++r) {
+        const float pv = opP[(ty + 16 * r) * K + k], qv = opQ[(ty + 16 * r) * K + k];
+#pragma unroll
+        for (int j = 0; j < F32_TPT; ++j) {
+          Yr[r][j] = fmaf(pv, x[j].x, Yr[r][j]);
+          Yi[r][j] = fmaf(qv, x[j].y, Yi[r][j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < F32_NR; ++r) {
+      const int row = ty + 16 * r;
+      const int m = mofs[row];
+      const float c = rc[2 * m], sn = rc[2 * m + 1];
+#pragma unroll
+      for (int j = 0; j < F32_TPT; ++j) {
+        Lr[r][j] += c * Yr[r][j] + sn * Yi[r][j];
+        Li[r][j] += c * Yi[r][j] - sn * Yr[r][j];
+      }
+    }
+    __syncthreads();  // the stage is refilled two steps later
+  }
+#pragma unroll
+  for (int j = 0; j < F32_TPT; ++j) {
+    const int t = tid_[tx + 16 * j];
+    if (t < 0) continue;
+#pragma unroll
+    for (int r = 0; r < F32_NR; ++r) {
+      const int row = ty + 16 * r;
+      if (row >= K) break;
+      L[((size_t)t * M2L_NSLOT + J.slot0 + slice) * K + row] = make_float2(Lr[r][j], Li[r][j]);
+    }
+  }
+}
+
+// L[box][k] += sum over the partial slots, in slot order (deterministic)
+struct RJob {
+  const void *part;
+  void *L;
+  int64_t n;     // boxes x K
+  int64_t e0;    // first element of this job in the flattened launch
+};
+template <typename T>
+__global__ void k_m2l_reduce(const RJob *jobs, int njobs, int K) {
+  typedef typename C2<T>::t T2;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].e0 <= g) lo = mid; else hi = mid - 1;
+  }
+  const RJob J = jobs[lo];
+  const int64_t e = g - J.e0;
+  if (e < 0 || e >= J.n) return;
+  const int64_t box = e / K, k = e % K;
+  const T2 *P = (const T2 *)J.part + box * M2L_NSLOT * K + k;
+  T sx = 0, sy = 0;
+#pragma unroll
+  for (int s = 0; s < M2L_NSLOT; ++s) {
+    sx += P[(size_t)s * K].x;
+    sy += P[(size_t)s * K].y;
+  }
+  T2 &d = ((T2 *)J.L)[e];
+  d.x += sx;
+  d.y += sy;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -478,102 +717,152 @@ __global__ void k_l2p(const uint32_t *d_nb, const uint64_t *bkey, const uint32_t
 }
 
 // ---------------------------------------------------------------------------------------
-// free-space P2P over the near list (27 neighbours incl. the box itself), pair math in T,
-// per-neighbour partial sums in T, per-target accumulation in FP64
+// free-space P2P over the near list (27 neighbours incl. the box itself).  One CTA of
+// P2P_TPB threads per target leaf; the sources of all neighbours are streamed through shared
+// memory in full tiles of P2P_SRC (position, charge) records; a thread holds up to two targets
+// (t and t + P2P_TPB), chosen per warp, so each shared-memory record read serves two pairs.
+// Pair math in T, per-tile partial sums in T, per-target accumulation in FP64.  The self pair
+// (r = 0) is dropped by a select, so distinct charges at one point do not interact either.
 // ---------------------------------------------------------------------------------------
-constexpr int P2P_THREADS = 128;
+constexpr int P2P_THREADS = 128;  // reaction near field
+constexpr int P2P_TPB = 64, P2P_SRC = 128;
 
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
 
-// Mixed precision keeps each offset from the box centre as an FP32 pair hi + lo (the FP64
-// offset to 48 bits); the pair difference (hi_t - hi_s) + (lo_t - lo_s) is then accurate to
-// FP32 precision of the difference itself, also for close pairs.
 template <typename T>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p_free(const uint32_t *d_nb, const uint64_t *bkey,
-                                                          const uint32_t *bstart, const uint32_t *bcount,
-                                                          const int32_t *ulist, const double *x, const double *y,
-                                                          const double *z, const double *q, const uint32_t *src,
-                                                          Geo geo, double lam, double scale, double *phi,
-                                                          double *field) {
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+template <typename T, int NT, bool COMP>
+__device__ __forceinline__ void p2p_free_tile(const V4<T> *__restrict__ sh, const V4<T> *__restrict__ sl, int nn,
+                                              const T (&px)[2], const T (&py)[2], const T (&pz)[2],
+                                              const T (&qx)[2], const T (&qy)[2], const T (&qz)[2], T lam,
+                                              T (&fp)[2], T (&fx)[2], T (&fy)[2], T (&fz)[2]) {
+#pragma unroll 2
+  for (int j = 0; j < nn; ++j) {
+    const V4<T> s = sh[j];
+    V4<T> sL;
+    if (COMP) sL = sl[j];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      T dx = px[t] - s.x, dy = py[t] - s.y, dz = pz[t] - s.z;
+      if (COMP) {
+        dx += qx[t] - sL.x;
+        dy += qy[t] - sL.y;
+        dz += qz[t] - sL.z;
+      }
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      const T ri = r2 > T(0) ? frsqrt(r2) : T(0);
+      const T r = r2 * ri;
+      const T e = s.w * fexp(-lam * r) * ri;
+      fp[t] += e;
+      const T f = e * (ri * ri) * (T(1) + lam * r);
+      fx[t] += f * dx;
+      fy[t] += f * dy;
+      fz[t] += f * dz;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(P2P_TPB) k_p2p_free(const uint32_t *d_nb, const uint64_t *bkey,
+                                                      const uint32_t *bstart, const uint32_t *bcount,
+                                                      const int32_t *ulist, const double *x, const double *y,
+                                                      const double *z, const double *q, const uint32_t *src,
+                                                      Geo geo, double lam, double scale, double *phi,
+                                                      double *field) {
   constexpr bool comp = sizeof(T) == 4;
-  __shared__ T sx[P2P_THREADS], sy[P2P_THREADS], sz[P2P_THREADS], sq[P2P_THREADS];
-  __shared__ T lx[P2P_THREADS], ly[P2P_THREADS], lz[P2P_THREADS];
-  __shared__ uint32_t sk[P2P_THREADS];
+  __shared__ V4<T> sh[P2P_SRC], sl[comp ? P2P_SRC : 1];
+  __shared__ uint32_t nb_start[NNEAR], nb_pre[NNEAR + 1];
   const uint32_t box = blockIdx.x;
   if (box >= *d_nb) return;
   double cx, cy, cz;
   box_center(bkey[box], geo, cx, cy, cz);
-  const uint32_t tst = bstart[box], tcnt = bcount[box];
-  const T tl = (T)lam;
-  for (uint32_t t0 = 0; t0 < tcnt; t0 += P2P_THREADS) {
-    const uint32_t tj = t0 + threadIdx.x;
-    const bool tv = tj < tcnt;
-    const uint32_t tk = tst + (tv ? tj : 0);
-    const double ox = x[tk] - cx, oy = y[tk] - cy, oz = z[tk] - cz;
-    const T px = (T)ox, py = (T)oy, pz = (T)oz;
-    const T plx = comp ? (T)(ox - (double)px) : T(0), ply = comp ? (T)(oy - (double)py) : T(0),
-            plz = comp ? (T)(oz - (double)pz) : T(0);
-    double aphi = 0, ax = 0, ay = 0, az = 0;
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
     for (int o = 0; o < NNEAR; ++o) {
       const int s = ulist[(size_t)box * NNEAR + o];
-      if (s < 0) continue;
-      const uint32_t sst = bstart[s], scnt = bcount[s];
-      T fphi = 0, fx = 0, fy = 0, fz = 0;
-      for (uint32_t s0 = 0; s0 < scnt; s0 += P2P_THREADS) {
-        __syncthreads();
-        if (s0 + threadIdx.x < scnt) {
-          const uint32_t k = sst + s0 + threadIdx.x;
-          const double qx = x[k] - cx, qy = y[k] - cy, qz = z[k] - cz;
-          const T hx = (T)qx, hy = (T)qy, hz = (T)qz;
-          sx[threadIdx.x] = hx;
-          sy[threadIdx.x] = hy;
-          sz[threadIdx.x] = hz;
+      nb_pre[o] = acc;
+      nb_start[o] = s < 0 ? 0u : bstart[s];
+      acc += s < 0 ? 0u : bcount[s];
+    }
+    nb_pre[NNEAR] = acc;
+  }
+  __syncthreads();
+  const uint32_t stot = nb_pre[NNEAR];
+  const uint32_t tst = bstart[box], tcnt = bcount[box];
+  const T tl = (T)lam;
+  const unsigned full = 0xffffffffu;
+  for (uint32_t t0 = 0; t0 < tcnt; t0 += 2 * P2P_TPB) {
+    T px[2], py[2], pz[2], qx[2], qy[2], qz[2];
+    bool tv[2];
+    uint32_t tk[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t tj = t0 + threadIdx.x + t * P2P_TPB;
+      tv[t] = tj < tcnt;
+      tk[t] = tst + (tv[t] ? tj : 0);
+      const double ox = x[tk[t]] - cx, oy = y[tk[t]] - cy, oz = z[tk[t]] - cz;
+      px[t] = (T)ox;
+      py[t] = (T)oy;
+      pz[t] = (T)oz;
+      qx[t] = comp ? (T)(ox - (double)px[t]) : T(0);
+      qy[t] = comp ? (T)(oy - (double)py[t]) : T(0);
+      qz[t] = comp ? (T)(oz - (double)pz[t]) : T(0);
+    }
+    const bool w2 = __any_sync(full, tv[1]), w1 = __any_sync(full, tv[0]);
+    double aphi[2] = {0, 0}, ax[2] = {0, 0}, ay[2] = {0, 0}, az[2] = {0, 0};
+    for (uint32_t s0 = 0; s0 < stot; s0 += P2P_SRC) {
+      __syncthreads();
+      for (uint32_t jj = threadIdx.x; jj < P2P_SRC; jj += P2P_TPB) {
+        const uint32_t g = s0 + jj;
+        if (g < stot) {
+          int o = 0;
+          while (nb_pre[o + 1] <= g) ++o;  // neighbour holding source g (empty ones skipped)
+          const uint32_t k = nb_start[o] + (g - nb_pre[o]);
+          const double ux = x[k] - cx, uy = y[k] - cy, uz = z[k] - cz;
+          V4<T> h;
+          h.x = (T)ux;
+          h.y = (T)uy;
+          h.z = (T)uz;
+          h.w = (T)q[k];
+          sh[jj] = h;
           if (comp) {
-            lx[threadIdx.x] = (T)(qx - (double)hx);
-            ly[threadIdx.x] = (T)(qy - (double)hy);
-            lz[threadIdx.x] = (T)(qz - (double)hz);
-          }
-          sq[threadIdx.x] = (T)q[k];
-          sk[threadIdx.x] = k;
-        }
-        __syncthreads();
-        const uint32_t nn = min((uint32_t)P2P_THREADS, scnt - s0);
-        if (tv) {
-          for (uint32_t jj = 0; jj < nn; ++jj) {
-            T dx = px - sx[jj], dy = py - sy[jj], dz = pz - sz[jj];
-            if (comp) {
-              dx += plx - lx[jj];
-              dy += ply - ly[jj];
-              dz += plz - lz[jj];
-            }
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            if (sk[jj] == tk || r2 == T(0)) continue;
-            const T ri = frsqrt(r2);
-            const T r = r2 * ri;
-            const T e = sq[jj] * fexp(-tl * r) * ri;
-            fphi += e;
-            const T f = e * (T(1) + tl * r) * ri * ri;
-            fx += f * dx;
-            fy += f * dy;
-            fz += f * dz;
+            V4<T> lo;
+            lo.x = (T)(ux - (double)h.x);
+            lo.y = (T)(uy - (double)h.y);
+            lo.z = (T)(uz - (double)h.z);
+            lo.w = T(0);
+            sl[jj] = lo;
           }
         }
       }
-      aphi += (double)fphi;
-      ax += (double)fx;
-      ay += (double)fy;
-      az += (double)fz;
+      __syncthreads();
+      const int nn = (int)min((uint32_t)P2P_SRC, stot - s0);
+      T fp[2] = {0, 0}, fx[2] = {0, 0}, fy[2] = {0, 0}, fz[2] = {0, 0};
+      if (w2) p2p_free_tile<T, 2, comp>(sh, sl, nn, px, py, pz, qx, qy, qz, tl, fp, fx, fy, fz);
+      else if (w1) p2p_free_tile<T, 1, comp>(sh, sl, nn, px, py, pz, qx, qy, qz, tl, fp, fx, fy, fz);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        aphi[t] += (double)fp[t];
+        ax[t] += (double)fx[t];
+        ay[t] += (double)fy[t];
+        az[t] += (double)fz[t];
+      }
     }
-    if (tv) {
-      const uint32_t i = src[tk];
-      phi[i] += scale * aphi;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (!tv[t]) continue;
+      const uint32_t i = src[tk[t]];
+      phi[i] += scale * aphi[t];
       if (field) {
-        field[3 * i] += scale * ax;
-        field[3 * i + 1] += scale * ay;
-        field[3 * i + 2] += scale * az;
+        field[3 * i] += scale * ax[t];
+        field[3 * i + 1] += scale * ay[t];
+        field[3 * i + 2] += scale * az[t];
       }
     }
   }
@@ -732,7 +1021,9 @@ static void make_tables(Ctx &c) {
   (void)c;
 }
 
+void upload_gl16();
 void init_fmm_tables(Ctx &c) {
+  upload_gl16();
   make_tables(c);
   upload_consts(c.stream);
 }
@@ -850,11 +1141,14 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
   const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
   std::vector<XJob> jobs;
   int64_t items = 0;
+  typedef typename C2<T>::t T2;
+  std::vector<RJob> rjobs;
+  int64_t relem = 0;
   auto add = [&](const int32_t *tlist, const uint32_t *d_ntl, int64_t ntb, const int32_t *vlist,
-                 const int32_t *cls_of, const void *M, const void *ops, void *L, int ntypes) {
+                 const int32_t *cls_of, const void *M, const void *ops, void *part, int ntypes, int slot0) {
     XJob j;
     j.tlist = tlist; j.d_ntl = d_ntl; j.ntb = ntb; j.vlist = vlist; j.cls_of = cls_of;
-    j.M = M; j.ops = ops; j.L = L; j.ntypes = ntypes; j.pad = 0; j.item0 = items;
+    j.M = M; j.ops = ops; j.L = part; j.ntypes = ntypes; j.slot0 = slot0; j.item0 = items;
     jobs.push_back(j);
     items += ((ntb + TT - 1) / TT) * M2L_NSLICE;
   };
@@ -863,18 +1157,54 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     const bool react_far = (parts & 2) && g.I.np > 0 && !(parts & 8);
     for (int l = 2; l <= g.D; ++l) {
       const int64_t ntb = g.T.lev[l].n;
-      if (!ntb) continue;
-      if (dofree) add(nullptr, nullptr, ntb, g.vfree[l], tb.cls_free, g.Mfree[l], g.op_free[l], g.Lt[l], 1);
+      if (!ntb || !(dofree || (react_far && g.vreact[l]))) continue;
+      T2 *part = c.arena.get<T2>((size_t)ntb * M2L_NSLOT * c.K);
+      LPB_CUDA(cudaMemsetAsync(part, 0, sizeof(T2) * ntb * M2L_NSLOT * c.K, c.stream));
+      RJob r;
+      r.part = part; r.L = g.Lt[l]; r.n = ntb * c.K; r.e0 = relem;
+      rjobs.push_back(r);
+      relem += r.n;
+      if (dofree) add(nullptr, nullptr, ntb, g.vfree[l], tb.cls_free, g.Mfree[l], g.op_free[l], part, 1, 0);
       if (react_far && g.vreact[l])
         for (int kt = 0; kt < 3; ++kt)
           add(g.rows[l] + (size_t)kt * ntb, g.nrows[l] + kt, ntb, g.vreact[l],
-              tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], g.Lt[l], g.ntypes);
+              tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], part, g.ntypes, M2L_NSLICE);
     }
   }
   if (jobs.empty()) return;
+  auto launch_reduce = [&]() {
+    RJob *dr = c.arena.get<RJob>(rjobs.size());
+    LPB_CUDA(cudaMemcpyAsync(dr, rjobs.data(), sizeof(RJob) * rjobs.size(), cudaMemcpyHostToDevice, c.stream));
+    k_m2l_reduce<T><<<(unsigned)((relem + 255) / 256), 256, 0, c.stream>>>(dr, (int)rjobs.size(), c.K);
+    LPB_LAUNCH();
+    c.launches++;
+  };
+  if (sizeof(T) == 4 && c.K <= F32_KR) {
+    // re-count items with the larger tile of the asynchronous FP32 kernel
+    int64_t it = 0;
+    for (auto &j : jobs) {
+      j.item0 = it;
+      it += ((j.ntb + F32_TT - 1) / F32_TT) * M2L_NSLICE;
+    }
+    const size_t smem = m2l_f32_smem(c.K);
+    static bool attr = false;
+    if (!attr) {  // the largest K of this kernel
+      LPB_CUDA(cudaFuncSetAttribute(k_m2l_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)m2l_f32_smem(F32_KR)));
+      attr = true;
+    }
+    XJob *dj = c.arena.get<XJob>(jobs.size());
+    LPB_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(XJob) * jobs.size(), cudaMemcpyHostToDevice, c.stream));
+    k_m2l_f32<<<(unsigned)it, 256, smem, c.stream>>>(dj, (int)jobs.size(), (const float *)tb.rot, c.K);
+    LPB_LAUNCH();
+    c.launches++;
+    launch_reduce();
+    return;
+  }
   if (c.K <= 80) launch_m2l_t<T, TPT, 5>(c, jobs, items);
   else if (c.K <= 128) launch_m2l_t<T, TPT, 8>(c, jobs, items);
   else launch_m2l_t<T, TPT, 10>(c, jobs, items);
+  launch_reduce();
 }
 
 // L2L (adding the parent's shifted expansion), L2P and the near fields of one group
@@ -897,7 +1227,7 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   }
   PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
   if (dofree) {
-    k_p2p_free<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(
+    k_p2p_free<T><<<(unsigned)g.T.lev[D].n, P2P_TPB, 0, c.stream>>>(
         g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q,
         g.T.src, geo_at<T>(g, D), c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
     LPB_LAUNCH();

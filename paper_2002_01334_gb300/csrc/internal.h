@@ -112,6 +112,7 @@ struct Ctx {
   // constant tables (device, FP64)
   double *gaunt = nullptr;   // [(p+1)^2 in][(p+1)^2 out][2p+1]
   double *tpoly = nullptr;   // [K][TPK] Legendre-product coefficients
+  double *sfac = nullptr;    // [KMAX_TAB+1][KMAX_TAB+1]: sqrt((K+d)! (K-d)!) for d <= K
   int tpk = 0;
   int *status = nullptr;     // device status word
   int *h_status = nullptr;   // pinned

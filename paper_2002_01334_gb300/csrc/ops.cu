@@ -26,10 +26,10 @@ struct OpDesc {
   int64_t dst;  // element offset of P (Q follows after K*K)
 };
 
+// half-representation index o = n(n+1)/2 + m -> (n, m), integer arithmetic only
 __device__ __forceinline__ void hdecode(int o, int &n, int &m) {
-  n = (int)((sqrt(8.0 * o + 1.0) - 1.0) * 0.5);
+  n = 0;
   while ((n + 1) * (n + 2) / 2 <= o) ++n;
-  while (n * (n + 1) / 2 > o) --n;
   m = o - n * (n + 1) / 2;
 }
 
@@ -106,7 +106,6 @@ __constant__ double c_rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
 __constant__ int c_kk_t[NKK] = {0, 0, 1, 0, 1, 2};
 __constant__ int c_kk_s[NKK] = {0, 1, 0, 2, 1, 0};
 
-constexpr int QCHUNK = 256;
 constexpr int MAXPANEL = 1024;
 
 __device__ __forceinline__ int stab_index(int KT, int K, int d, int ij) { return ((K * (KT + 1)) + d) * 4 + ij; }
@@ -125,107 +124,199 @@ __device__ void make_panels(double umax, double wmax, double lmin, double *pu, d
   *np = n;
 }
 
-// Gauss-Legendre 16-point rule on [-1,1], nodes by Newton iteration (shared by the kernels)
-__device__ void gl16(double *x, double *w) {
+// Gauss-Legendre 16-point rule on [-1,1] (nodes by Newton iteration on the host)
+__constant__ double c_glx[16], c_glw[16];
+static bool g_gl_ready = false;
+void upload_gl16() {
+  if (g_gl_ready) return;
+  double x[16], w[16];
   for (int i = 0; i < 16; ++i) {
-    double z = cos(PI * (i + 0.75) / 16.5), dp = 1.0;
+    long double z = cosl(3.14159265358979323846264338L * (i + 0.75L) / 16.5L), dp = 1;
     for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int k = 2; k <= 16; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
-      dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
+      long double p0 = 1, p1 = z;
+      for (int k = 2; k <= 16; ++k) { long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+      dp = 16 * (z * p1 - p0) / (z * z - 1);
+      const long double dz = p1 / dp;
       z -= dz;
-      if (fabs(dz) < 1e-16) break;
+      if (fabsl(dz) < 1e-19L) break;
     }
-    double p0 = 1.0, p1 = z;
-    for (int k = 2; k <= 16; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
-    dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    long double p0 = 1, p1 = z;
+    for (int k = 2; k <= 16; ++k) { long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+    dp = 16 * (z * p1 - p0) / (z * z - 1);
+    x[i] = (double)z;
+    w[i] = (double)(2 / ((1 - z * z) * dp * dp));
+  }
+  LPB_CUDA(cudaMemcpyToSymbol(c_glx, x, sizeof x));
+  LPB_CUDA(cudaMemcpyToSymbol(c_glw, w, sizeof w));
+  g_gl_ready = true;
+}
+__device__ __forceinline__ void gl16(double *x, double *w) {
+  for (int i = 0; i < 16; ++i) { x[i] = c_glx[i]; w[i] = c_glw[i]; }
+}
+
+// Quadrature of S^K S_{K d, ij} for d = 0, 1, K = 0..KT on one composite Gauss-Legendre node
+// set per (component, level) in u = lambda_rho h: panel width min(2/zeta_min, pi/rho_max),
+// graded near u = 0 to resolve the branch points at u = +-i Lambda.  Node data (first kernel):
+//   nd[q] = {u, w sigma / u_z, Lam / u_z, Lamp / u'_z, e^{-u_z (k+1/2)} (k=0..2),
+//            e^{-u'_z (k+1/2)} (k=0..2), J0(u rho_r), J1(u rho_r) (r = 0..9)}
+constexpr int NDF = 10 + 2 * NRHO;
+
+// host: the u beyond which u^KT e^{-zeta u} has fallen by tol (and e^-3 more) below its peak
+// at u = KT/zeta
+static double node_umax(int KT, double zeta, double tol) {
+  const double pk = fmax(KT / zeta, 1.0 / zeta);
+  const double target = KT * log(pk) - zeta * pk + log(tol) - 3.0;
+  double umax = pk;
+  while (KT * log(umax) - zeta * umax > target) umax += 0.25 / zeta;
+  return umax;
+}
+
+struct NDesc {
+  double umax, wmax, lmin;
+  double ucut[3];  // truncation point for zeta = 1, 2, 3 (zeta = k_t + k_s + 1)
+  int npan, nq;
+  double *nodes;  // [nq][NDF]
+};
+
+__global__ void k_stab_nodes(const RDesc *descs, const NDesc *nds, Medium md) {
+  const RDesc D = descs[blockIdx.y];
+  const NDesc N = nds[blockIdx.y];
+  __shared__ double pu[MAXPANEL], pw[MAXPANEL];
+  __shared__ int npan;
+  if (threadIdx.x == 0) make_panels(N.umax, N.wmax, N.lmin, pu, pw, &npan);
+  __syncthreads();
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N.nq; j += gridDim.x * blockDim.x) {
+    double *o = N.nodes + (size_t)j * NDF;
+    if (j >= npan * 16) {
+      for (int k = 0; k < NDF; ++k) o[k] = 0.0;
+      continue;
+    }
+    const int pi_ = j >> 4, gi = 15 - (j & 15);  // ascending abscissae
+    const double u = pu[pi_] + 0.5 * pw[pi_] * (c_glx[gi] + 1.0);
+    const double w = 0.5 * pw[pi_] * c_glw[gi];
+    const double sg = layer_sigma(md, u / D.h, D.l, D.a, D.lp, D.b);
+    const double uz = sqrt(D.Lam * D.Lam + u * u), uzp = sqrt(D.Lamp * D.Lamp + u * u);
+    o[0] = u;
+    o[1] = w * sg / uz;
+    o[2] = D.Lam / uz;
+    o[3] = D.Lamp / uzp;
+    for (int k = 0; k < 3; ++k) {
+      o[4 + k] = exp(-uz * (k + 0.5));
+      o[7 + k] = exp(-uzp * (k + 0.5));
+    }
+    for (int r = 0; r < NRHO; ++r) {
+      const double x = u * sqrt(c_rho2[r]);
+      o[10 + r] = j0(x);
+      o[10 + NRHO + r] = j1(x);
+    }
   }
 }
 
-// quadrature of S^K S_{K d, ij} for d = 0, 1, K = 0..KT (block = 256 threads, 8 warps)
-__global__ void k_stab_quad(const RDesc *descs, Medium md, int KT, double tol) {
+// One CTA per used class.  Per chunk of 256 nodes the power columns u^K (K = 0..KT) and the
+// eight node values v_{d,ij} = w sigma/u_z (Lam/u_z)^i (Lamp/u'_z)^j Z_{kt,ks} J_d(u rho) are
+// staged in shared memory; thread (d, i, j, K) accumulates sum_q u_q^K v_{d,ij}(q), a
+// [KT+1 x Q] x [Q x 8] product in FP64, for the entries with K - d odd: the operators use
+// only those, because K = 1 + |m| + |mu| + 2s and d = |mu - m| differ by an odd number.
+constexpr int SQ_CHUNK = 256, SQ_LD = SQ_CHUNK + 1;
+__global__ void k_stab_quad(const RDesc *descs, const NDesc *nds, int KT, const double *sfac) {
   const RDesc D = descs[blockIdx.y];
+  const NDesc N = nds[blockIdx.y];
   const int cls = blockIdx.x;
   if (D.used && !D.used[cls]) return;
-  __shared__ double pu[MAXPANEL], pw[MAXPANEL];
-  __shared__ double gx[16], gw[16];
-  __shared__ double g[8][QCHUNK];
-  __shared__ double uu[QCHUNK];
-  __shared__ int npan;
+  extern __shared__ double sqsm[];
+  double *Pw = sqsm;                          // [KT+1][SQ_LD] powers
+  double *V = sqsm + (size_t)(KT + 1) * SQ_LD;  // [8][SQ_LD] node values
   const int ri = cls / NKK, kk = cls % NKK;
-  const double rh = sqrt(c_rho2[ri]);
-  const double zt = c_kk_t[kk] + 0.5, zs = c_kk_s[kk] + 0.5, zeta = zt + zs;
-  if (threadIdx.x == 0) {
-    gl16(gx, gw);
-    // u^KT e^{-zeta u} has fallen by tol below its peak at u = KT/zeta
-    const double pk = fmax(KT / zeta, 1.0 / zeta);
-    const double target = KT * log(pk) - zeta * pk + log(tol) - 3.0;
-    double umax = pk;
-    while (KT * log(umax) - zeta * umax > target) umax += 0.25 / zeta;
-    double wmax = 2.0 / zeta;
-    if (rh > 0.0) wmax = fmin(wmax, PI / rh);
-    make_panels(umax, wmax, fmin(D.Lam, D.Lamp), pu, pw, &npan);
+  const int kt = c_kk_t[kk], ks = c_kk_s[kk];
+  const double ucut = N.ucut[kt + ks];
+  // output of this thread: d, ij, K with K - d odd
+  const int n0 = (KT + 1) / 2, n1 = KT / 2;  // K odd (d = 0): 1,3,..; K even >= 2 (d = 1): 2,4,..
+  const int nout = 4 * (n0 + n1);
+  int od = 0, oij = 0, oK = -1;
+  if ((int)threadIdx.x < nout) {
+    const int t = threadIdx.x;
+    oij = t & 3;
+    const int r = t >> 2;
+    if (r < n0) { od = 0; oK = 2 * r + 1; } else { od = 1; oK = 2 * (r - n0) + 2; }
   }
-  __syncthreads();
-  const int nnodes = npan * 16;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int dsel = warp >> 2, ij = warp & 3;
-  double acc[KMAX_TAB + 1];
-#pragma unroll
-  for (int k = 0; k <= KMAX_TAB; ++k) acc[k] = 0.0;
-  for (int c0 = 0; c0 < nnodes; c0 += QCHUNK) {
-    const int j = c0 + threadIdx.x;
-    if (j < nnodes) {
-      const int pi_ = j >> 4, gi = j & 15;
-      const double u = pu[pi_] + 0.5 * pw[pi_] * (gx[gi] + 1.0);
-      const double w = 0.5 * pw[pi_] * gw[gi];
-      const double sg = layer_sigma(md, u / D.h, D.l, D.a, D.lp, D.b);
-      const double uz = sqrt(D.Lam * D.Lam + u * u), uzp = sqrt(D.Lamp * D.Lamp + u * u);
-      const double base = w * sg * exp(-uz * zt - uzp * zs) / uz;
-      const double fi = D.Lam / uz, fj = D.Lamp / uzp;
-      const double j0v = j0(u * rh), j1v = j1(u * rh);
-      const double f00 = base, f01 = base * fj, f10 = base * fi, f11 = base * fi * fj;
-      g[0][threadIdx.x] = f00 * j0v; g[1][threadIdx.x] = f01 * j0v;
-      g[2][threadIdx.x] = f10 * j0v; g[3][threadIdx.x] = f11 * j0v;
-      g[4][threadIdx.x] = f00 * j1v; g[5][threadIdx.x] = f01 * j1v;
-      g[6][threadIdx.x] = f10 * j1v; g[7][threadIdx.x] = f11 * j1v;
-      uu[threadIdx.x] = u;
+  double acc = 0.0;
+  for (int c0 = 0; c0 < N.nq; c0 += SQ_CHUNK) {
+    const int q = c0 + threadIdx.x;
+    double u = 0.0;
+    if (q < N.nq) {
+      const double *o = N.nodes + (size_t)q * NDF;
+      u = o[0];
+      const double base = o[1] * o[4 + kt] * o[7 + ks];
+      const double j0v = o[10 + ri], j1v = o[10 + NRHO + ri], fi = o[2], fj = o[3];
+      const bool in = u <= ucut && u > 0.0;
+      const double b0 = in ? base * j0v : 0.0, b1 = in ? base * j1v : 0.0;
+      V[0 * SQ_LD + threadIdx.x] = b0;
+      V[1 * SQ_LD + threadIdx.x] = b0 * fj;
+      V[2 * SQ_LD + threadIdx.x] = b0 * fi;
+      V[3 * SQ_LD + threadIdx.x] = b0 * fi * fj;
+      V[4 * SQ_LD + threadIdx.x] = b1;
+      V[5 * SQ_LD + threadIdx.x] = b1 * fj;
+      V[6 * SQ_LD + threadIdx.x] = b1 * fi;
+      V[7 * SQ_LD + threadIdx.x] = b1 * fi * fj;
     } else {
-      for (int k = 0; k < 8; ++k) g[k][threadIdx.x] = 0.0;
-      uu[threadIdx.x] = 0.0;
+      for (int k = 0; k < 8; ++k) V[k * SQ_LD + threadIdx.x] = 0.0;
+    }
+    double pw = 1.0;
+    for (int K = 0; K <= KT; ++K) {
+      Pw[K * SQ_LD + threadIdx.x] = pw;
+      pw *= u;
     }
     __syncthreads();
-    for (int jj = lane; jj < QCHUNK; jj += 32) {
-      const double v = g[warp][jj], u = uu[jj];
-      double pw_ = v;
-#pragma unroll
-      for (int k = 0; k <= KMAX_TAB; ++k) {
-        if (k <= KT) acc[k] += pw_;
-        pw_ *= u;
-      }
+    if (oK >= 0) {
+      const double *pr = Pw + oK * SQ_LD, *vr = V + (od * 4 + oij) * SQ_LD;
+      const int nn = min(SQ_CHUNK, N.nq - c0);
+      for (int j = 0; j < nn; ++j) acc = fma(pr[j], vr[j], acc);
     }
     __syncthreads();
+    if (c0 + SQ_CHUNK < N.nq && N.nodes[(size_t)(c0 + SQ_CHUNK) * NDF] > ucut) break;
   }
-#pragma unroll
-  for (int k = 0; k <= KMAX_TAB; ++k) {
-    double v = acc[k];
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    acc[k] = v;
+  double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  if (oK >= 0) {
+    const double nrm = 1.0 / sfac[oK * (KMAX_TAB + 1) + od];
+    S[stab_index(KT, oK, od, oij)] = acc * nrm;
   }
-  if (lane == 0) {
-    double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
-    // ij index in the table: 2i + j ; warp ij = 2*i + j with f01 = (i=0,j=1)
-#pragma unroll
-    for (int k = 0; k <= KMAX_TAB; ++k) {
-      if (k > KT) break;
-      if (dsel == 1 && k < 1) continue;
-      const double nrm = 1.0 / sqrt(tgamma(k + dsel + 1.0) * tgamma(k - dsel + 1.0));
-      S[stab_index(KT, k, dsel, ij)] = acc[k] * nrm;
-    }
+  // entries with K - d even for d = 0, 1 are not used by the operators: zero
+  for (int e = threadIdx.x; e < (KT + 1) * 2 * 4; e += blockDim.x) {
+    const int K = e / 8, d = (e >> 2) & 1, ij = e & 3;
+    if (((K - d) & 1) == 0 && K >= d) S[stab_index(KT, K, d, ij)] = 0.0;
   }
+}
+static size_t stab_quad_smem(int KT) { return sizeof(double) * (size_t)(KT + 1 + 8) * SQ_LD; }
+
+// host: node set of one (component, level) covering every class (zeta >= 1, rho <= sqrt(18) h)
+// number of panels of the graded rule (host mirror of make_panels)
+static int count_panels(double umax, double wmax, double lmin) {
+  int n = 0;
+  double u = 0.0;
+  while (u < umax && n < MAXPANEL) {
+    double w = fmin(wmax, 0.5 * (lmin + u));
+    if (u + w > umax) w = umax - u;
+    u += w;
+    ++n;
+  }
+  return n;
+}
+
+// Panel width 2 in u = lambda_rho h: with rho <= sqrt(18) the Bessel factor J_d(u rho) has
+// derivatives bounded by rho^n, and the 16-point Gauss rule's error term on a width-2 panel,
+// rho^32 2^33 (16!)^4 / (33 (32!)^3), is ~1e-25 of the integrand's scale; the factors
+// e^{-zeta u} (zeta <= 3) are smoother still.  The panels are graded towards u = 0, where the
+// branch points u = +-i Lambda of u_z sit.
+static NDesc node_desc(int KT, double tol, double Lam, double Lamp) {
+  NDesc N;
+  N.umax = node_umax(KT, 1.0, tol);
+  for (int z = 0; z < 3; ++z) N.ucut[z] = node_umax(KT, z + 1.0, tol);
+  N.wmax = 2.0;
+  N.lmin = fmin(Lam, Lamp);
+  N.npan = count_panels(N.umax, N.wmax, N.lmin);
+  N.nq = N.npan * 16;
+  N.nodes = nullptr;
+  return N;
 }
 
 // forward recurrence in d (Sec. 3.5 eq. recurrence1), one warp per class
@@ -255,6 +346,14 @@ __global__ void k_stab_recur(const RDesc *descs, int KT) {
 // C_s(n,m,nu,mu) = sum_{k+k'=s} c^{nm}_k c^{nu mu}_{k'} Lam^{n-m-2k} Lamp^{nu-mu-2k'}
 __global__ void k_react_coef(const RDesc *descs, const double *tpoly, int tpk, int p, int K) {
   const RDesc D = descs[blockIdx.y];
+  __shared__ double pl[PMAX + 3], plp[PMAX + 3];  // Lam^e, Lamp^e for e = -1..p+1 at index e+1
+  if (threadIdx.x == 0) {
+    pl[0] = 1.0 / D.Lam;
+    plp[0] = 1.0 / D.Lamp;
+    pl[1] = plp[1] = 1.0;
+    for (int e = 2; e <= p + 2; ++e) { pl[e] = pl[e - 1] * D.Lam; plp[e] = plp[e - 1] * D.Lamp; }
+  }
+  __syncthreads();
   const int NS = p + 2;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= K * K) return;
@@ -268,30 +367,33 @@ __global__ void k_react_coef(const RDesc *descs, const double *tpoly, int tpk, i
     for (int k = 0; k <= k1; ++k) {
       const int kp = s - k;
       if (kp < 0 || kp > k2) continue;
-      acc += tpoly[o * tpk + k] * tpoly[i * tpk + kp] * pow(D.Lam, n - m - 2 * k) * pow(D.Lamp, nu - mu - 2 * kp);
+      acc += tpoly[o * tpk + k] * tpoly[i * tpk + kp] * pl[n - m - 2 * k + 1] * plp[nu - mu - 2 * kp + 1];
     }
     D.coef[(size_t)e * NS + s] = acc;
   }
 }
 
 template <typename T>
-__global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, T *out) {
+__global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const double *sfac, T *out) {
   const RDesc D = descs[blockIdx.y];
   const int cls = blockIdx.x;
   if (D.used && !D.used[cls]) return;
-  __shared__ double fac[KMAX_TAB + 1][KMAX_TAB + 1];
-  __shared__ double smm[PMAX + 1];
-  for (int e = threadIdx.x; e < (KT + 1) * (KT + 1); e += blockDim.x) {
-    const int Kk = e / (KT + 1), d = e % (KT + 1);
-    fac[Kk][d] = (d <= Kk) ? sqrt(tgamma(Kk + d + 1.0) * tgamma(Kk - d + 1.0)) : 0.0;
+  extern __shared__ double asm_sm[];
+  double *Sf = asm_sm;  // [(KT+1)^2 * 4]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}
+  __shared__ double smm[PMAX + 1], rdf[PMAX + 1];
+  const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  for (int e = threadIdx.x; e < (KT + 1) * (KT + 1) * 4; e += blockDim.x) {
+    const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
+    Sf[e] = (d <= Kk) ? sfac[Kk * (KMAX_TAB + 1) + d] * S[e] : 0.0;
   }
   if (threadIdx.x == 0) {
     double s = 1.0;
     smm[0] = 1.0;
     for (int m = 1; m <= p; ++m) { s *= -sqrt((2.0 * m + 1.0) / (2.0 * m)); smm[m] = s; }
+    rdf[0] = 1.0;
+    for (int n = 1; n <= p; ++n) rdf[n] = rdf[n - 1] / (2.0 * n + 1.0);  // 1/(2n+1)!!
   }
   __syncthreads();
-  const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   const int NS = p + 2;
   const size_t KK = (size_t)K * K;
   T *P = out + D.dst + (size_t)cls * D.ntypes * 2 * KK;
@@ -300,35 +402,36 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, T *ou
     int n, m, nu, mu;
     hdecode(o, n, m);
     hdecode(i, nu, mu);
-    const int ii = (n - m) & 1, jj = (nu - mu) & 1;
-    double A = smm[m] * smm[mu] / (4.0 * PI) / (dfact2(n) * dfact2(nu)) / D.h;
+    const int ij = 2 * ((n - m) & 1) + ((nu - mu) & 1);
+    double A = smm[m] * smm[mu] * (0.25 / PI) * rdf[n] * rdf[nu] / D.h;
     if ((n - m) & 1) A *= D.st;                 // st^{n-m}
     if ((nu - mu) & 1) A *= -D.st;              // (-st)^{nu-mu}
     const int smax = (n - m + 1) / 2 + (nu - mu + 1) / 2;
-    double r[2] = {0.0, 0.0};
-    for (int sgn = 0; sgn < 2; ++sgn) {
-      if (sgn && mu == 0) break;
-      const int dd = (sgn ? -mu : mu) - m, ad = abs(dd);
-      double acc = 0.0;
-      for (int s = 0; s <= smax; ++s) {
-        const int Kk = 1 + m + mu + 2 * s;
-        if (Kk > KT) break;
-        acc += D.coef[(size_t)e * NS + s] * fac[Kk][ad] * S[stab_index(KT, Kk, ad, 2 * ii + jj)];
-      }
-      if (dd < 0 && (ad & 1)) acc = -acc;
-      r[sgn] = A * acc;
+    const double *cf = D.coef + (size_t)e * NS;
+    const int dp = mu - m, dm = mu + m;  // |d| for +mu and -mu
+    const int adp = dp < 0 ? -dp : dp;
+    double accp = 0.0, accm = 0.0;
+    for (int s = 0; s <= smax; ++s) {
+      const int Kk = 1 + m + mu + 2 * s;
+      if (Kk > KT) break;
+      const double c = cf[s];
+      accp += c * Sf[((Kk * (KT + 1)) + adp) * 4 + ij];
+      accm += c * Sf[((Kk * (KT + 1)) + dm) * 4 + ij];
     }
+    if (dp < 0 && (adp & 1)) accp = -accp;
+    if (dm > 0 && (dm & 1)) accm = -accm;   // d = -mu - m < 0
     double Pv, Qv;
-    if (mu == 0) { Pv = r[0]; Qv = 0.0; }
+    if (mu == 0) { Pv = A * accp; Qv = 0.0; }
     else {
       const double sg = (mu & 1) ? -1.0 : 1.0;
-      Pv = r[0] + sg * r[1];
-      Qv = r[0] - sg * r[1];
+      Pv = A * (accp + sg * accm);
+      Qv = A * (accp - sg * accm);
     }
     P[(size_t)D.tau * 2 * KK + (size_t)o * K + i] = (T)Pv;
     P[(size_t)D.tau * 2 * KK + KK + (size_t)o * K + i] = (T)Qv;
   }
 }
+static size_t assemble_smem(int KT) { return sizeof(double) * (size_t)(KT + 1) * (KT + 1) * 4; }
 
 // near-field reaction quadrature nodes: W = w lr sigma / (4 pi lz_l), lz_l, lz_l'
 __global__ void k_near_nodes(Medium md, int l, int a, int ntypes, double umax, double wmax, double lmin,
@@ -347,7 +450,7 @@ __global__ void k_near_nodes(Medium md, int l, int a, int ntypes, double umax, d
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nq; j += gridDim.x * blockDim.x) {
     double *o = nodes + ((size_t)tau * nq + j) * 4;
     if (j >= npan * 16) { o[0] = o[1] = 0.0; o[2] = o[3] = 1.0; continue; }
-    const int pi_ = j >> 4, gi = j & 15;
+    const int pi_ = j >> 4, gi = 15 - (j & 15);  // ascending abscissae
     const double lr = pu[pi_] + 0.5 * pw[pi_] * (gx[gi] + 1.0);
     const double w = 0.5 * pw[pi_] * gw[gi];
     const double lz = sqrt(md.lam[l] * md.lam[l] + lr * lr), lzp = sqrt(md.lam[lp] * md.lam[lp] + lr * lr);
@@ -358,22 +461,9 @@ __global__ void k_near_nodes(Medium md, int l, int a, int ntypes, double umax, d
   }
 }
 
-// number of panels of the graded rule (host mirror of make_panels)
-static int count_panels(double umax, double wmax, double lmin) {
-  int n = 0;
-  double u = 0.0;
-  while (u < umax && n < MAXPANEL) {
-    double w = fmin(wmax, 0.5 * (lmin + u));
-    if (u + w > umax) w = umax - u;
-    u += w;
-    ++n;
-  }
-  return n;
-}
-
 template <typename T>
 static void build_ops_t(Ctx &c, Group &g, int parts) {
-  const int p = c.p, K = c.K, L = c.md.L;
+  const int p = c.p, K = c.K;
   const size_t KK = (size_t)K * K;
   const double lam_t = c.md.lam[g.l];
   std::vector<OpDesc> descs;
@@ -484,8 +574,31 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
     RDesc *dr = c.arena.get<RDesc>(rd.size());
     LPB_CUDA(cudaMemcpyAsync(dr, rd.data(), sizeof(RDesc) * rd.size(), cudaMemcpyHostToDevice, c.stream));
     const unsigned nd = (unsigned)rd.size();
-    k_stab_quad<<<dim3(NREACT_CLS, nd), 256, 0, c.stream>>>(dr, c.md, KT, fmax(c.tol, 1e-16));
+    const double tol = fmax(c.tol, 1e-16);
+    std::vector<NDesc> nv;
+    int maxq = 0;
+    for (auto &d : rd) {
+      NDesc N = node_desc(KT, tol, d.Lam, d.Lamp);
+      N.nodes = c.arena.get<double>((size_t)N.nq * NDF);
+      maxq = std::max(maxq, N.nq);
+      nv.push_back(N);
+    }
+    NDesc *dn = c.arena.get<NDesc>(nv.size());
+    LPB_CUDA(cudaMemcpyAsync(dn, nv.data(), sizeof(NDesc) * nv.size(), cudaMemcpyHostToDevice, c.stream));
+    k_stab_nodes<<<dim3((unsigned)((maxq + 255) / 256), nd), 256, 0, c.stream>>>(dr, dn, c.md);
     LPB_LAUNCH();
+    {
+      const size_t sm = stab_quad_smem(KT);
+      static bool attr = false;
+      if (!attr) {  // the largest table any order needs
+        LPB_CUDA(cudaFuncSetAttribute(k_stab_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)stab_quad_smem(KMAX_TAB)));
+        attr = true;
+      }
+      k_stab_quad<<<dim3(NREACT_CLS, nd), SQ_CHUNK, sm, c.stream>>>(dr, dn, KT, c.sfac);
+      LPB_LAUNCH();
+    }
+    c.launches += 1;
     k_stab_recur<<<dim3(NREACT_CLS, nd), 32, 0, c.stream>>>(dr, KT);
     LPB_LAUNCH();
     k_react_coef<<<dim3((unsigned)((KK + 255) / 256), nd), 256, 0, c.stream>>>(dr, c.tpoly, c.tpk, p, K);
@@ -496,8 +609,14 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       const int l = rd[first].pad;
       size_t last = first;
       while (last < rd.size() && rd[last].pad == l) ++last;
-      k_react_assemble<T><<<dim3(NREACT_CLS, (unsigned)(last - first)), 256, 0, c.stream>>>(
-          dr + first, p, K, KT, (T *)g.op_react[l]);
+      static bool attr = false;
+      if (!attr) {
+        LPB_CUDA(cudaFuncSetAttribute(k_react_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)assemble_smem(KMAX_TAB)));
+        attr = true;
+      }
+      k_react_assemble<T><<<dim3(NREACT_CLS, (unsigned)(last - first)), 256, assemble_smem(KT), c.stream>>>(
+          dr + first, p, K, KT, c.sfac, (T *)g.op_react[l]);
       LPB_LAUNCH();
       c.launches++;
       first = last;
@@ -558,8 +677,21 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
   d.h = h; d.Lam = c.md.lam[l] * h; d.Lamp = c.md.lam[lp] * h;
   d.used = used; d.stab = stab; d.coef = nullptr; d.dst = 0;
   LPB_CUDA(cudaMemcpyAsync(dr, &d, sizeof(RDesc), cudaMemcpyHostToDevice, c.stream));
-  k_stab_quad<<<dim3(NREACT_CLS, 1), 256, 0, c.stream>>>(dr, c.md, KT, fmax(c.tol, 1e-16));
+  const double tol = fmax(c.tol, 1e-16);
+  NDesc N = node_desc(KT, tol, d.Lam, d.Lamp);
+  NDesc *dn = nullptr;
+  LPB_CUDA(cudaMalloc(&N.nodes, sizeof(double) * (size_t)N.nq * NDF));
+  LPB_CUDA(cudaMalloc(&dn, sizeof(NDesc)));
+  LPB_CUDA(cudaMemcpyAsync(dn, &N, sizeof(NDesc), cudaMemcpyHostToDevice, c.stream));
+  k_stab_nodes<<<dim3((unsigned)((N.nq + 255) / 256), 1), 256, 0, c.stream>>>(dr, dn, c.md);
   LPB_LAUNCH();
+  {
+    const size_t sm = stab_quad_smem(KT);
+    LPB_CUDA(cudaFuncSetAttribute(k_stab_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)stab_quad_smem(KMAX_TAB)));
+    k_stab_quad<<<dim3(NREACT_CLS, 1), SQ_CHUNK, sm, c.stream>>>(dr, dn, KT, c.sfac);
+    LPB_LAUNCH();
+  }
   k_stab_recur<<<dim3(NREACT_CLS, 1), 32, 0, c.stream>>>(dr, KT);
   LPB_LAUNCH();
   std::vector<double> h_out(TS);
@@ -569,6 +701,8 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
   cudaFree(stab);
   cudaFree(used);
   cudaFree(dr);
+  cudaFree(N.nodes);
+  cudaFree(dn);
   // out[((K*(Kmax+1)) + d)*4 + ij] with ij = 2i + j
   for (size_t e = 0; e < TS; ++e) out[e] = h_out[e];
 }

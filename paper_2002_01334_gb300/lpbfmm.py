@@ -54,6 +54,7 @@ def lib():
         L.lpbfmm_debug_stable.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                           C.c_double, C.c_double, C.c_int, dp]
         L.lpbfmm_debug_array.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, C.c_int, vp, i64, C.POINTER(i64)]
+        L.lpbfmm_last_counts.argtypes = [vp, C.POINTER(i64)]
         L.lpbfmm_status.argtypes = [vp]
         L.lpbfmm_strerror.argtypes = [C.c_int]
         L.lpbfmm_strerror.restype = C.c_char_p
@@ -136,6 +137,12 @@ class Context:
                                   _dptr(gq, torch.float64), _dptr(gx, torch.float64))
         _check(rc, "lpbfmm_adjoint")
         return gq, gx
+
+    def counts(self):
+        out = (C.c_int64 * 8)()
+        _check(lib().lpbfmm_last_counts(self.h, out), "lpbfmm_last_counts")
+        keys = ["m2l_free", "m2l_react", "p2p_pairs", "near_react_pairs", "targets", "images", "boxes", "launches"]
+        return dict(zip(keys, list(out)))
 
     def profile(self):
         cap = 64
