@@ -162,6 +162,25 @@ int lpbfmm_debug_stable(lpbfmm_t h, int l, int a, int lp, int b, double hbox, do
                         double zs, int Kmax, double *out);
 
 /*
+ * The table of lpbfmm_debug_stable for one class, computed without allocating: no cudaMalloc,
+ * cudaFree or allocating library call.  The paper has no counterpart; this entry point serves
+ * callers that cannot allocate, e.g. a loop that has given all free device memory to its own
+ * pool, or one that must not suffer the device-wide synchronisation of cudaMalloc/cudaFree.
+ *   out   device array of (Kmax+1)^2 * 4 doubles, same layout as lpbfmm_debug_stable; written
+ *         on the context's stream (the call does not synchronize), owned by the caller.
+ *   Kmax  at most LPBFMM_NOALLOC_KMAX; the class's quadrature may use at most
+ *         LPBFMM_NOALLOC_NQ nodes.  Larger requests return LPBFMM_ERR_UNSUPPORTED.
+ * Temporaries live in one fixed device array of about 2.1 MB per device, whose address is
+ * looked up on the first call on each device: make that first call before any stream capture.
+ * Calls that overlap in time on one device (other streams, other contexts) share that array
+ * and race; serialize them.  Other errors as lpbfmm_debug_stable.
+ */
+#define LPBFMM_NOALLOC_KMAX 23   /* = 2p + 3 at p = 10 */
+#define LPBFMM_NOALLOC_NQ 4096
+int lpbfmm_stable_noalloc(lpbfmm_t h, int l, int a, int lp, int b, double hbox, double rho, double zt,
+                          double zs, int Kmax, double *out);
+
+/*
  * Diagnostics: after an lpbfmm_eval, copy an intermediate device array of group (l, a) at
  * level lev into the host buffer dst (capacity cap bytes); *bytes receives its size.  Names:
  * "Mimg", "Mfree", "Lt" (expansions, complex, working precision), "op_react", "op_free"

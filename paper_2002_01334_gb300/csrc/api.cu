@@ -720,4 +720,20 @@ int lpbfmm_debug_stable(lpbfmm_t h, int l, int a, int lp, int b, double hbox, do
   return LPBFMM_OK;
 }
 
+int lpbfmm_stable_noalloc(lpbfmm_t h, int l, int a, int lp, int b, double hbox, double rho, double zt, double zs,
+                          int Kmax, double *out) {
+  if (!h || !out || Kmax < 0 || !(hbox > 0)) return LPBFMM_ERR_ARG;
+  if (l < 0 || l > h->md.L || lp < 0 || lp > h->md.L || (a == 1 && l == h->md.L) || (a == 2 && l == 0) ||
+      (b == 1 && lp == h->md.L) || (b == 2 && lp == 0) || a < 1 || a > 2 || b < 1 || b > 2)
+    return LPBFMM_ERR_ARG;
+  try {
+    stable_noalloc(*h, l, a, lp, b, hbox, rho, zt, zs, Kmax, out);
+  } catch (const CudaError &e) {
+    return map_error(e);
+  } catch (const StatusError &e) {
+    return e.code;
+  }
+  return LPBFMM_OK;
+}
+
 }  // extern "C"

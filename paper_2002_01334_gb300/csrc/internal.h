@@ -151,6 +151,8 @@ void layer_rank(Ctx &c, int64_t n, const int32_t *layer, int lay, uint32_t *rank
 // ops.cu
 void build_operators(Ctx &c, Group &g, int parts);
 void build_near_nodes(Ctx &c, Group &g, double zeta_min, double rho_max);
+void stable_noalloc(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
+                    double *out);
 void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
                   double *out);
 

@@ -15,6 +15,8 @@
 // phi = sum L~_nm itilde_n(lambda r) R_n^m(r/h) with R_n^m = r^n Y_n^m.
 #include "internal.h"
 
+#include <mutex>
+
 namespace lpb {
 
 struct OpDesc {
@@ -705,6 +707,92 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
   cudaFree(dn);
   // out[((K*(Kmax+1)) + d)*4 + ij] with ij = 2i + j
   for (size_t e = 0; e < TS; ++e) out[e] = h_out[e];
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Sommerfeld table of one class without any allocation.  Callers that cannot allocate: a
+// host loop that has handed all free device memory to its own pool (cudaMalloc would fail),
+// or one sharing the device with latency-critical streams (cudaMalloc and cudaFree may
+// synchronize the whole device).  Every temporary lives in one fixed device array; its
+// address is resolved per device with cudaGetSymbolAddress on the first call on that device.
+// ---------------------------------------------------------------------------------------
+constexpr size_t NA_TS = (size_t)(LPBFMM_NOALLOC_KMAX + 1) * (LPBFMM_NOALLOC_KMAX + 1) * 4;
+constexpr size_t NA_STAB = (size_t)NREACT_CLS * NA_TS;             // doubles, all classes
+constexpr size_t NA_NODES = (size_t)LPBFMM_NOALLOC_NQ * NDF;        // doubles
+constexpr size_t NA_DESC = (sizeof(RDesc) + sizeof(NDesc) + NREACT_CLS + 7) / 8 + 8;
+constexpr size_t NA_DOUBLES = NA_STAB + NA_NODES + NA_DESC;        // ~2.1 MB in all
+static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_addr[64] = {};
+
+static double *noalloc_scratch() {
+  int dev = 0;
+  LPB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    LPB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = (double *)p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+// descriptors, class mask and the class's table are (re)initialised by one launch: the table
+// entries the kernels do not write (d > K, and d >= 2 with K < d + 1) must read as zero
+__global__ void k_noalloc_init(RDesc d, NDesc n, RDesc *rd, NDesc *nd, uint8_t *used, int cls, double *stab_cls,
+                               int ts) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  if (t == 0) {
+    *rd = d;
+    *nd = n;
+  }
+  for (int e = t; e < NREACT_CLS; e += stride) used[e] = (e == cls) ? 1 : 0;
+  for (int e = t; e < ts; e += stride) stab_cls[e] = 0.0;
+}
+
+void stable_noalloc(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
+                    double *out) {
+  if (Kmax > LPBFMM_NOALLOC_KMAX) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+  const double rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+  const double r2 = (rho / h) * (rho / h);
+  int ri = -1;
+  for (int k = 0; k < NRHO; ++k)
+    if (fabs(r2 - rho2[k]) < 1e-9) ri = k;
+  const int kt = (int)llround(zt / h - 0.5), ks = (int)llround(zs / h - 0.5);
+  const int kkt[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
+  if (ri < 0 || kt < 0 || ks < 0 || kt + ks > 2 || fabs(zt / h - 0.5 - kt) > 1e-9 || fabs(zs / h - 0.5 - ks) > 1e-9)
+    throw StatusError{LPBFMM_ERR_ARG};
+  const int cls = ri * NKK + kkt[kt][ks];
+  const int KT = Kmax;
+  const size_t TS = (size_t)(KT + 1) * (KT + 1) * 4;
+  RDesc d;
+  d.l = l; d.a = a; d.lp = lp; d.b = b; d.tau = 0; d.ntypes = 1; d.st = a == 1 ? -1 : 1; d.pad = 0;
+  d.h = h; d.Lam = c.md.lam[l] * h; d.Lamp = c.md.lam[lp] * h;
+  d.coef = nullptr; d.dst = 0;
+  NDesc N = node_desc(KT, fmax(c.tol, 1e-16), d.Lam, d.Lamp);
+  if (N.nq > LPBFMM_NOALLOC_NQ) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+  double *base = noalloc_scratch();
+  double *stab = base, *nodes = base + NA_STAB;
+  RDesc *dr = (RDesc *)(nodes + NA_NODES);
+  NDesc *dn = (NDesc *)((char *)dr + ((sizeof(RDesc) + 15) / 16) * 16);
+  uint8_t *used = (uint8_t *)((char *)dn + ((sizeof(NDesc) + 15) / 16) * 16);
+  d.used = used;
+  d.stab = stab;
+  N.nodes = nodes;
+  k_noalloc_init<<<8, 256, 0, c.stream>>>(d, N, dr, dn, used, cls, stab + (size_t)cls * TS, (int)TS);
+  LPB_LAUNCH();
+  k_stab_nodes<<<dim3((unsigned)((N.nq + 255) / 256), 1), 256, 0, c.stream>>>(dr, dn, c.md);
+  LPB_LAUNCH();
+  LPB_CUDA(cudaFuncSetAttribute(k_stab_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stab_quad_smem(KMAX_TAB)));
+  k_stab_quad<<<dim3(NREACT_CLS, 1), SQ_CHUNK, stab_quad_smem(KT), c.stream>>>(dr, dn, KT, c.sfac);
+  LPB_LAUNCH();
+  k_stab_recur<<<dim3(NREACT_CLS, 1), 32, 0, c.stream>>>(dr, KT);
+  LPB_LAUNCH();
+  LPB_CUDA(cudaMemcpyAsync(out, stab + (size_t)cls * TS, sizeof(double) * TS, cudaMemcpyDeviceToDevice, c.stream));
 }
 
 }  // namespace lpb

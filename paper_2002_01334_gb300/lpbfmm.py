@@ -53,6 +53,8 @@ def lib():
                                          C.POINTER(i64), vp, vp]
         L.lpbfmm_debug_stable.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                           C.c_double, C.c_double, C.c_int, dp]
+        L.lpbfmm_stable_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                            C.c_double, C.c_double, C.c_int, vp]
         L.lpbfmm_debug_array.argtypes = [vp, C.c_int, C.c_int, C.c_char_p, C.c_int, vp, i64, C.POINTER(i64)]
         L.lpbfmm_last_counts.argtypes = [vp, C.POINTER(i64)]
         L.lpbfmm_status.argtypes = [vp]
@@ -196,6 +198,15 @@ class Context:
         _check(lib().lpbfmm_debug_stable(self.h, l, a, lp, b, float(h), float(rho), float(zt), float(zs), Kmax,
                                          out.ctypes.data_as(C.POINTER(C.c_double))), "lpbfmm_debug_stable")
         return out.reshape(Kmax + 1, Kmax + 1, 2, 2)
+
+    def stable_noalloc(self, l, a, lp, b, h, rho, zt, zs, Kmax, out):
+        """lpbfmm_stable_noalloc into the CUDA float64 tensor out ((Kmax+1)^2*4 elements), on
+        the context's stream; the table of debug_stable computed without any allocation."""
+        if out.dtype != torch.float64 or not out.is_cuda or out.numel() != (Kmax + 1) * (Kmax + 1) * 4:
+            raise ValueError("out must be a CUDA float64 tensor of (Kmax+1)^2*4 elements")
+        _check(lib().lpbfmm_stable_noalloc(self.h, l, a, lp, b, float(h), float(rho), float(zt), float(zs), Kmax,
+                                           C.c_void_p(out.data_ptr())), "lpbfmm_stable_noalloc")
+        return out
 
 
 def eval_batched(ctxs, offsets, q, xyz, layer, field=True):
