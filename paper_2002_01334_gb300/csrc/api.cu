@@ -81,6 +81,43 @@ static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w
 // G[a][c][q] = int Y_a^alpha Y_q^{gamma-alpha} conj(Y_c^gamma) dOmega (all real), full indices a, c
 // sqrt((K+d)! (K-d)!) for 0 <= d <= K <= KMAX_TAB, the normalisation of the scaled
 // Sommerfeld tables (long double products, then rounded once)
+// Phat_q^k(cos theta), q <= 2p, of the 72 translation directions: the free-space M2L classes
+// (rho^2 index ri, dz) at index ri * 7 + dz + 3, b = (rho, 0, -dz), and the child-parent
+// directions b = (1, 1, -1) / (1, 1, 1) (index 70, 71).  Orthonormal, Condon-Shortley phase,
+// by the standard three-term recurrences in long double.
+static std::vector<double> phat_dir_table(int p) {
+  const int qmax = 2 * p, npl = (qmax + 1) * (qmax + 2) / 2;
+  const long double rho2[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+  std::vector<double> out((size_t)72 * npl, 0.0);
+  auto idx = [](int q, int k) { return q * (q + 1) / 2 + k; };
+  for (int dir = 0; dir < 72; ++dir) {
+    long double x;
+    if (dir < 70) {
+      const int ri = dir / 7, dz = dir % 7 - 3;
+      const long double bz = -dz, bn = sqrtl(rho2[ri] + (long double)dz * dz);
+      x = bn > 0 ? bz / bn : 1.0L;
+    } else {
+      x = (dir == 70 ? -1.0L : 1.0L) / sqrtl(3.0L);
+    }
+    std::vector<long double> P(npl, 0.0L);
+    const long double s = sqrtl(fmaxl(0.0L, 1.0L - x * x));
+    P[0] = 0.5L / sqrtl(3.14159265358979323846264338L);
+    for (int k = 1; k <= qmax; ++k) P[idx(k, k)] = -sqrtl((2.0L * k + 1) / (2.0L * k)) * s * P[idx(k - 1, k - 1)];
+    for (int k = 0; k < qmax; ++k) {
+      P[idx(k + 1, k)] = sqrtl(2.0L * k + 3) * x * P[idx(k, k)];
+      for (int q = k + 2; q <= qmax; ++q) {
+        const long double qq = (long double)q * q - (long double)k * k;
+        const long double a = sqrtl((4.0L * q * q - 1) / qq);
+        const long double b = sqrtl(((q - 1.0L) * (q - 1.0L) - (long double)k * k) * (2.0L * q + 1) /
+                                    ((2.0L * q - 3) * qq));
+        P[idx(q, k)] = a * x * P[idx(q - 1, k)] - b * P[idx(q - 2, k)];
+      }
+    }
+    for (int e = 0; e < npl; ++e) out[(size_t)dir * npl + e] = (double)P[e];
+  }
+  return out;
+}
+
 static std::vector<double> sfac_table() {
   const int n = KMAX_TAB + 1;
   std::vector<long double> f(2 * n + 1);
@@ -380,6 +417,9 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     std::vector<double> sf = sfac_table();
     LPB_CUDA(cudaMalloc(&c->sfac, sizeof(double) * sf.size()));
     LPB_CUDA(cudaMemcpy(c->sfac, sf.data(), sizeof(double) * sf.size(), cudaMemcpyHostToDevice));
+    std::vector<double> pd = phat_dir_table(p);
+    LPB_CUDA(cudaMalloc(&c->phat_dir, sizeof(double) * pd.size()));
+    LPB_CUDA(cudaMemcpy(c->phat_dir, pd.data(), sizeof(double) * pd.size(), cudaMemcpyHostToDevice));
     LPB_CUDA(cudaMalloc(&c->status, sizeof(int)));
     LPB_CUDA(cudaMemset(c->status, 0, sizeof(int)));
     LPB_CUDA(cudaMallocHost(&c->h_pinned, 1 << 16));
@@ -489,6 +529,7 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (h->gaunt) cudaFree(h->gaunt);
   if (h->tpoly) cudaFree(h->tpoly);
   if (h->sfac) cudaFree(h->sfac);
+  if (h->phat_dir) cudaFree(h->phat_dir);
   if (h->status) cudaFree(h->status);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int k = 0; k < 64; ++k)

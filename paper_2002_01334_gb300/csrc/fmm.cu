@@ -5,6 +5,7 @@
 //   M~_nm = sum_j q_j 4 pi itilde_n(lambda r_j) conj(R_n^m(r_j / h)),
 //   phi(r) = sum_n [L~_n0 itilde_n R_n^0 + 2 Re sum_{m>0} L~_nm itilde_n R_n^m](r / h).
 #include "internal.h"
+#include "tc.cuh"
 
 namespace lpb {
 
@@ -256,7 +257,32 @@ struct XJob {
   void *L;                // partial sums [ntb][M2L_NSLOT][K]: slot = slot0 + dx-slice
   int ntypes, slot0;
   int64_t item0;          // first work item of this job
+  // octant tiles (free-space jobs at levels >= 3): tile = (octant, run of parents); its slot j
+  // holds the child of parent j with that octant.  Boxes of one octant share their far offsets.
+  const uint32_t *pstart; // parents' first child (nullptr: plain tiles over tlist / 0..ntb-1)
+  const uint32_t *pcount;
+  const uint64_t *ckey;   // keys of the target level
+  int64_t npar;
 };
+
+__host__ __device__ __forceinline__ int64_t m2l_tiles(const XJob &J, int TT) {
+  return J.pstart ? 8 * ((J.npar + TT - 1) / TT) : (J.ntb + TT - 1) / TT;
+}
+
+// target box of slot j of tile ti, or -1
+__device__ __forceinline__ int m2l_target(const XJob &J, int64_t ti, int j, int TT, int64_t ntl) {
+  if (J.pstart) {
+    const int oct = (int)(ti & 7);
+    const int64_t P = (ti >> 3) * TT + j;
+    if (P >= J.npar) return -1;
+    const uint32_t s0 = J.pstart[P], n = J.pcount[P];
+    for (uint32_t k = 0; k < n; ++k)
+      if ((int)(J.ckey[s0 + k] & 7ull) == oct) return (int)(s0 + k);
+    return -1;
+  }
+  const int64_t t = ti * TT + j;
+  return t < ntl ? (J.tlist ? J.tlist[t] : (int)t) : -1;
+}
 constexpr int M2L_NSLOT = 2 * M2L_NSLICE;  // free-space slices, then reaction slices
 
 template <typename T>
@@ -285,18 +311,15 @@ __global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const 
   const XJob J = jobs[lo];
   const int64_t local = (int64_t)blockIdx.x - J.item0;
   const int slice = (int)(local % M2L_NSLICE);
-  const int64_t tile0 = (local / M2L_NSLICE) * TT;
+  const int64_t ti = local / M2L_NSLICE;
   const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
-  if (tile0 >= ntl) return;
+  if (J.pstart ? (ti >> 3) * TT >= J.npar : ti * TT >= ntl) return;
   const T2 *M = (const T2 *)J.M;
   const T *ops = (const T *)J.ops;
   T2 *L = (T2 *)J.L;
   const int ntypes = J.ntypes;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  if (threadIdx.x < TT) {
-    const int64_t j = tile0 + threadIdx.x;
-    tid_[threadIdx.x] = (j < ntl) ? (J.tlist ? J.tlist[j] : (int)j) : -1;
-  }
+  if (threadIdx.x < TT) tid_[threadIdx.x] = m2l_target(J, ti, threadIdx.x, TT, ntl);
   T Lr[NR][TPT], Li[NR][TPT];
 #pragma unroll
   for (int r = 0; r < NR; ++r)
@@ -446,19 +469,16 @@ __global__ void __launch_bounds__(256, 1) k_m2l_f32(const XJob *jobs, int njobs,
   const XJob J = jobs[lo];
   const int64_t local = (int64_t)blockIdx.x - J.item0;
   const int slice = (int)(local % M2L_NSLICE);
-  const int64_t tile0 = (local / M2L_NSLICE) * F32_TT;
+  const int64_t ti = local / M2L_NSLICE;
   const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
-  if (tile0 >= ntl) return;
+  if (J.pstart ? (ti >> 3) * F32_TT >= J.npar : ti * F32_TT >= ntl) return;
   const float2 *M = (const float2 *)J.M;
   const float *ops = (const float *)J.ops;
   float2 *L = (float2 *)J.L;
   const int ntypes = J.ntypes;
   const size_t KK = (size_t)K * K;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  if (threadIdx.x < F32_TT) {
-    const int64_t j = tile0 + threadIdx.x;
-    tid_[threadIdx.x] = (j < ntl) ? (J.tlist ? J.tlist[j] : (int)j) : -1;
-  }
+  if (threadIdx.x < F32_TT) tid_[threadIdx.x] = m2l_target(J, ti, threadIdx.x, F32_TT, ntl);
   if (threadIdx.x < 2) hasmask[threadIdx.x] = 0u;
   if (threadIdx.x < F32_KR) mofs[threadIdx.x] = threadIdx.x < K ? cK.mof[threadIdx.x] : 0;
   // zero the operator padding rows K..KR-1 of both stages once
@@ -868,6 +888,218 @@ __global__ void __launch_bounds__(P2P_TPB) k_p2p_free(const uint32_t *d_nb, cons
   }
 }
 
+// Mixed-precision P2P.  Every point of the target tree carries its offset from its own leaf
+// centre as FP32 hi + lo pairs (k_split_points, once per evaluation).  For a neighbour whose
+// centre lies delta * h away (delta in {-1,0,1}^3), the targets are moved into the
+// neighbour's frame by an exact FP32 two-sum with h = hh + hl, so source records are plain
+// copies: they are staged with cp.async, one neighbour chunk ahead of the one being summed.
+// Per-chunk sums are folded into Kahan-compensated FP32 totals; no FP64 in the pair loop.
+__global__ void k_split_points(const uint32_t *d_nb, const uint64_t *bkey, const uint32_t *bstart,
+                               const uint32_t *bcount, const double *x, const double *y, const double *z,
+                               const double *q, Geo geo, float4 *h4, float4 *l4) {
+  const uint32_t box = blockIdx.x;
+  if (box >= *d_nb) return;
+  double cx, cy, cz;
+  box_center(bkey[box], geo, cx, cy, cz);
+  const uint32_t st = bstart[box], cnt = bcount[box];
+  for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const uint32_t k = st + j;
+    const double ox = x[k] - cx, oy = y[k] - cy, oz = z[k] - cz;
+    const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
+    h4[k] = make_float4(hx, hy, hz, (float)q[k]);
+    l4[k] = make_float4((float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
+  }
+}
+
+__device__ __forceinline__ void two_sum_shift(float hi, float lo, float b, float bl, float &oh, float &ol) {
+  // (hi + lo) + (b + bl) with b exact: oh + ol, the rounding error of hi + b kept in ol
+  const float a = hi + b;
+  const float bb = a - hi;
+  const float e = (hi - (a - bb)) + (b - bb);
+  oh = a;
+  ol = (lo + bl) + e;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <int NT>
+__device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int nn,
+                                              const float (&px)[4], const float (&py)[4], const float (&pz)[4],
+                                              const float (&qx)[4], const float (&qy)[4], const float (&qz)[4],
+                                              float lam, float (&fp)[4], float (&fx)[4], float (&fy)[4],
+                                              float (&fz)[4]) {
+#pragma unroll 2
+  for (int j = 0; j < nn; ++j) {
+    const float4 s = sh[j], sL = sl[j];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const float dx = (px[t] - s.x) + (qx[t] - sL.x);
+      const float dy = (py[t] - s.y) + (qy[t] - sL.y);
+      const float dz = (pz[t] - s.z) + (qz[t] - sL.z);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+      const float r = r2 * ri;
+      const float e = s.w * __expf(-lam * r) * ri;
+      fp[t] += e;
+      const float f = e * (ri * ri) * (1.f + lam * r);
+      fx[t] += f * dx;
+      fy[t] += f * dy;
+      fz[t] += f * dz;
+    }
+  }
+}
+
+// One warp per (target leaf, half) and no block-wide barriers: warp h of a leaf takes the
+// targets 128 i + 64 h + lane + 32 t (t = 0, 1) and streams the sources of the 27 neighbours
+// through its own double-buffered chunks of P2P_WSRC records.  Two warps per leaf and a
+// 64-register budget keep 32 warps resident per SM.
+constexpr int P2P_WARPS = 4, P2P_WSRC = 64;
+
+template <int NT>
+__device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tcnt, uint32_t tst,
+                                              const float4 *__restrict__ h4, const float4 *__restrict__ l4,
+                                              const uint32_t *src, float hh, float hl, float lam, double scale,
+                                              double *phi, double *field, float4 (*sh)[P2P_WSRC],
+                                              float4 (*sl)[P2P_WSRC], const uint32_t *nb_start,
+                                              const uint32_t *nb_cnt, const uint32_t *ch_pre, const int (*nb_d)[3],
+                                              int nch) {
+  float th[2][3], tl[2][3];
+  uint32_t tk[2];
+  bool tv[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const uint32_t tj = t0 + lane + 32 * t;
+    tv[t] = t < NT && tj < tcnt;
+    tk[t] = tst + (tv[t] ? tj : 0);
+    const float4 a = h4[tk[t]], b = l4[tk[t]];
+    th[t][0] = a.x; th[t][1] = a.y; th[t][2] = a.z;
+    tl[t][0] = b.x; tl[t][1] = b.y; tl[t][2] = b.z;
+  }
+  auto chunk = [&](int c, int &o, uint32_t &first, int &nn) {
+    o = 0;
+    while ((int)ch_pre[o + 1] <= c) ++o;
+    const uint32_t off = (uint32_t)(c - (int)ch_pre[o]) * P2P_WSRC;
+    first = nb_start[o] + off;
+    nn = (int)min((uint32_t)P2P_WSRC, nb_cnt[o] - off);
+  };
+  auto issue = [&](int c, int buf) {
+    int o, nn;
+    uint32_t first;
+    chunk(c, o, first, nn);
+    for (int e = lane; e < 2 * P2P_WSRC; e += 32) {
+      const int j = e >> 1;
+      if (j < nn) {
+        if (e & 1) cp_async16(&sl[buf][j], &l4[first + j], true);
+        else cp_async16(&sh[buf][j], &h4[first + j], true);
+      }
+    }
+    cp_commit();
+  };
+  float sp[2] = {0, 0}, cp[2] = {0, 0}, sx[2] = {0, 0}, cx[2] = {0, 0};
+  float sy[2] = {0, 0}, cy[2] = {0, 0}, sz[2] = {0, 0}, cz[2] = {0, 0};
+  if (nch > 0) issue(0, 0);
+  for (int c = 0; c < nch; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nch) {
+      issue(c + 1, buf ^ 1);
+      cp_wait1();
+    } else {
+      cp_wait0();
+    }
+    __syncwarp();
+    int o, nn;
+    uint32_t first;
+    chunk(c, o, first, nn);
+    float px[4], py[4], pz[4], qx[4], qy[4], qz[4];
+    const float dxh = -(float)nb_d[o][0], dyh = -(float)nb_d[o][1], dzh = -(float)nb_d[o][2];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      two_sum_shift(th[t][0], tl[t][0], dxh * hh, dxh * hl, px[t], qx[t]);
+      two_sum_shift(th[t][1], tl[t][1], dyh * hh, dyh * hl, py[t], qy[t]);
+      two_sum_shift(th[t][2], tl[t][2], dzh * hh, dzh * hl, pz[t], qz[t]);
+    }
+    float fp[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fy[4] = {0, 0, 0, 0}, fz[4] = {0, 0, 0, 0};
+    p2p_f32_chunk<NT>(sh[buf], sl[buf], nn, px, py, pz, qx, qy, qz, lam, fp, fx, fy, fz);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      kahan_add(sp[t], cp[t], fp[t]);
+      kahan_add(sx[t], cx[t], fx[t]);
+      kahan_add(sy[t], cy[t], fy[t]);
+      kahan_add(sz[t], cz[t], fz[t]);
+    }
+    __syncwarp();  // buffer buf is refilled by the issue of chunk c + 2
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    if (!tv[t]) continue;
+    const uint32_t i = src[tk[t]];
+    phi[i] += scale * ((double)sp[t] - (double)cp[t]);
+    if (field) {
+      field[3 * i] += scale * ((double)sx[t] - (double)cx[t]);
+      field[3 * i + 1] += scale * ((double)sy[t] - (double)cy[t]);
+      field[3 * i + 2] += scale * ((double)sz[t] - (double)cz[t]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32 * P2P_WARPS, 6) k_p2p_free_f32(const uint32_t *d_nb, const uint64_t *bkey,
+                                                                    const uint32_t *bstart, const uint32_t *bcount,
+                                                                    const int32_t *ulist, const float4 *h4,
+                                                                    const float4 *l4, const uint32_t *src, float hh,
+                                                                    float hl, float lam, double scale, double *phi,
+                                                                    double *field) {
+  __shared__ __align__(16) float4 sh_[P2P_WARPS][2][P2P_WSRC], sl_[P2P_WARPS][2][P2P_WSRC];
+  __shared__ uint32_t nb_start_[P2P_WARPS][NNEAR], nb_cnt_[P2P_WARPS][NNEAR], ch_pre_[P2P_WARPS][NNEAR + 1];
+  __shared__ int nb_d_[P2P_WARPS][NNEAR][3];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t gw = blockIdx.x * P2P_WARPS + w;
+  const uint32_t box = gw >> 1, half = gw & 1;
+  if (box >= *d_nb) return;
+  const uint32_t tst = bstart[box], tcnt = bcount[box];
+  if (64 * half >= tcnt) return;
+  uint32_t *nb_start = nb_start_[w], *nb_cnt = nb_cnt_[w], *ch_pre = ch_pre_[w];
+  int(*nb_d)[3] = nb_d_[w];
+  if (lane < NNEAR) {
+    const int o = lane;
+    const int sb = ulist[(size_t)box * NNEAR + o];
+    const uint64_t kt = bkey[box];
+    nb_start[o] = sb < 0 ? 0u : bstart[sb];
+    nb_cnt[o] = sb < 0 ? 0u : bcount[sb];
+    if (sb >= 0) {
+      const uint64_t ks = bkey[sb];
+      nb_d[o][0] = (int)compact3_(ks >> 2) - (int)compact3_(kt >> 2);
+      nb_d[o][1] = (int)compact3_(ks >> 1) - (int)compact3_(kt >> 1);
+      nb_d[o][2] = (int)compact3_(ks) - (int)compact3_(kt);
+    } else {
+      nb_d[o][0] = nb_d[o][1] = nb_d[o][2] = 0;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    uint32_t acc = 0;
+    for (int o = 0; o < NNEAR; ++o) {
+      ch_pre[o] = acc;
+      acc += (nb_cnt[o] + P2P_WSRC - 1) / P2P_WSRC;
+    }
+    ch_pre[NNEAR] = acc;
+  }
+  __syncwarp();
+  const int nch = (int)ch_pre[NNEAR];
+  for (uint32_t t0 = 64 * half; t0 < tcnt; t0 += 128) {
+    if (tcnt - t0 > 32)
+      p2p_warp_pass<2>(lane, t0, tcnt, tst, h4, l4, src, hh, hl, lam, scale, phi, field, sh_[w], sl_[w], nb_start,
+                       nb_cnt, ch_pre, nb_d, nch);
+    else
+      p2p_warp_pass<1>(lane, t0, tcnt, tst, h4, l4, src, hh, hl, lam, scale, phi, field, sh_[w], sl_[w], nb_start,
+                       nb_cnt, ch_pre, nb_d, nch);
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // reaction near field: target leaf box vs adjacent image leaf boxes across the interface,
 // Sommerfeld integral by the precomputed node rule, truncated per pair at exp(-36)
@@ -1049,6 +1281,302 @@ static void launch_l2p(Ctx &c, const Level &Lv, int64_t nb, const PointSet &P, G
   c.launches++;
 }
 
+// ---------------------------------------------------------------------------------------
+// Free-space M2L on the tensor cores (tcgen05, TF32 with a three-product split).
+//
+// In real form a translation is linear in the 2K - (p+1) real numbers of an expansion (the real
+// parts of all K half-representation coefficients and the imaginary parts of those with m > 0;
+// the m = 0 imaginary parts vanish for real charges).  With these R real coordinates padded to
+// NC chunks of 32, the offset o maps source rows to target rows by one real matrix W_o
+// (the class operator P, Q with both azimuth rotations folded in).  A CTA owns 128 target
+// boxes of one octant (identical far-offset sets) and one dx-slice of the offsets; for every
+// offset it gathers the 128 source rows into shared memory and accumulates
+//     D[128 x 32NC] += A_o[128 x 32NC] * W_o^T
+// in TMEM, as hi*hi + hi*lo + lo*hi TF32 products (x = hi + lo, hi = x rounded to TF32).
+// ---------------------------------------------------------------------------------------
+// real coordinate c -> half-representation index: >= 0 real part, <= -2 imaginary part of
+// index (-code - 2), -1 padding
+__host__ __device__ __forceinline__ int tc_remap(int c, int K, int p) {
+  const int NI = K - (p + 1);
+  if (c < K) return c;
+  const int j = c - K;
+  if (j >= NI) return -1;
+  int n = 1;
+  while ((n + 1) * n / 2 <= j) ++n;  // entries with m > 0 below degree n: n(n-1)/2
+  const int m = j - n * (n - 1) / 2 + 1;
+  return -(n * (n + 1) / 2 + m) - 2;
+}
+
+// source rows of one level: hi and lo TF32 parts, ldr = 32 NC floats per box
+__global__ void k_tc_pack_rows(const float2 *M, int64_t nbox, int K, int p, int ldr, float *hi, float *lo) {
+  const int64_t total = nbox * ldr;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / ldr;
+    const int c = (int)(e % ldr);
+    const int code = tc_remap(c, K, p);
+    float v = 0.f;
+    if (code >= 0) v = M[b * K + code].x;
+    else if (code <= -2) v = M[b * K + (-code - 2)].y;
+    const float h = tc::to_tf32(v);
+    hi[e] = h;
+    lo[e] = tc::to_tf32(v - h);
+  }
+}
+
+// W_o for every offset with a class: [NOFF][ldr rows (outputs)][ldr cols (inputs)], hi and lo
+__global__ void k_tc_pack_w(const float *ops, const int32_t *cls_of, const float *rot, int K, int p, int ldr,
+                            float *whi, float *wlo) {
+  const int o = blockIdx.x;
+  const int cls = cls_of[o];
+  if (cls < 0) return;
+  const size_t KK = (size_t)K * K;
+  const float *P = ops + (size_t)cls * 2 * KK, *Q = P + KK;
+  const float *rc = rot + (size_t)o * (PMAX + 1) * 2;
+  const int total = ldr * ldr;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < total; e += gridDim.y * blockDim.x) {
+    const int r = e / ldr, k = e % ldr;
+    const int ro = tc_remap(r, K, p), ko = tc_remap(k, K, p);
+    float w = 0.f;
+    if (ro != -1 && ko != -1) {
+      const int oh = ro >= 0 ? ro : -ro - 2, ih = ko >= 0 ? ko : -ko - 2;
+      const int m = cK.mof[oh], mu = cK.mof[ih];
+      const float cm = rc[2 * m], sm = rc[2 * m + 1], cu = rc[2 * mu], su = rc[2 * mu + 1];
+      const float pv = P[(size_t)oh * K + ih], qv = Q[(size_t)oh * K + ih];
+      if (ro >= 0 && ko >= 0) w = cm * cu * pv + sm * su * qv;
+      else if (ro >= 0) w = -cm * su * pv + sm * cu * qv;
+      else if (ko >= 0) w = -sm * cu * pv + cm * su * qv;
+      else w = sm * su * pv + cm * cu * qv;
+    }
+    const float h = tc::to_tf32(w);
+    const size_t at = ((size_t)o * ldr + r) * ldr + k;
+    whi[at] = h;
+    wlo[at] = tc::to_tf32(w - h);
+  }
+}
+
+struct TJob {
+  const float *ahi, *alo;   // [nsb][ldr]
+  const float *whi, *wlo;   // [NOFF][ldr][ldr]
+  const int32_t *vlist;     // [ntb][NOFF]
+  const int32_t *cls_of;    // [NOFF]
+  float2 *L;                // partial sums [ntb][M2L_NSLOT][K]
+  int64_t ntb, item0;
+  int slot0, pad;
+  const uint32_t *pstart, *pcount;  // octant tiles (nullptr: plain tiles of 128)
+  const uint64_t *ckey;
+  int64_t npar;
+};
+
+constexpr int TC_ROWS = 128;
+constexpr int TC_WAIT = 1 << 22;  // mbarrier polls before the kernel reports a timeout
+
+__host__ __device__ constexpr int tc_nst(int NC) { return NC <= 5 ? 3 : 2; }
+__host__ __device__ constexpr size_t tc_stage_bytes(int NC) { return (size_t)2 * (TC_ROWS + 32 * NC) * 128; }
+static size_t tc_smem(int NC) { return tc_nst(NC) * tc_stage_bytes(NC) + 1024; }
+
+// The tensor core's FP32 accumulation loses precision over long MMA chains, so every offset
+// accumulates in a fresh TMEM accumulator (a 32NC-term dot product per output, in 3 x NC x 4
+// MMAs) and is then folded into FP32 registers, one row per thread; two accumulators alternate
+// so that folding offset i overlaps the MMAs of offset i + 1.
+template <int NC>
+__global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, int K, int p, int *status) {
+  constexpr int N = 32 * NC, NST = tc_nst(NC);
+  constexpr int TCOLS = 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256));
+  static_assert(2 * N <= 256, "two accumulators of N columns");
+  constexpr size_t SA = (size_t)TC_ROWS * 128, SB = (size_t)N * 128;  // bytes of one A / B chunk tile
+  extern __shared__ __align__(16) unsigned char tcsm[];  // base rounded up to 1024 below
+  unsigned char *sbase = (unsigned char *)(((uintptr_t)tcsm + 1023) & ~(uintptr_t)1023);
+  __shared__ int tid_[TC_ROWS];
+  __shared__ int steps[49];
+  __shared__ int nsteps;
+  __shared__ unsigned hasmask[2];
+  __shared__ uint64_t mbar[NST], accbar[2];
+  __shared__ uint32_t tbase;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].item0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const TJob &J = jobs[lo];
+  const int64_t local = (int64_t)blockIdx.x - J.item0;
+  const int slice = (int)(local % M2L_NSLICE);
+  const int64_t ti = local / M2L_NSLICE;
+  if (J.pstart ? (ti >> 3) * TC_ROWS >= J.npar : ti * TC_ROWS >= J.ntb) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    int t = -1;
+    if (J.pstart) {
+      const int oct = (int)(ti & 7);
+      const int64_t P = (ti >> 3) * TC_ROWS + tid;
+      if (P < J.npar) {
+        const uint32_t s0 = J.pstart[P], n = J.pcount[P];
+        for (uint32_t k = 0; k < n; ++k)
+          if ((int)(J.ckey[s0 + k] & 7ull) == oct) t = (int)(s0 + k);
+      }
+    } else {
+      const int64_t j = ti * TC_ROWS + tid;
+      if (j < J.ntb) t = (int)j;
+    }
+    tid_[tid] = t;
+  }
+  if (tid < 2) hasmask[tid] = 0u;
+  __syncthreads();
+  {
+    const int t = tid_[tid];
+    if (t >= 0)
+      for (int k = 0; k < 49; ++k) {
+        const int o = slice * 49 + k;
+        if (J.cls_of[o] >= 0 && J.vlist[(size_t)t * NOFF + o] >= 0) atomicOr(&hasmask[k >> 5], 1u << (k & 31));
+      }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    for (int k = 0; k < 49; ++k)
+      if (hasmask[k >> 5] & (1u << (k & 31))) steps[n++] = slice * 49 + k;
+    nsteps = n;
+  }
+  __syncthreads();
+  const int ns = nsteps;
+  if (ns == 0) return;
+  if (warp == 0) tc::tmem_alloc(&tbase, TCOLS);
+  if (tid == 0) {
+    for (int b = 0; b < NST; ++b) tc::mbar_init(&mbar[b], 1);
+    tc::mbar_init(&accbar[0], 1);
+    tc::mbar_init(&accbar[1], 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tbase, lanebase = (uint32_t)(warp * 32) << 16;
+  const int S = ns * NC;  // stages: (offset, K-chunk)
+  const int myt = tid_[tid];
+  constexpr uint32_t IDESC = tc::idesc_tf32(TC_ROWS, N);
+  float racc[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) racc[j] = 0.f;
+  // fold the accumulator of offset index oi into racc (whole CTA; false on timeout)
+  auto fold = [&](int oi) -> bool {
+    const bool ok = tc::mbar_wait(&accbar[oi & 1], (uint32_t)((oi >> 1) & 1), TC_WAIT);
+    if (ok) {
+      tc::fence_after();
+      const uint32_t col = (uint32_t)((oi & 1) * N);
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 8) {
+        float v[8];
+        tc::tmem_ld8(tmem + lanebase + col + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) racc[c0 + j] += v[j];
+      }
+      tc::fence_before();
+    }
+    return ok;
+  };
+  bool fail = false;
+  int committed = -1;  // last stage whose MMAs were committed
+  int cur_o = -1, my_src = -1;
+  for (int s = 0; s < S + NST - 1; ++s) {
+    if (s < S) {
+      const int b = s % NST;
+      if (s >= NST) {
+        const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)((s / NST - 1) & 1), TC_WAIT);
+        if (__syncthreads_or(!ok)) {
+          fail = true;
+          break;
+        }
+      }
+      const int o = steps[s / NC], kc = s % NC;
+      if (o != cur_o) {
+        cur_o = o;
+        my_src = myt >= 0 ? J.vlist[(size_t)myt * NOFF + o] : -1;
+      }
+      unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
+      unsigned char *Ah = st, *Al = st + SA, *Bh = st + 2 * SA, *Bl = st + 2 * SA + SB;
+      {
+        const bool v = my_src >= 0;
+        const float *gh = J.ahi + (size_t)(v ? my_src : 0) * N + kc * 32;
+        const float *gl = J.alo + (size_t)(v ? my_src : 0) * N + kc * 32;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cp_async16(Ah + tc::swz16(tid, u), gh + 4 * u, v);
+          cp_async16(Al + tc::swz16(tid, u), gl + 4 * u, v);
+        }
+      }
+      {
+        const float *wh = J.whi + (size_t)o * N * N + kc * 32, *wl = J.wlo + (size_t)o * N * N + kc * 32;
+        for (int e = tid; e < N * 8; e += 128) {
+          const int r = e >> 3, u = e & 7;
+          cp_async16(Bh + tc::swz16(r, u), wh + (size_t)r * N + 4 * u, true);
+          cp_async16(Bl + tc::swz16(r, u), wl + (size_t)r * N + 4 * u, true);
+        }
+      }
+    }
+    cp_commit();
+    const int sc = s - (NST - 1);
+    if (sc >= 0) {
+      if (NST == 3) asm volatile("cp.async.wait_group 2;\n" ::);
+      else asm volatile("cp.async.wait_group 1;\n" ::);
+      tc::fence_async_smem();
+      __syncthreads();
+      const int oi = sc / NC, kc = sc % NC;
+      if (tid == 0) {
+        tc::fence_after();
+        const int b = sc % NST;
+        unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
+        const uint32_t ah = tc::smem_u32(st), al = ah + (uint32_t)SA, bh = ah + 2 * (uint32_t)SA,
+                       bl = bh + (uint32_t)SB;
+        const uint32_t dacc = tmem + (uint32_t)((oi & 1) * N);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kk * 32;
+          tc::mma_tf32(dacc, tc::sdesc(ah + off), tc::sdesc(bh + off), IDESC, (kc | kk) ? 1u : 0u);
+          tc::mma_tf32(dacc, tc::sdesc(ah + off), tc::sdesc(bl + off), IDESC, 1u);
+          tc::mma_tf32(dacc, tc::sdesc(al + off), tc::sdesc(bh + off), IDESC, 1u);
+        }
+        tc::commit(&mbar[b]);
+        if (kc == NC - 1) tc::commit(&accbar[oi & 1]);
+      }
+      committed = sc;
+      // offset oi is queued in full: fold offset oi - 1, whose accumulator offset oi + 1 reuses
+      if (kc == NC - 1 && oi >= 1) {
+        if (__syncthreads_or(!fold(oi - 1))) {
+          fail = true;
+          break;
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+  if (!fail) {
+    if (__syncthreads_or(!fold(ns - 1))) fail = true;
+  } else if (committed >= 0) {
+    // drain: every MMA has completed once the last committed stage's barrier phase completes
+    tc::mbar_wait(&mbar[committed % NST], (uint32_t)((committed / NST) & 1), TC_WAIT);
+  }
+  if (fail) {
+    if (tid == 0) atomicExch(status, LPBFMM_ERR_TIMEOUT);
+  } else {
+    const int t = tid_[tid];  // this thread's row
+    if (t >= 0) {
+      float2 *Lrow = J.L + ((size_t)t * M2L_NSLOT + J.slot0 + slice) * K;
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        const int code = tc_remap(c, K, p);
+        if (code >= 0) {
+          Lrow[code].x = racc[c];
+          if (cK.mof[code] == 0) Lrow[code].y = 0.f;
+        } else if (code <= -2) {
+          Lrow[-code - 2].y = racc[c];
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, TCOLS);
+}
+
 template <typename T, int TPT, int NR>
 static void launch_m2l_t(Ctx &c, const std::vector<XJob> &jobs, int64_t items) {
   constexpr int TT = 16 * TPT, KR = 16 * NR;
@@ -1144,13 +1672,23 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
   typedef typename C2<T>::t T2;
   std::vector<RJob> rjobs;
   int64_t relem = 0;
+  // tensor-core free-space path: mixed precision, 2K - (p+1) <= 128 real coordinates
+  const int tc_nc = (2 * c.K - (c.p + 1) + 31) / 32;
+  const bool use_tc = sizeof(T) == 4 && tc_nc <= 4;  // p <= 10
+  std::vector<TJob> tjobs;
+  int64_t titems = 0;
   auto add = [&](const int32_t *tlist, const uint32_t *d_ntl, int64_t ntb, const int32_t *vlist,
-                 const int32_t *cls_of, const void *M, const void *ops, void *part, int ntypes, int slot0) {
+                 const int32_t *cls_of, const void *M, const void *ops, void *part, int ntypes, int slot0,
+                 const Level *par, const Level *lev) {
     XJob j;
     j.tlist = tlist; j.d_ntl = d_ntl; j.ntb = ntb; j.vlist = vlist; j.cls_of = cls_of;
     j.M = M; j.ops = ops; j.L = part; j.ntypes = ntypes; j.slot0 = slot0; j.item0 = items;
+    j.pstart = par ? par->start : nullptr;
+    j.pcount = par ? par->count : nullptr;
+    j.ckey = par ? lev->key : nullptr;
+    j.npar = par ? par->n : 0;
     jobs.push_back(j);
-    items += ((ntb + TT - 1) / TT) * M2L_NSLICE;
+    items += m2l_tiles(j, TT) * M2L_NSLICE;
   };
   for (auto &g : groups) {
     const bool dofree = g.is_free && (parts & 1);
@@ -1164,14 +1702,63 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
       r.part = part; r.L = g.Lt[l]; r.n = ntb * c.K; r.e0 = relem;
       rjobs.push_back(r);
       relem += r.n;
-      if (dofree) add(nullptr, nullptr, ntb, g.vfree[l], tb.cls_free, g.Mfree[l], g.op_free[l], part, 1, 0);
+      if (dofree && use_tc) {
+        // tensor-core path: pack the level's source rows and the offsets' real operators
+        const int N = 32 * tc_nc;
+        float *ahi = c.arena.get<float>((size_t)ntb * N), *alo = c.arena.get<float>((size_t)ntb * N);
+        const int64_t tot = ntb * N;
+        k_tc_pack_rows<<<(unsigned)std::min<int64_t>(4096, (tot + 255) / 256), 256, 0, c.stream>>>(
+            (const float2 *)g.Mfree[l], ntb, c.K, c.p, N, ahi, alo);
+        LPB_LAUNCH();
+        float *whi = c.arena.get<float>((size_t)NOFF * N * N), *wlo = c.arena.get<float>((size_t)NOFF * N * N);
+        k_tc_pack_w<<<dim3(NOFF, 8), 256, 0, c.stream>>>((const float *)g.op_free[l], tb.cls_free,
+                                                          (const float *)tb.rot, c.K, c.p, N, whi, wlo);
+        LPB_LAUNCH();
+        c.launches += 2;
+        TJob j;
+        j.ahi = ahi; j.alo = alo; j.whi = whi; j.wlo = wlo; j.vlist = g.vfree[l]; j.cls_of = tb.cls_free;
+        j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = 0; j.pad = 0;
+        const Level *par = l >= 3 ? &g.T.lev[l - 1] : nullptr;
+        j.pstart = par ? par->start : nullptr;
+        j.pcount = par ? par->count : nullptr;
+        j.ckey = par ? g.T.lev[l].key : nullptr;
+        j.npar = par ? par->n : 0;
+        const int64_t tiles = par ? 8 * ((j.npar + TC_ROWS - 1) / TC_ROWS) : (ntb + TC_ROWS - 1) / TC_ROWS;
+        titems += tiles * M2L_NSLICE;
+        tjobs.push_back(j);
+      } else if (dofree) {
+        add(nullptr, nullptr, ntb, g.vfree[l], tb.cls_free, g.Mfree[l], g.op_free[l], part, 1, 0,
+            l >= 3 ? &g.T.lev[l - 1] : nullptr, &g.T.lev[l]);
+      }
       if (react_far && g.vreact[l])
         for (int kt = 0; kt < 3; ++kt)
           add(g.rows[l] + (size_t)kt * ntb, g.nrows[l] + kt, ntb, g.vreact[l],
-              tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], part, g.ntypes, M2L_NSLICE);
+              tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], part, g.ntypes, M2L_NSLICE,
+              nullptr, nullptr);
     }
   }
-  if (jobs.empty()) return;
+  if (jobs.empty() && tjobs.empty()) return;
+  if (!tjobs.empty()) {
+    TJob *dj = c.arena.get<TJob>(tjobs.size());
+    LPB_CUDA(cudaMemcpyAsync(dj, tjobs.data(), sizeof(TJob) * tjobs.size(), cudaMemcpyHostToDevice, c.stream));
+    switch (tc_nc) {
+#define LPB_TC_CASE(NCV)                                                                                     \
+  case NCV: {                                                                                                \
+    static bool attr = false;                                                                                \
+    if (!attr) {                                                                                             \
+      LPB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NCV>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                    (int)tc_smem(NCV)));                                                     \
+      attr = true;                                                                                           \
+    }                                                                                                        \
+    k_m2l_tc<NCV><<<(unsigned)titems, 128, tc_smem(NCV), c.stream>>>(dj, (int)tjobs.size(), c.K, c.p, c.status); \
+    break;                                                                                                   \
+  }
+      LPB_TC_CASE(1) LPB_TC_CASE(2) LPB_TC_CASE(3) LPB_TC_CASE(4)
+#undef LPB_TC_CASE
+    }
+    LPB_LAUNCH();
+    c.launches++;
+  }
   auto launch_reduce = [&]() {
     RJob *dr = c.arena.get<RJob>(rjobs.size());
     LPB_CUDA(cudaMemcpyAsync(dr, rjobs.data(), sizeof(RJob) * rjobs.size(), cudaMemcpyHostToDevice, c.stream));
@@ -1179,12 +1766,16 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     LPB_LAUNCH();
     c.launches++;
   };
+  if (jobs.empty()) {
+    launch_reduce();
+    return;
+  }
   if (sizeof(T) == 4 && c.K <= F32_KR) {
     // re-count items with the larger tile of the asynchronous FP32 kernel
     int64_t it = 0;
     for (auto &j : jobs) {
       j.item0 = it;
-      it += ((j.ntb + F32_TT - 1) / F32_TT) * M2L_NSLICE;
+      it += m2l_tiles(j, F32_TT) * M2L_NSLICE;
     }
     const size_t smem = m2l_f32_smem(c.K);
     static bool attr = false;
@@ -1227,11 +1818,28 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   }
   PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
   if (dofree) {
-    k_p2p_free<T><<<(unsigned)g.T.lev[D].n, P2P_TPB, 0, c.stream>>>(
-        g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q,
-        g.T.src, geo_at<T>(g, D), c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
-    LPB_LAUNCH();
-    c.launches++;
+    if (sizeof(T) == 4) {
+      const unsigned nb = (unsigned)g.T.lev[D].n;
+      const int64_t np = g.T.np;
+      float4 *h4 = c.arena.get<float4>((size_t)np), *l4 = c.arena.get<float4>((size_t)np);
+      k_split_points<<<nb, 64, 0, c.stream>>>(g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count,
+                                               g.T.x, g.T.y, g.T.z, g.T.q, geo_at<T>(g, D), h4, l4);
+      LPB_LAUNCH();
+      const double hD = g.h(D);
+      const float hh = (float)hD, hl = (float)(hD - (double)hh);
+      k_p2p_free_f32<<<(2 * nb + P2P_WARPS - 1) / P2P_WARPS, 32 * P2P_WARPS, 0, c.stream>>>(g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start,
+                                                    g.T.lev[D].count, g.ufree, h4, l4, g.T.src, hh, hl,
+                                                    (float)c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi,
+                                                    field);
+      LPB_LAUNCH();
+      c.launches += 2;
+    } else {
+      k_p2p_free<T><<<(unsigned)g.T.lev[D].n, P2P_TPB, 0, c.stream>>>(
+          g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count, g.ufree, g.T.x, g.T.y, g.T.z,
+          g.T.q, g.T.src, geo_at<T>(g, D), c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
+      LPB_LAUNCH();
+      c.launches++;
+    }
   }
   if (react_near && g.ureact && g.nodes) {
     k_p2p_react<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(

@@ -113,6 +113,7 @@ struct Ctx {
   double *gaunt = nullptr;   // [(p+1)^2 in][(p+1)^2 out][2p+1]
   double *tpoly = nullptr;   // [K][TPK] Legendre-product coefficients
   double *sfac = nullptr;    // [KMAX_TAB+1][KMAX_TAB+1]: sqrt((K+d)! (K-d)!) for d <= K
+  double *phat_dir = nullptr;  // [72][(2p+1)(2p+2)/2]: Phat_q^k(cos theta) of the operator directions
   int tpk = 0;
   int *status = nullptr;     // device status word
   int *h_status = nullptr;   // pinned

@@ -23,7 +23,7 @@ struct OpDesc {
   int kind;     // 0 = M2L free, 1 = M2M, 2 = L2L
   int out_inv;  // 0: out scale x^n/(2n+1)!!, 1: (2n+1)!!/x^n
   int in_inv;
-  int pad;
+  int dir;      // direction of b: free M2L class 0..69, 70 + cz for M2M / L2L (Ctx::phat_dir)
   double lam, bnorm, cosb, xout, xin, pref;
   int64_t dst;  // element offset of P (Q follows after K*K)
 };
@@ -35,27 +35,48 @@ __device__ __forceinline__ void hdecode(int o, int &n, int &m) {
   m = o - n * (n + 1) / 2;
 }
 
-template <typename T>
-__global__ void k_build_ops(const OpDesc *descs, int p, int K, const double *gaunt, T *out) {
-  const OpDesc d = descs[blockIdx.x];
-  __shared__ double f[2 * PMAX + 1];
-  __shared__ double Pl[(2 * PMAX + 1) * (2 * PMAX + 2) / 2];
-  __shared__ double so[PMAX + 1], si[PMAX + 1];
+// Per-descriptor radial factors, one thread each: f[q] = k_q or i_q (lambda |b|) and the
+// output / input scalings so[n], si[n], stored as [NPREP] doubles per descriptor.  The angular
+// factor Phat_q^k(cos theta_b) depends only on the direction of b and comes from Ctx::phat_dir.
+constexpr int PREP_F = 0, PREP_SO = 2 * PMAX + 1, PREP_SI = PREP_SO + PMAX + 1, NPREP = PREP_SI + PMAX + 1;
+constexpr int NPL_MAX = (2 * PMAX + 1) * (2 * PMAX + 2) / 2;
+
+__global__ void k_ops_prep(const OpDesc *descs, int nd, int p, double *prep) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  const OpDesc d = descs[i];
+  double *w = prep + (size_t)i * NPREP;
   const int qmax = 2 * p;
-  if (threadIdx.x == 0) {
-    const double x = d.lam * d.bnorm;
-    if (d.kind == 0) kbessel_all(x, qmax, f);
-    else ibessel_all(x, qmax, f);
-    phat_all(d.cosb, qmax, Pl);
-    for (int n = 0; n <= p; ++n) {
-      const double a = pow(d.xout, n) / dfact2(n), b = pow(d.xin, n) / dfact2(n);
-      so[n] = (d.out_inv ? 1.0 / a : a) * d.pref;
-      si[n] = d.in_inv ? 1.0 / b : b;
+  const double x = d.lam * d.bnorm;
+  if (d.kind == 0) kbessel_all(x, qmax, w + PREP_F);
+  else ibessel_all(x, qmax, w + PREP_F);
+  double a = 1.0, b = 1.0;  // x^n / (2n+1)!!
+  for (int n = 0; n <= p; ++n) {
+    if (n > 0) {
+      a *= d.xout / (2.0 * n + 1.0);
+      b *= d.xin / (2.0 * n + 1.0);
     }
+    w[PREP_SO + n] = (d.out_inv ? 1.0 / a : a) * d.pref;
+    w[PREP_SI + n] = d.in_inv ? 1.0 / b : b;
   }
+}
+
+constexpr int OPS_SPLIT = 4;  // CTAs per descriptor
+
+template <typename T>
+__global__ void k_build_ops(const OpDesc *descs, const double *prep, const double *phat_dir, int p, int K,
+                            const double *gaunt, T *out) {
+  const OpDesc d = descs[blockIdx.x];
+  __shared__ double w[NPREP], Pl[NPL_MAX];
+  const double *pw = prep + (size_t)blockIdx.x * NPREP;
+  for (int e = threadIdx.x; e < NPREP; e += blockDim.x) w[e] = pw[e];
+  const int npl = (2 * p + 1) * (2 * p + 2) / 2;
+  const double *pd = phat_dir + (size_t)d.dir * npl;
+  for (int e = threadIdx.x; e < npl; e += blockDim.x) Pl[e] = pd[e];
   __syncthreads();
+  const double *f = w + PREP_F, *so = w + PREP_SO, *si = w + PREP_SI;
   const int NF = (p + 1) * (p + 1), NQ = 2 * p + 1;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < K * K; e += gridDim.y * blockDim.x) {
     const int o = e / K, i = e % K;
     int n, m, nu, mu;
     hdecode(o, n, m);
@@ -64,21 +85,21 @@ __global__ void k_build_ops(const OpDesc *descs, int p, int K, const double *gau
     for (int sgn = 0; sgn < 2; ++sgn) {
       const int mus = sgn ? -mu : mu;
       if (sgn && mu == 0) break;
-      double s = 0.0;
+      double acc = 0.0;
       for (int q = abs(n - nu); q <= n + nu; q += 2) {
         if (d.kind == 2 || d.kind == 0) {
           const int k = m - mus;
           if (abs(k) > q) continue;
-          s += f[q] * phat_signed(Pl, q, k) * gaunt[((size_t)fidx(nu, mus) * NF + fidx(n, m)) * NQ + q];
+          acc += f[q] * phat_signed(Pl, q, k) * gaunt[((size_t)fidx(nu, mus) * NF + fidx(n, m)) * NQ + q];
         } else {
           const int k = mus - m;
           if (abs(k) > q) continue;
-          s += f[q] * phat_signed(Pl, q, k) * gaunt[((size_t)fidx(n, m) * NF + fidx(nu, mus)) * NQ + q];
+          acc += f[q] * phat_signed(Pl, q, k) * gaunt[((size_t)fidx(n, m) * NF + fidx(nu, mus)) * NQ + q];
         }
       }
-      s *= 4.0 * PI * so[n] * si[nu];
-      if (d.kind == 0 && (n & 1)) s = -s;
-      r[sgn] = s;
+      acc *= 4.0 * PI * so[n] * si[nu];
+      if (d.kind == 0 && (n & 1)) acc = -acc;
+      r[sgn] = acc;
     }
     double P, Q;
     if (mu == 0) { P = r[0]; Q = 0.0; }
@@ -471,17 +492,16 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
   std::vector<OpDesc> descs;
   size_t total = 0;
   auto add = [&](int kind, int out_inv, int in_inv, double lam, double bx, double by, double bz, double xout,
-                 double xin, double pref, void **slot, size_t offset_in_slot) {
+                 double xin, double pref, int dir, size_t offset_in_slot) {
     OpDesc d;
-    d.kind = kind; d.out_inv = out_inv; d.in_inv = in_inv; d.pad = 0;
+    d.kind = kind; d.out_inv = out_inv; d.in_inv = in_inv; d.dir = dir;
     d.lam = lam;
     d.bnorm = sqrt(bx * bx + by * by + bz * bz);
     d.cosb = bz / d.bnorm;
     d.xout = xout; d.xin = xin; d.pref = pref;
     d.dst = (int64_t)(total + offset_in_slot);
     descs.push_back(d);
-    (void)slot;
-  };
+      };
   // layout: per level a block with M2M (free + types), L2L, free M2L classes
   struct Blk { size_t m2m_t, m2m_i, l2l, fm2l; };
   std::vector<Blk> blk(DMAX + 1);
@@ -493,7 +513,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       if (g.is_free && (parts & 1)) {
         b.m2m_t = total;
         for (int cz = 0; cz < 2; ++cz)
-          add(1, 1, 0, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hp, lam_t * hc, 1.0, nullptr,
+          add(1, 1, 0, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hp, lam_t * hc, 1.0, 70 + cz,
               (size_t)cz * 2 * KK);
         total += 4 * KK;
       }
@@ -504,7 +524,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
           type_decode(t, lp, bb);
           const double la = c.md.lam[lp];
           for (int cz = 0; cz < 2; ++cz)
-            add(1, 1, 0, la, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, la * hp, la * hc, 1.0, nullptr,
+            add(1, 1, 0, la, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, la * hp, la * hc, 1.0, 70 + cz,
                 ((size_t)t * 2 + cz) * 2 * KK);
         }
         total += (size_t)g.ntypes * 4 * KK;
@@ -512,7 +532,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       // L2L: parent (l-1) -> child at l
       b.l2l = total;
       for (int cz = 0; cz < 2; ++cz)
-        add(2, 0, 1, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hc, lam_t * hp, 1.0, nullptr,
+        add(2, 0, 1, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hc, lam_t * hp, 1.0, 70 + cz,
             (size_t)cz * 2 * KK);
       total += 4 * KK;
     }
@@ -526,7 +546,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
           const bool adjacent = rho2[ri] <= 2.0 && abs(dz) <= 1;
           if (adjacent) continue;
           // b = c_t - c_s = -(offset) h; azimuth factored out: b = (rho h, 0, -dz h)
-          add(0, 0, 0, lam_t, sqrt(rho2[ri]) * h, 0.0, -dz * h, lam_t * h, lam_t * h, pref, nullptr,
+          add(0, 0, 0, lam_t, sqrt(rho2[ri]) * h, 0.0, -dz * h, lam_t * h, lam_t * h, pref, cls,
               (size_t)cls * 2 * KK);
         }
       total += (size_t)NFREE_CLS * 2 * KK;
@@ -543,9 +563,13 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
   if (!descs.empty()) {
     OpDesc *dd = c.arena.get<OpDesc>(descs.size());
     LPB_CUDA(cudaMemcpyAsync(dd, descs.data(), sizeof(OpDesc) * descs.size(), cudaMemcpyHostToDevice, c.stream));
-    k_build_ops<T><<<(unsigned)descs.size(), 256, 0, c.stream>>>(dd, p, K, c.gaunt, ops);
+    double *prep = c.arena.get<double>(descs.size() * NPREP);
+    k_ops_prep<<<(unsigned)((descs.size() + 63) / 64), 64, 0, c.stream>>>(dd, (int)descs.size(), p, prep);
     LPB_LAUNCH();
-    c.launches++;
+    k_build_ops<T><<<dim3((unsigned)descs.size(), OPS_SPLIT), 256, 0, c.stream>>>(dd, prep, c.phat_dir, p, K,
+                                                                                  c.gaunt, ops);
+    LPB_LAUNCH();
+    c.launches += 2;
   }
   if (!(parts & 2) || !g.I.np) return;
   // reaction: one descriptor per (level, type)

@@ -1,0 +1,99 @@
+// Blackwell (sm_103a) tensor-core primitives in inline PTX: tcgen05 MMA with the accumulator
+// in tensor memory (TMEM), shared-memory matrix descriptors for the 128-byte swizzled K-major
+// layout, mbarrier completion tracking with bounded waits, and TMEM loads.
+//
+// Operand tiles: a K-chunk of 32 TF32 values (128 bytes) per row; rows are 128 bytes apart and
+// every 8-row group (1024 bytes) is one swizzle atom, in which the 16-byte unit u of row r sits
+// at unit u ^ (r & 7).  Tiles start on 1024-byte boundaries.  An MMA of K = 8 (32 bytes)
+// addresses its slice of the chunk by advancing the descriptor's start address.
+#pragma once
+#include <cstdint>
+
+namespace lpb {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) (k < 32) inside a swizzled [rows x 32] TF32 tile
+__device__ __forceinline__ uint32_t swz(int r, int k) {
+  return (uint32_t)(r * 128 + (((k >> 2) ^ (r & 7)) << 4) + ((k & 3) << 2));
+}
+// byte offset of the 16-byte unit u (0..7) of row r
+__device__ __forceinline__ uint32_t swz16(int r, int u) { return (uint32_t)(r * 128 + ((u ^ (r & 7)) << 4)); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused within one atom)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::tf32, D in F32, A and B K-major, shape M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;"); }
+
+// wait for the completion of the mbarrier phase with the given parity; false after max_iter polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int max_iter) {
+  uint32_t done = 0;
+  for (int it = 0; it < max_iter && !done; ++it)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_u32(mbar)), "r"(parity));
+  return done != 0;
+}
+
+// whole warp: allocate / free ncols TMEM columns (power of two >= 32); address written to *dst
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, int ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, int ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+// generic-proxy shared-memory writes (st.shared, cp.async) made visible to the tensor core
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
+
+// whole warp: 8 consecutive 32-bit columns of this warp's 32 TMEM lanes (lane = row)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// round to TF32 (nearest, ties away), as the tensor core consumes it
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+}  // namespace tc
+}  // namespace lpb
