@@ -191,7 +191,7 @@ def run_ours(args, rank, world, local_rank):
     counts = ctx.counts()
     launches_per_step = counts["launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    m2l_ms = []
+    phase_ms = {}  # per-phase CUDA-event intervals on the evaluation stream, summed over steps
     barrier()
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
@@ -199,8 +199,8 @@ def run_ours(args, rank, world, local_rank):
             ev[k][0].record(stream)
             ctx.eval(q, x, l, out=(phi, fld))
             ev[k][1].record(stream)
-            prof = dict((nm, ms) for nm, ms, _ in ctx.profile())
-            m2l_ms.append(prof.get("m2l", float("nan")))
+            for nm, ms, _ in ctx.profile():
+                phase_ms[nm] = phase_ms.get(nm, 0.0) + ms
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
@@ -258,22 +258,44 @@ def run_ours(args, rank, world, local_rank):
                     "gate": 1e-6}
         ctx64.close()
 
-    # roofline of the dominant kernel: the merged multipole-to-local launch, FP32 FMA pipe (SIMT)
+    # rooflines of the heaviest kernels, from their CUDA-event intervals (per evaluation)
     K = (args.p + 1) * (args.p + 2) // 2
-    flops = 4.0 * K * K * (counts["m2l_free"] + counts["m2l_react"])
-    m2l_med = float(np.nanmedian(m2l_ms))
-    achieved = flops / (m2l_med / 1000.0) / 1e12
-    peak = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "m2l_traffic.json")
-    if os.path.exists(tf):
+    R = 2 * K - (args.p + 1)  # real coordinates of an expansion
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock (TFLOP/s)
+    bf16 = peaks.get("bf16_tflops")
+    tf32_peak = (bf16 if bf16 else 1900.0) * 1.1 / 2.25  # measured bf16 burst x nominal TF32/BF16 ratio
+    per = lambda nm: phase_ms.get(nm, float("nan")) / args.steps
+
+    def traffic_of(kernel):
         try:
-            traffic = json.load(open(tf)).get("bytes_per_launch_1M")
+            return json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
         except Exception:
-            traffic = None
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_m2l (free + reaction multipole-to-local, FP32 FMA)",
-            "ms_per_launch": m2l_med, "algorithmic_flops_per_launch": flops}
+            return None
+
+    def roof(kernel, bound, flops, t, peak, unit_note):
+        a = flops / (t / 1e3) / 1e12
+        return {"kernel": kernel, "bound": bound, "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "traffic": traffic_of(kernel.split()[0]), "ms_per_eval": t, "algorithmic_flops": flops,
+                "flops_per_unit": unit_note}
+
+    roofs = []
+    if "p2p" in phase_ms:
+        roofs.append(roof("k_p2p_free_f32 (free-space near field; interval includes k_split_points)", "alu",
+                          24.0 * counts["p2p_pairs"], per("p2p"), fp32_peak, "24 per pair (+2 SFU)"))
+    if "m2l_tc" in phase_ms:
+        tr = counts["m2l_free"] + counts["m2l_react"]
+        roofs.append(roof("k_m2l_tc (free-space and reaction M2L, tcgen05 3xTF32)", "tensor", 2.0 * R * R * tr,
+                          per("m2l_tc"), tf32_peak,
+                          "2 R^2 = %d per translation (R = %d real coordinates)" % (2 * R * R, R)))
+    if "m2l_simt" in phase_ms:
+        roofs.append(roof("k_m2l_f32 (M2L, FP32 SIMT)", "alu", 4.0 * K * K * counts["m2l_react"], per("m2l_simt"),
+                          fp32_peak, "4 K^2 per translation"))
+    roof_main = max(roofs, key=lambda r: r["ms_per_eval"]) if roofs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -290,7 +312,8 @@ def run_ours(args, rank, world, local_rank):
                 "config": workload_config(n, args.p, "mixed"), "clocks": clk.summary(),
                 "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
                         "d2h_bytes_per_step": n * (8 + 24)},
-                "gpu_launches": launches_per_step * args.steps, "roofline": roof, "cpu_baseline": cpu,
+                "gpu_launches": launches_per_step * args.steps, "roofline": roof_main, "rooflines": roofs,
+                "phases_ms_per_eval": {k: v / args.steps for k, v in phase_ms.items()}, "cpu_baseline": cpu,
                 "fp64_fmm_value": fp64_value, "accuracy": accuracy, "counts": counts}
         print(json.dumps(line), flush=True)
     if dist:

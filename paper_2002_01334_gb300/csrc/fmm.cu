@@ -927,12 +927,21 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
+// 2^x on the special-function unit (max. relative error about 2^-22)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// e^{-lambda r} = 2^{(-lambda log2 e) r}; field factor (1 + lambda r) / r^2 = (1/r)(1/r + lambda)
 template <int NT>
 __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int nn,
                                               const float (&px)[4], const float (&py)[4], const float (&pz)[4],
                                               const float (&qx)[4], const float (&qy)[4], const float (&qz)[4],
                                               float lam, float (&fp)[4], float (&fx)[4], float (&fy)[4],
                                               float (&fz)[4]) {
+  const float nl2 = -lam * 1.44269504088896341f;
 #pragma unroll 2
   for (int j = 0; j < nn; ++j) {
     const float4 s = sh[j], sL = sl[j];
@@ -943,10 +952,9 @@ __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, con
       const float dz = (pz[t] - s.z) + (qz[t] - sL.z);
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-      const float r = r2 * ri;
-      const float e = s.w * __expf(-lam * r) * ri;
+      const float e = s.w * ex2_approx(nl2 * (r2 * ri)) * ri;
       fp[t] += e;
-      const float f = e * (ri * ri) * (1.f + lam * r);
+      const float f = e * ri * (ri + lam);
       fx[t] += f * dx;
       fy[t] += f * dy;
       fz[t] += f * dz;
@@ -956,8 +964,8 @@ __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, con
 
 // One warp per (target leaf, half) and no block-wide barriers: warp h of a leaf takes the
 // targets 128 i + 64 h + lane + 32 t (t = 0, 1) and streams the sources of the 27 neighbours
-// through its own double-buffered chunks of P2P_WSRC records.  Two warps per leaf and a
-// 64-register budget keep 32 warps resident per SM.
+// through its own double-buffered chunks of P2P_WSRC records.  Two warps per leaf and an
+// 80-register budget keep 24 warps resident per SM.
 constexpr int P2P_WARPS = 4, P2P_WSRC = 64;
 
 template <int NT>
@@ -1282,90 +1290,85 @@ static void launch_l2p(Ctx &c, const Level &Lv, int64_t nb, const PointSet &P, G
 }
 
 // ---------------------------------------------------------------------------------------
-// Free-space M2L on the tensor cores (tcgen05, TF32 with a three-product split).
+// M2L on the tensor cores (tcgen05, TF32 with a three-product split), free space and reaction.
 //
-// In real form a translation is linear in the 2K - (p+1) real numbers of an expansion (the real
-// parts of all K half-representation coefficients and the imaginary parts of those with m > 0;
-// the m = 0 imaginary parts vanish for real charges).  With these R real coordinates padded to
-// NC chunks of 32, the offset o maps source rows to target rows by one real matrix W_o
-// (the class operator P, Q with both azimuth rotations folded in).  A CTA owns 128 target
-// boxes of one octant (identical far-offset sets) and one dx-slice of the offsets; for every
-// offset it gathers the 128 source rows into shared memory and accumulates
-//     D[128 x 32NC] += A_o[128 x 32NC] * W_o^T
-// in TMEM, as hi*hi + hi*lo + lo*hi TF32 products (x = hi + lo, hi = x rounded to TF32).
+// Every translation of this library has the azimuth-factored form
+//     X = e^{i mu phi} M,   Y_nm = sum P_{nm,nu mu} Re X_{nu mu} + i sum Q_{nm,nu mu} Im X_{nu mu},
+//     L_nm += e^{-i m phi} Y_nm
+// with real class operators P, Q that do not depend on the azimuth phi of the offset.  In real
+// form (R = 2K - (p+1) coordinates: for m > 0 the pair (Re, Im) in adjacent columns, then the
+// real parts of the m = 0 coefficients; the m = 0 imaginary parts vanish for real charges) the
+// middle step is one real matrix W_c (P between real parts, Q between imaginary parts) per
+// class c and source type.  A CTA owns 128 target boxes (an octant tile, or a run of a target
+// list) and one dx-slice of the offsets.  For every (offset, source type) step it copies the
+// unrotated source rows and W_c into shared memory with cp.async; before the MMAs each thread
+// rotates its own row in place and splits it into TF32 hi + lo (the rotation couples only the
+// adjacent Re, Im columns of one coefficient); it accumulates D = X W_c^T in a fresh TMEM accumulator
+// as hi*hi + hi*lo + lo*hi, and folds D into FP32 registers after the rotation e^{-i m phi}:
+// the tensor core's accumulation loses precision over long chains (measured), a dot product of
+// 32 NC terms per step does not.
 // ---------------------------------------------------------------------------------------
 // real coordinate c -> half-representation index: >= 0 real part, <= -2 imaginary part of
 // index (-code - 2), -1 padding
 __host__ __device__ __forceinline__ int tc_remap(int c, int K, int p) {
-  const int NI = K - (p + 1);
-  if (c < K) return c;
-  const int j = c - K;
-  if (j >= NI) return -1;
-  int n = 1;
-  while ((n + 1) * n / 2 <= j) ++n;  // entries with m > 0 below degree n: n(n-1)/2
-  const int m = j - n * (n - 1) / 2 + 1;
-  return -(n * (n + 1) / 2 + m) - 2;
-}
-
-// source rows of one level: hi and lo TF32 parts, ldr = 32 NC floats per box
-__global__ void k_tc_pack_rows(const float2 *M, int64_t nbox, int K, int p, int ldr, float *hi, float *lo) {
-  const int64_t total = nbox * ldr;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / ldr;
-    const int c = (int)(e % ldr);
-    const int code = tc_remap(c, K, p);
-    float v = 0.f;
-    if (code >= 0) v = M[b * K + code].x;
-    else if (code <= -2) v = M[b * K + (-code - 2)].y;
-    const float h = tc::to_tf32(v);
-    hi[e] = h;
-    lo[e] = tc::to_tf32(v - h);
+  const int NI = K - (p + 1);  // coefficients with m > 0
+  if (c < 2 * NI) {
+    const int j = c >> 1;
+    int n = 1;
+    while ((n + 1) * n / 2 <= j) ++n;  // entries with m > 0 below degree n: n(n-1)/2
+    const int h = n * (n + 1) / 2 + (j - n * (n - 1) / 2 + 1);
+    return (c & 1) ? -h - 2 : h;
   }
+  const int n = c - 2 * NI;
+  return n <= p ? n * (n + 1) / 2 : -1;
 }
 
-// W_o for every offset with a class: [NOFF][ldr rows (outputs)][ldr cols (inputs)], hi and lo
-__global__ void k_tc_pack_w(const float *ops, const int32_t *cls_of, const float *rot, int K, int p, int ldr,
-                            float *whi, float *wlo) {
-  const int o = blockIdx.x;
-  const int cls = cls_of[o];
-  if (cls < 0) return;
+// W_c for every class and source type: [ncls * ntypes][ldr rows (outputs)][ldr cols], hi and lo
+__global__ void k_tc_pack_w(const float *ops, int ncls_types, int K, int p, int ldr, float *whi, float *wlo) {
+  const int ct = blockIdx.x;
+  if (ct >= ncls_types) return;
   const size_t KK = (size_t)K * K;
-  const float *P = ops + (size_t)cls * 2 * KK, *Q = P + KK;
-  const float *rc = rot + (size_t)o * (PMAX + 1) * 2;
+  const float *P = ops + (size_t)ct * 2 * KK, *Q = P + KK;
   const int total = ldr * ldr;
   for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < total; e += gridDim.y * blockDim.x) {
     const int r = e / ldr, k = e % ldr;
     const int ro = tc_remap(r, K, p), ko = tc_remap(k, K, p);
     float w = 0.f;
-    if (ro != -1 && ko != -1) {
-      const int oh = ro >= 0 ? ro : -ro - 2, ih = ko >= 0 ? ko : -ko - 2;
-      const int m = cK.mof[oh], mu = cK.mof[ih];
-      const float cm = rc[2 * m], sm = rc[2 * m + 1], cu = rc[2 * mu], su = rc[2 * mu + 1];
-      const float pv = P[(size_t)oh * K + ih], qv = Q[(size_t)oh * K + ih];
-      if (ro >= 0 && ko >= 0) w = cm * cu * pv + sm * su * qv;
-      else if (ro >= 0) w = -cm * su * pv + sm * cu * qv;
-      else if (ko >= 0) w = -sm * cu * pv + cm * su * qv;
-      else w = sm * su * pv + cm * cu * qv;
-    }
+    if (ro >= 0 && ko >= 0) w = P[(size_t)ro * K + ko];
+    else if (ro <= -2 && ko <= -2) w = Q[(size_t)(-ro - 2) * K + (-ko - 2)];
     const float h = tc::to_tf32(w);
-    const size_t at = ((size_t)o * ldr + r) * ldr + k;
+    const size_t at = ((size_t)ct * ldr + r) * ldr + k;
     whi[at] = h;
     wlo[at] = tc::to_tf32(w - h);
   }
 }
 
+// unrotated source rows in real-coordinate order (FP32), ldr = 32 NC floats per (box, type)
+__global__ void k_tc_pack_raw(const float2 *M, int64_t nrows, int K, int p, int ldr, float *raw) {
+  const int64_t total = nrows * ldr;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / ldr;
+    const int code = tc_remap((int)(e % ldr), K, p);
+    raw[e] = code >= 0 ? M[b * K + code].x : (code <= -2 ? M[b * K + (-code - 2)].y : 0.f);
+  }
+}
+
 struct TJob {
-  const float *ahi, *alo;   // [nsb][ldr]
-  const float *whi, *wlo;   // [NOFF][ldr][ldr]
+  const float *raw;         // source rows [nsb][ntypes][ldr], unrotated real coordinates
+  const float *whi, *wlo;   // [ncls][ntypes][ldr][ldr]
+  const float *rot;         // [NOFF][PMAX+1][2] cos, sin of m phi
   const int32_t *vlist;     // [ntb][NOFF]
   const int32_t *cls_of;    // [NOFF]
+  const int32_t *tlist;     // target boxes (nullptr: octant or plain tiles over 0..ntb-1)
+  const uint32_t *d_ntl;    // number of entries of tlist (device)
   float2 *L;                // partial sums [ntb][M2L_NSLOT][K]
   int64_t ntb, item0;
-  int slot0, pad;
+  int slot0, ntypes;
   const uint32_t *pstart, *pcount;  // octant tiles (nullptr: plain tiles of 128)
   const uint64_t *ckey;
   int64_t npar;
 };
+constexpr int TC_MAXSTEP = 49 * 2 * MAXLAYER;
 
 constexpr int TC_ROWS = 128;
 constexpr int TC_WAIT = 1 << 22;  // mbarrier polls before the kernel reports a timeout
@@ -1374,10 +1377,6 @@ __host__ __device__ constexpr int tc_nst(int NC) { return NC <= 5 ? 3 : 2; }
 __host__ __device__ constexpr size_t tc_stage_bytes(int NC) { return (size_t)2 * (TC_ROWS + 32 * NC) * 128; }
 static size_t tc_smem(int NC) { return tc_nst(NC) * tc_stage_bytes(NC) + 1024; }
 
-// The tensor core's FP32 accumulation loses precision over long MMA chains, so every offset
-// accumulates in a fresh TMEM accumulator (a 32NC-term dot product per output, in 3 x NC x 4
-// MMAs) and is then folded into FP32 registers, one row per thread; two accumulators alternate
-// so that folding offset i overlaps the MMAs of offset i + 1.
 template <int NC>
 __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, int K, int p, int *status) {
   constexpr int N = 32 * NC, NST = tc_nst(NC);
@@ -1387,7 +1386,8 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   extern __shared__ __align__(16) unsigned char tcsm[];  // base rounded up to 1024 below
   unsigned char *sbase = (unsigned char *)(((uintptr_t)tcsm + 1023) & ~(uintptr_t)1023);
   __shared__ int tid_[TC_ROWS];
-  __shared__ int steps[49];
+  __shared__ int steps[TC_MAXSTEP];  // (offset << 4) | source type
+  __shared__ int remap_s[N];
   __shared__ int nsteps;
   __shared__ unsigned hasmask[2];
   __shared__ uint64_t mbar[NST], accbar[2];
@@ -1401,11 +1401,17 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   const int64_t local = (int64_t)blockIdx.x - J.item0;
   const int slice = (int)(local % M2L_NSLICE);
   const int64_t ti = local / M2L_NSLICE;
-  if (J.pstart ? (ti >> 3) * TC_ROWS >= J.npar : ti * TC_ROWS >= J.ntb) return;
+  const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
+  if (J.pstart ? (ti >> 3) * TC_ROWS >= J.npar : ti * TC_ROWS >= ntl) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntypes = J.ntypes;
+  for (int c = tid; c < N; c += 128) remap_s[c] = tc_remap(c, K, p);
   {
     int t = -1;
-    if (J.pstart) {
+    if (J.tlist) {
+      const int64_t j = ti * TC_ROWS + tid;
+      if (j < ntl) t = J.tlist[j];
+    } else if (J.pstart) {
       const int oct = (int)(ti & 7);
       const int64_t P = (ti >> 3) * TC_ROWS + tid;
       if (P < J.npar) {
@@ -1433,7 +1439,8 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   if (tid == 0) {
     int n = 0;
     for (int k = 0; k < 49; ++k)
-      if (hasmask[k >> 5] & (1u << (k & 31))) steps[n++] = slice * 49 + k;
+      if (hasmask[k >> 5] & (1u << (k & 31)))
+        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * 49 + k) << 4) | tau;
     nsteps = n;
   }
   __syncthreads();
@@ -1450,24 +1457,37 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tbase, lanebase = (uint32_t)(warp * 32) << 16;
-  const int S = ns * NC;  // stages: (offset, K-chunk)
+  const int S = ns * NC;  // stages: (step, K-chunk)
   const int myt = tid_[tid];
+  const int NI2 = 2 * (K - (p + 1));  // columns holding (Re, Im) pairs
   constexpr uint32_t IDESC = tc::idesc_tf32(TC_ROWS, N);
   float racc[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) racc[j] = 0.f;
-  // fold the accumulator of offset index oi into racc (whole CTA; false on timeout)
-  auto fold = [&](int oi) -> bool {
-    const bool ok = tc::mbar_wait(&accbar[oi & 1], (uint32_t)((oi >> 1) & 1), TC_WAIT);
+  // fold the accumulator of step i into racc after the output rotation e^{-i m phi}
+  auto fold = [&](int i) -> bool {
+    const bool ok = tc::mbar_wait(&accbar[i & 1], (uint32_t)((i >> 1) & 1), TC_WAIT);
     if (ok) {
       tc::fence_after();
-      const uint32_t col = (uint32_t)((oi & 1) * N);
+      const float *rc = J.rot + (size_t)(steps[i] >> 4) * (PMAX + 1) * 2;
+      const uint32_t col = (uint32_t)((i & 1) * N);
 #pragma unroll
       for (int c0 = 0; c0 < N; c0 += 8) {
         float v[8];
         tc::tmem_ld8(tmem + lanebase + col + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) racc[c0 + j] += v[j];
+        for (int j = 0; j < 8; j += 2) {
+          const int c = c0 + j;
+          if (c < NI2) {
+            const int m = cK.mof[remap_s[c]];
+            const float cm = __ldg(rc + 2 * m), sm = __ldg(rc + 2 * m + 1);
+            racc[c] += cm * v[j] + sm * v[j + 1];
+            racc[c + 1] += cm * v[j + 1] - sm * v[j];
+          } else {
+            racc[c] += v[j];
+            racc[c + 1] += v[j + 1];
+          }
+        }
       }
       tc::fence_before();
     }
@@ -1486,30 +1506,29 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
           break;
         }
       }
-      const int o = steps[s / NC], kc = s % NC;
+      const int o = steps[s / NC] >> 4, tau = steps[s / NC] & 15, kc = s % NC;
       if (o != cur_o) {
         cur_o = o;
         my_src = myt >= 0 ? J.vlist[(size_t)myt * NOFF + o] : -1;
       }
       unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
       unsigned char *Ah = st, *Al = st + SA, *Bh = st + 2 * SA, *Bl = st + 2 * SA + SB;
+      // B and this thread's source row chunk, both asynchronous
       {
-        const bool v = my_src >= 0;
-        const float *gh = J.ahi + (size_t)(v ? my_src : 0) * N + kc * 32;
-        const float *gl = J.alo + (size_t)(v ? my_src : 0) * N + kc * 32;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          cp_async16(Ah + tc::swz16(tid, u), gh + 4 * u, v);
-          cp_async16(Al + tc::swz16(tid, u), gl + 4 * u, v);
-        }
-      }
-      {
-        const float *wh = J.whi + (size_t)o * N * N + kc * 32, *wl = J.wlo + (size_t)o * N * N + kc * 32;
+        const size_t ct = (size_t)J.cls_of[o] * ntypes + tau;
+        const float *wh = J.whi + ct * N * N + kc * 32, *wl = J.wlo + ct * N * N + kc * 32;
         for (int e = tid; e < N * 8; e += 128) {
           const int r = e >> 3, u = e & 7;
           cp_async16(Bh + tc::swz16(r, u), wh + (size_t)r * N + 4 * u, true);
           cp_async16(Bl + tc::swz16(r, u), wl + (size_t)r * N + 4 * u, true);
         }
+      }
+      {
+        // this thread's source row chunk, unrotated, into the A-hi slots (rotated at consumption)
+        const bool v = my_src >= 0;
+        const float *g = J.raw + ((size_t)(v ? my_src : 0) * ntypes + tau) * N + kc * 32;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) cp_async16(Ah + tc::swz16(tid, u), g + 4 * u, v);
       }
     }
     cp_commit();
@@ -1517,16 +1536,52 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
     if (sc >= 0) {
       if (NST == 3) asm volatile("cp.async.wait_group 2;\n" ::);
       else asm volatile("cp.async.wait_group 1;\n" ::);
+      const int si = sc / NC, kc = sc % NC;
+      {
+        // rotate this thread's row by e^{i mu phi} and split it into TF32 hi (in place) + lo
+        unsigned char *st = sbase + (size_t)(sc % NST) * tc_stage_bytes(NC);
+        unsigned char *Ah = st, *Al = st + SA;
+        const float *rc = J.rot + (size_t)(steps[si] >> 4) * (PMAX + 1) * 2;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float4 x = *(float4 *)(Ah + tc::swz16(tid, u));
+          const int c = kc * 32 + 4 * u;
+          if (c < NI2) {
+            const int m0 = cK.mof[remap_s[c]];
+            const float c0 = __ldg(rc + 2 * m0), s0 = __ldg(rc + 2 * m0 + 1);
+            const float xr = c0 * x.x - s0 * x.y, xi = s0 * x.x + c0 * x.y;
+            x.x = xr;
+            x.y = xi;
+          }
+          if (c + 2 < NI2) {
+            const int m1 = cK.mof[remap_s[c + 2]];
+            const float c1 = __ldg(rc + 2 * m1), s1 = __ldg(rc + 2 * m1 + 1);
+            const float xr = c1 * x.z - s1 * x.w, xi = s1 * x.z + c1 * x.w;
+            x.z = xr;
+            x.w = xi;
+          }
+          float4 h4v, l4v;
+          h4v.x = tc::to_tf32(x.x);
+          h4v.y = tc::to_tf32(x.y);
+          h4v.z = tc::to_tf32(x.z);
+          h4v.w = tc::to_tf32(x.w);
+          l4v.x = tc::to_tf32(x.x - h4v.x);
+          l4v.y = tc::to_tf32(x.y - h4v.y);
+          l4v.z = tc::to_tf32(x.z - h4v.z);
+          l4v.w = tc::to_tf32(x.w - h4v.w);
+          *(float4 *)(Ah + tc::swz16(tid, u)) = h4v;
+          *(float4 *)(Al + tc::swz16(tid, u)) = l4v;
+        }
+      }
       tc::fence_async_smem();
       __syncthreads();
-      const int oi = sc / NC, kc = sc % NC;
       if (tid == 0) {
         tc::fence_after();
         const int b = sc % NST;
         unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
         const uint32_t ah = tc::smem_u32(st), al = ah + (uint32_t)SA, bh = ah + 2 * (uint32_t)SA,
                        bl = bh + (uint32_t)SB;
-        const uint32_t dacc = tmem + (uint32_t)((oi & 1) * N);
+        const uint32_t dacc = tmem + (uint32_t)((si & 1) * N);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t off = kk * 32;
@@ -1535,12 +1590,12 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
           tc::mma_tf32(dacc, tc::sdesc(al + off), tc::sdesc(bh + off), IDESC, 1u);
         }
         tc::commit(&mbar[b]);
-        if (kc == NC - 1) tc::commit(&accbar[oi & 1]);
+        if (kc == NC - 1) tc::commit(&accbar[si & 1]);
       }
       committed = sc;
-      // offset oi is queued in full: fold offset oi - 1, whose accumulator offset oi + 1 reuses
-      if (kc == NC - 1 && oi >= 1) {
-        if (__syncthreads_or(!fold(oi - 1))) {
+      // step si is queued in full: fold step si - 1, whose accumulator step si + 1 reuses
+      if (kc == NC - 1 && si >= 1) {
+        if (__syncthreads_or(!fold(si - 1))) {
           fail = true;
           break;
         }
@@ -1562,7 +1617,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
       float2 *Lrow = J.L + ((size_t)t * M2L_NSLOT + J.slot0 + slice) * K;
 #pragma unroll
       for (int c = 0; c < N; ++c) {
-        const int code = tc_remap(c, K, p);
+        const int code = remap_s[c];
         if (code >= 0) {
           Lrow[code].x = racc[c];
           if (cK.mof[code] == 0) Lrow[code].y = 0.f;
@@ -1703,21 +1758,22 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
       rjobs.push_back(r);
       relem += r.n;
       if (dofree && use_tc) {
-        // tensor-core path: pack the level's source rows and the offsets' real operators
+        // tensor-core path: the level's class operators as TF32 hi/lo real matrices
         const int N = 32 * tc_nc;
-        float *ahi = c.arena.get<float>((size_t)ntb * N), *alo = c.arena.get<float>((size_t)ntb * N);
-        const int64_t tot = ntb * N;
-        k_tc_pack_rows<<<(unsigned)std::min<int64_t>(4096, (tot + 255) / 256), 256, 0, c.stream>>>(
-            (const float2 *)g.Mfree[l], ntb, c.K, c.p, N, ahi, alo);
+        float *whi = c.arena.get<float>((size_t)NFREE_CLS * N * N), *wlo = c.arena.get<float>((size_t)NFREE_CLS * N * N);
+        k_tc_pack_w<<<dim3(NFREE_CLS, 4), 256, 0, c.stream>>>((const float *)g.op_free[l], NFREE_CLS, c.K, c.p, N,
+                                                               whi, wlo);
         LPB_LAUNCH();
-        float *whi = c.arena.get<float>((size_t)NOFF * N * N), *wlo = c.arena.get<float>((size_t)NOFF * N * N);
-        k_tc_pack_w<<<dim3(NOFF, 8), 256, 0, c.stream>>>((const float *)g.op_free[l], tb.cls_free,
-                                                          (const float *)tb.rot, c.K, c.p, N, whi, wlo);
+        c.launches++;
+        float *raw = c.arena.get<float>((size_t)ntb * N);
+        k_tc_pack_raw<<<(unsigned)std::min<int64_t>(4096, (ntb * N + 255) / 256), 256, 0, c.stream>>>(
+            (const float2 *)g.Mfree[l], ntb, c.K, c.p, N, raw);
         LPB_LAUNCH();
-        c.launches += 2;
+        c.launches++;
         TJob j;
-        j.ahi = ahi; j.alo = alo; j.whi = whi; j.wlo = wlo; j.vlist = g.vfree[l]; j.cls_of = tb.cls_free;
-        j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = 0; j.pad = 0;
+        j.raw = raw; j.whi = whi; j.wlo = wlo; j.rot = (const float *)tb.rot;
+        j.vlist = g.vfree[l]; j.cls_of = tb.cls_free; j.tlist = nullptr; j.d_ntl = nullptr;
+        j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = 0; j.ntypes = 1;
         const Level *par = l >= 3 ? &g.T.lev[l - 1] : nullptr;
         j.pstart = par ? par->start : nullptr;
         j.pcount = par ? par->count : nullptr;
@@ -1730,14 +1786,40 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
         add(nullptr, nullptr, ntb, g.vfree[l], tb.cls_free, g.Mfree[l], g.op_free[l], part, 1, 0,
             l >= 3 ? &g.T.lev[l - 1] : nullptr, &g.T.lev[l]);
       }
-      if (react_far && g.vreact[l])
+      if (react_far && g.vreact[l] && use_tc && g.ntypes <= 16) {
+        // tensor-core reaction path: class operators per (class, source type)
+        const int N = 32 * tc_nc;
+        const int nct = NREACT_CLS * g.ntypes;
+        float *whi = c.arena.get<float>((size_t)nct * N * N), *wlo = c.arena.get<float>((size_t)nct * N * N);
+        k_tc_pack_w<<<dim3(nct, 4), 256, 0, c.stream>>>((const float *)g.op_react[l], nct, c.K, c.p, N, whi, wlo);
+        LPB_LAUNCH();
+        c.launches++;
+        const int64_t nir = g.I.lev[l].n * g.ntypes;
+        float *raw = c.arena.get<float>((size_t)nir * N);
+        k_tc_pack_raw<<<(unsigned)std::min<int64_t>(4096, (nir * N + 255) / 256), 256, 0, c.stream>>>(
+            (const float2 *)g.Mimg[l], nir, c.K, c.p, N, raw);
+        LPB_LAUNCH();
+        c.launches++;
+        for (int kt = 0; kt < 3; ++kt) {
+          TJob j;
+          j.raw = raw; j.whi = whi; j.wlo = wlo; j.rot = (const float *)tb.rot;
+          j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF;
+          j.tlist = g.rows[l] + (size_t)kt * ntb; j.d_ntl = g.nrows[l] + kt;
+          j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = M2L_NSLICE; j.ntypes = g.ntypes;
+          j.pstart = nullptr; j.pcount = nullptr; j.ckey = nullptr; j.npar = 0;
+          titems += ((ntb + TC_ROWS - 1) / TC_ROWS) * M2L_NSLICE;
+          tjobs.push_back(j);
+        }
+      } else if (react_far && g.vreact[l]) {
         for (int kt = 0; kt < 3; ++kt)
           add(g.rows[l] + (size_t)kt * ntb, g.nrows[l] + kt, ntb, g.vreact[l],
               tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], part, g.ntypes, M2L_NSLICE,
               nullptr, nullptr);
+      }
     }
   }
   if (jobs.empty() && tjobs.empty()) return;
+  prof_mark(c, "m2l_prep");
   if (!tjobs.empty()) {
     TJob *dj = c.arena.get<TJob>(tjobs.size());
     LPB_CUDA(cudaMemcpyAsync(dj, tjobs.data(), sizeof(TJob) * tjobs.size(), cudaMemcpyHostToDevice, c.stream));
@@ -1758,6 +1840,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     }
     LPB_LAUNCH();
     c.launches++;
+    prof_mark(c, "m2l_tc");
   }
   auto launch_reduce = [&]() {
     RJob *dr = c.arena.get<RJob>(rjobs.size());
@@ -1789,6 +1872,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     k_m2l_f32<<<(unsigned)it, 256, smem, c.stream>>>(dj, (int)jobs.size(), (const float *)tb.rot, c.K);
     LPB_LAUNCH();
     c.launches++;
+    prof_mark(c, "m2l_simt");
     launch_reduce();
     return;
   }
@@ -1818,6 +1902,7 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   }
   PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
   if (dofree) {
+    prof_mark(c, "downward");
     if (sizeof(T) == 4) {
       const unsigned nb = (unsigned)g.T.lev[D].n;
       const int64_t np = g.T.np;
@@ -1840,6 +1925,7 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
       LPB_LAUNCH();
       c.launches++;
     }
+    prof_mark(c, "p2p");
   }
   if (react_near && g.ureact && g.nodes) {
     k_p2p_react<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(
