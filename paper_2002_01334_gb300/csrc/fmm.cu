@@ -1370,7 +1370,7 @@ struct TJob {
 };
 constexpr int TC_MAXSTEP = 49 * 2 * MAXLAYER;
 
-constexpr int TC_ROWS = 128;
+constexpr int TC_ROWS = 128, TC_THREADS = 256;
 constexpr int TC_WAIT = 1 << 22;  // mbarrier polls before the kernel reports a timeout
 
 __host__ __device__ constexpr int tc_nst(int NC) { return NC <= 5 ? 3 : 2; }
@@ -1378,7 +1378,7 @@ __host__ __device__ constexpr size_t tc_stage_bytes(int NC) { return (size_t)2 *
 static size_t tc_smem(int NC) { return tc_nst(NC) * tc_stage_bytes(NC) + 1024; }
 
 template <int NC>
-__global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, int K, int p, int *status) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int njobs, int K, int p, int *status) {
   constexpr int N = 32 * NC, NST = tc_nst(NC);
   constexpr int TCOLS = 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256));
   static_assert(2 * N <= 256, "two accumulators of N columns");
@@ -1387,7 +1387,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   unsigned char *sbase = (unsigned char *)(((uintptr_t)tcsm + 1023) & ~(uintptr_t)1023);
   __shared__ int tid_[TC_ROWS];
   __shared__ int steps[TC_MAXSTEP];  // (offset << 4) | source type
-  __shared__ int remap_s[N];
+  __shared__ int remap_s[N], mcol[N];  // coordinate -> half index code; m of that coefficient
   __shared__ int nsteps;
   __shared__ unsigned hasmask[2];
   __shared__ uint64_t mbar[NST], accbar[2];
@@ -1403,10 +1403,16 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   const int64_t ti = local / M2L_NSLICE;
   const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
   if (J.pstart ? (ti >> 3) * TC_ROWS >= J.npar : ti * TC_ROWS >= ntl) return;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // thread = (row, half): row = target slot and TMEM lane, half = which 4 of a chunk's 8 units and
+  // which half of the accumulator columns it handles
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, row = tid & (TC_ROWS - 1), hf = tid >> 7;
   const int ntypes = J.ntypes;
-  for (int c = tid; c < N; c += 128) remap_s[c] = tc_remap(c, K, p);
-  {
+  for (int c = tid; c < N; c += TC_THREADS) {
+    const int code = tc_remap(c, K, p);
+    remap_s[c] = code;
+    mcol[c] = code == -1 ? 0 : cK.mof[code >= 0 ? code : -code - 2];
+  }
+  if (tid < TC_ROWS) {
     int t = -1;
     if (J.tlist) {
       const int64_t j = ti * TC_ROWS + tid;
@@ -1427,7 +1433,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   }
   if (tid < 2) hasmask[tid] = 0u;
   __syncthreads();
-  {
+  if (tid < TC_ROWS) {
     const int t = tid_[tid];
     if (t >= 0)
       for (int k = 0; k < 49; ++k) {
@@ -1458,34 +1464,35 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   tc::fence_after();
   const uint32_t tmem = tbase, lanebase = (uint32_t)(warp * 32) << 16;
   const int S = ns * NC;  // stages: (step, K-chunk)
-  const int myt = tid_[tid];
+  const int myt = tid_[row];
   const int NI2 = 2 * (K - (p + 1));  // columns holding (Re, Im) pairs
   constexpr uint32_t IDESC = tc::idesc_tf32(TC_ROWS, N);
-  float racc[N];
+  constexpr int NH = N / 2;  // accumulator columns per thread
+  float racc[NH];
 #pragma unroll
-  for (int j = 0; j < N; ++j) racc[j] = 0.f;
+  for (int j = 0; j < NH; ++j) racc[j] = 0.f;
   // fold the accumulator of step i into racc after the output rotation e^{-i m phi}
   auto fold = [&](int i) -> bool {
     const bool ok = tc::mbar_wait(&accbar[i & 1], (uint32_t)((i >> 1) & 1), TC_WAIT);
     if (ok) {
       tc::fence_after();
       const float *rc = J.rot + (size_t)(steps[i] >> 4) * (PMAX + 1) * 2;
-      const uint32_t col = (uint32_t)((i & 1) * N);
+      const uint32_t col = (uint32_t)((i & 1) * N + hf * NH);
 #pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 8) {
+      for (int c0 = 0; c0 < NH; c0 += 8) {
         float v[8];
         tc::tmem_ld8(tmem + lanebase + col + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
-          const int c = c0 + j;
+          const int c = hf * NH + c0 + j;
           if (c < NI2) {
-            const int m = cK.mof[remap_s[c]];
+            const int m = mcol[c];
             const float cm = __ldg(rc + 2 * m), sm = __ldg(rc + 2 * m + 1);
-            racc[c] += cm * v[j] + sm * v[j + 1];
-            racc[c + 1] += cm * v[j + 1] - sm * v[j];
+            racc[c0 + j] += cm * v[j] + sm * v[j + 1];
+            racc[c0 + j + 1] += cm * v[j + 1] - sm * v[j];
           } else {
-            racc[c] += v[j];
-            racc[c + 1] += v[j + 1];
+            racc[c0 + j] += v[j];
+            racc[c0 + j + 1] += v[j + 1];
           }
         }
       }
@@ -1496,7 +1503,9 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   bool fail = false;
   int committed = -1;  // last stage whose MMAs were committed
   int cur_o = -1, my_src = -1;
-  for (int s = 0; s < S + NST - 1; ++s) {
+  // stage s is copied at iteration s and consumed (rotated, split, multiplied) at iteration s + 1, so
+  // the MMAs of a stage have until iteration s + NST - 1 before its buffer is refilled
+  for (int s = 0; s < S + 1; ++s) {
     if (s < S) {
       const int b = s % NST;
       if (s >= NST) {
@@ -1517,7 +1526,7 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
       {
         const size_t ct = (size_t)J.cls_of[o] * ntypes + tau;
         const float *wh = J.whi + ct * N * N + kc * 32, *wl = J.wlo + ct * N * N + kc * 32;
-        for (int e = tid; e < N * 8; e += 128) {
+        for (int e = tid; e < N * 8; e += TC_THREADS) {
           const int r = e >> 3, u = e & 7;
           cp_async16(Bh + tc::swz16(r, u), wh + (size_t)r * N + 4 * u, true);
           cp_async16(Bl + tc::swz16(r, u), wl + (size_t)r * N + 4 * u, true);
@@ -1528,33 +1537,33 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
         const bool v = my_src >= 0;
         const float *g = J.raw + ((size_t)(v ? my_src : 0) * ntypes + tau) * N + kc * 32;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) cp_async16(Ah + tc::swz16(tid, u), g + 4 * u, v);
+        for (int u = hf * 4; u < hf * 4 + 4; ++u) cp_async16(Ah + tc::swz16(row, u), g + 4 * u, v);
       }
     }
     cp_commit();
-    const int sc = s - (NST - 1);
+    const int sc = s - 1;
     if (sc >= 0) {
-      if (NST == 3) asm volatile("cp.async.wait_group 2;\n" ::);
-      else asm volatile("cp.async.wait_group 1;\n" ::);
+      asm volatile("cp.async.wait_group 1;\n" ::);
       const int si = sc / NC, kc = sc % NC;
       {
-        // rotate this thread's row by e^{i mu phi} and split it into TF32 hi (in place) + lo
+        // rotate this thread's half row by e^{i mu phi} and split it into TF32 hi (in place) + lo
         unsigned char *st = sbase + (size_t)(sc % NST) * tc_stage_bytes(NC);
         unsigned char *Ah = st, *Al = st + SA;
         const float *rc = J.rot + (size_t)(steps[si] >> 4) * (PMAX + 1) * 2;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float4 x = *(float4 *)(Ah + tc::swz16(tid, u));
+        for (int uu = 0; uu < 4; ++uu) {
+          const int u = hf * 4 + uu;
+          float4 x = *(float4 *)(Ah + tc::swz16(row, u));
           const int c = kc * 32 + 4 * u;
           if (c < NI2) {
-            const int m0 = cK.mof[remap_s[c]];
+            const int m0 = mcol[c];
             const float c0 = __ldg(rc + 2 * m0), s0 = __ldg(rc + 2 * m0 + 1);
             const float xr = c0 * x.x - s0 * x.y, xi = s0 * x.x + c0 * x.y;
             x.x = xr;
             x.y = xi;
           }
           if (c + 2 < NI2) {
-            const int m1 = cK.mof[remap_s[c + 2]];
+            const int m1 = mcol[c + 2];
             const float c1 = __ldg(rc + 2 * m1), s1 = __ldg(rc + 2 * m1 + 1);
             const float xr = c1 * x.z - s1 * x.w, xi = s1 * x.z + c1 * x.w;
             x.z = xr;
@@ -1569,8 +1578,8 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
           l4v.y = tc::to_tf32(x.y - h4v.y);
           l4v.z = tc::to_tf32(x.z - h4v.z);
           l4v.w = tc::to_tf32(x.w - h4v.w);
-          *(float4 *)(Ah + tc::swz16(tid, u)) = h4v;
-          *(float4 *)(Al + tc::swz16(tid, u)) = l4v;
+          *(float4 *)(Ah + tc::swz16(row, u)) = h4v;
+          *(float4 *)(Al + tc::swz16(row, u)) = l4v;
         }
       }
       tc::fence_async_smem();
@@ -1612,17 +1621,17 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const TJob *jobs, int njobs, 
   if (fail) {
     if (tid == 0) atomicExch(status, LPBFMM_ERR_TIMEOUT);
   } else {
-    const int t = tid_[tid];  // this thread's row
+    const int t = tid_[row];
     if (t >= 0) {
       float2 *Lrow = J.L + ((size_t)t * M2L_NSLOT + J.slot0 + slice) * K;
 #pragma unroll
-      for (int c = 0; c < N; ++c) {
-        const int code = remap_s[c];
+      for (int j = 0; j < NH; ++j) {
+        const int code = remap_s[hf * NH + j];
         if (code >= 0) {
-          Lrow[code].x = racc[c];
-          if (cK.mof[code] == 0) Lrow[code].y = 0.f;
+          Lrow[code].x = racc[j];
+          if (mcol[hf * NH + j] == 0) Lrow[code].y = 0.f;
         } else if (code <= -2) {
-          Lrow[-code - 2].y = racc[c];
+          Lrow[-code - 2].y = racc[j];
         }
       }
     }
@@ -1832,7 +1841,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
                                     (int)tc_smem(NCV)));                                                     \
       attr = true;                                                                                           \
     }                                                                                                        \
-    k_m2l_tc<NCV><<<(unsigned)titems, 128, tc_smem(NCV), c.stream>>>(dj, (int)tjobs.size(), c.K, c.p, c.status); \
+    k_m2l_tc<NCV><<<(unsigned)titems, TC_THREADS, tc_smem(NCV), c.stream>>>(dj, (int)tjobs.size(), c.K, c.p, c.status); \
     break;                                                                                                   \
   }
       LPB_TC_CASE(1) LPB_TC_CASE(2) LPB_TC_CASE(3) LPB_TC_CASE(4)
