@@ -1323,16 +1323,21 @@ __host__ __device__ __forceinline__ int tc_remap(int c, int K, int p) {
   return n <= p ? n * (n + 1) / 2 : -1;
 }
 
-// W_c for every class and source type: [ncls * ntypes][ldr rows (outputs)][ldr cols], hi and lo
-__global__ void k_tc_pack_w(const float *ops, int ncls_types, int K, int p, int ldr, float *whi, float *wlo) {
+// W_c for every class and source type: [ncls * ntypes][ldr rows (outputs)][ldr cols], hi and lo;
+// classes that used[] marks absent at this level are skipped
+__global__ void k_tc_pack_w(const float *ops, int ncls_types, int ntypes, const uint8_t *used, int K, int p, int ldr,
+                            float *whi, float *wlo) {
+  __shared__ int code[256];
   const int ct = blockIdx.x;
-  if (ct >= ncls_types) return;
+  if (ct >= ncls_types || (used && !used[ct / ntypes])) return;
+  for (int c = threadIdx.x; c < ldr; c += blockDim.x) code[c] = tc_remap(c, K, p);
+  __syncthreads();
   const size_t KK = (size_t)K * K;
   const float *P = ops + (size_t)ct * 2 * KK, *Q = P + KK;
   const int total = ldr * ldr;
   for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < total; e += gridDim.y * blockDim.x) {
     const int r = e / ldr, k = e % ldr;
-    const int ro = tc_remap(r, K, p), ko = tc_remap(k, K, p);
+    const int ro = code[r], ko = code[k];
     float w = 0.f;
     if (ro >= 0 && ko >= 0) w = P[(size_t)ro * K + ko];
     else if (ro <= -2 && ko <= -2) w = Q[(size_t)(-ro - 2) * K + (-ko - 2)];
@@ -1770,8 +1775,8 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
         // tensor-core path: the level's class operators as TF32 hi/lo real matrices
         const int N = 32 * tc_nc;
         float *whi = c.arena.get<float>((size_t)NFREE_CLS * N * N), *wlo = c.arena.get<float>((size_t)NFREE_CLS * N * N);
-        k_tc_pack_w<<<dim3(NFREE_CLS, 4), 256, 0, c.stream>>>((const float *)g.op_free[l], NFREE_CLS, c.K, c.p, N,
-                                                               whi, wlo);
+        k_tc_pack_w<<<dim3(NFREE_CLS, 4), 256, 0, c.stream>>>((const float *)g.op_free[l], NFREE_CLS, 1, nullptr,
+                                                               c.K, c.p, N, whi, wlo);
         LPB_LAUNCH();
         c.launches++;
         float *raw = c.arena.get<float>((size_t)ntb * N);
@@ -1800,7 +1805,8 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
         const int N = 32 * tc_nc;
         const int nct = NREACT_CLS * g.ntypes;
         float *whi = c.arena.get<float>((size_t)nct * N * N), *wlo = c.arena.get<float>((size_t)nct * N * N);
-        k_tc_pack_w<<<dim3(nct, 4), 256, 0, c.stream>>>((const float *)g.op_react[l], nct, c.K, c.p, N, whi, wlo);
+        k_tc_pack_w<<<dim3(nct, 4), 256, 0, c.stream>>>((const float *)g.op_react[l], nct, g.ntypes, g.used[l], c.K,
+                                                        c.p, N, whi, wlo);
         LPB_LAUNCH();
         c.launches++;
         const int64_t nir = g.I.lev[l].n * g.ntypes;
