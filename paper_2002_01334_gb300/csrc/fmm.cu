@@ -17,6 +17,33 @@ struct Consts {
   int mof[KHALF_MAX];
 };
 __constant__ Consts cK;
+// FP32 copies of the recurrence constants: the FP32 kernels read these directly (a conversion
+// from FP64 runs on the FP64 pipe, ~2 lanes per clock per SM on this GPU)
+struct ConstsF {
+  float A[PMAX + 2][PMAX + 2], B[PMAX + 2][PMAX + 2];
+  float sect[PMAX + 2], sub[PMAX + 2];
+  float gz[PMAX + 2][PMAX + 2], ga[PMAX + 2][PMAX + 2], gb[PMAX + 2][PMAX + 2];
+};
+__constant__ ConstsF cKf;
+template <typename T> struct CK;
+template <> struct CK<float> {
+  static __device__ __forceinline__ float A(int n, int m) { return cKf.A[n][m]; }
+  static __device__ __forceinline__ float B(int n, int m) { return cKf.B[n][m]; }
+  static __device__ __forceinline__ float sect(int m) { return cKf.sect[m]; }
+  static __device__ __forceinline__ float sub(int m) { return cKf.sub[m]; }
+  static __device__ __forceinline__ float gz(int n, int m) { return cKf.gz[n][m]; }
+  static __device__ __forceinline__ float ga(int n, int m) { return cKf.ga[n][m]; }
+  static __device__ __forceinline__ float gb(int n, int m) { return cKf.gb[n][m]; }
+};
+template <> struct CK<double> {
+  static __device__ __forceinline__ double A(int n, int m) { return cK.A[n][m]; }
+  static __device__ __forceinline__ double B(int n, int m) { return cK.B[n][m]; }
+  static __device__ __forceinline__ double sect(int m) { return cK.sect[m]; }
+  static __device__ __forceinline__ double sub(int m) { return cK.sub[m]; }
+  static __device__ __forceinline__ double gz(int n, int m) { return cK.gz[n][m]; }
+  static __device__ __forceinline__ double ga(int n, int m) { return cK.ga[n][m]; }
+  static __device__ __forceinline__ double gb(int n, int m) { return cK.gb[n][m]; }
+};
 
 void upload_consts(cudaStream_t s) {
   static Consts h;
@@ -42,6 +69,19 @@ void upload_consts(cudaStream_t s) {
   for (int n = 0; n <= PMAX; ++n)
     for (int m = 0; m <= n; ++m) h.mof[hidx(n, m)] = m;
   LPB_CUDA(cudaMemcpyToSymbolAsync(cK, &h, sizeof(Consts), 0, cudaMemcpyHostToDevice, s));
+  static ConstsF hf;
+  for (int n = 0; n <= PMAX + 1; ++n) {
+    for (int m = 0; m <= PMAX + 1; ++m) {
+      hf.A[n][m] = (float)h.A[n][m];
+      hf.B[n][m] = (float)h.B[n][m];
+      hf.gz[n][m] = (float)h.gz[n][m];
+      hf.ga[n][m] = (float)h.ga[n][m];
+      hf.gb[n][m] = (float)h.gb[n][m];
+    }
+    hf.sect[n] = (float)h.sect[n];
+    hf.sub[n] = (float)h.sub[n];
+  }
+  LPB_CUDA(cudaMemcpyToSymbolAsync(cKf, &hf, sizeof(ConstsF), 0, cudaMemcpyHostToDevice, s));
   LPB_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -115,7 +155,7 @@ __global__ void k_p2m(const uint32_t *d_nseg, const uint32_t *seg_start, const u
     for (int m = 0; m <= PT; ++m) {
       if (m > p) break;
       if (m > 0) {
-        const T s = (T)cK.sect[m];
+        const T s = CK<T>::sect(m);
         const T2 t = T2{Rmm.x * rx - Rmm.y * ry, Rmm.x * ry + Rmm.y * rx};
         Rmm = T2{s * t.x, s * t.y};
       }
@@ -125,9 +165,9 @@ __global__ void k_p2m(const uint32_t *d_nseg, const uint32_t *seg_start, const u
         if (n > p) break;
         T2 R;
         if (n == m) R = Rmm;
-        else if (n == m + 1) { const T s = (T)cK.sub[m] * rz; R = T2{s * p1.x, s * p1.y}; }
+        else if (n == m + 1) { const T s = CK<T>::sub(m) * rz; R = T2{s * p1.x, s * p1.y}; }
         else {
-          const T a = (T)cK.A[n][m] * rz, b = (T)cK.B[n][m] * r2;
+          const T a = CK<T>::A(n, m) * rz, b = CK<T>::B(n, m) * r2;
           R = T2{a * p1.x - b * p2.x, a * p1.y - b * p2.y};
         }
         p2 = p1;
@@ -685,7 +725,7 @@ __global__ void k_l2p(const uint32_t *d_nb, const uint64_t *bkey, const uint32_t
     for (int m = 0; m <= PT; ++m) {
       if (m > p) break;
       if (m > 0) {
-        const T s = (T)cK.sect[m];
+        const T s = CK<T>::sect(m);
         const T2 t = T2{Rmm.x * rx - Rmm.y * ry, Rmm.x * ry + Rmm.y * rx};
         Rmm = T2{s * t.x, s * t.y};
       }
@@ -696,9 +736,9 @@ __global__ void k_l2p(const uint32_t *d_nb, const uint64_t *bkey, const uint32_t
         if (n > p) break;
         T2 R;
         if (n == m) R = Rmm;
-        else if (n == m + 1) { const T s = (T)cK.sub[m] * rz; R = T2{s * p1.x, s * p1.y}; }
+        else if (n == m + 1) { const T s = CK<T>::sub(m) * rz; R = T2{s * p1.x, s * p1.y}; }
         else {
-          const T a = (T)cK.A[n][m] * rz, b = (T)cK.B[n][m] * r2;
+          const T a = CK<T>::A(n, m) * rz, b = CK<T>::B(n, m) * r2;
           R = T2{a * p1.x - b * p2.x, a * p1.y - b * p2.y};
         }
         p2 = p1;
@@ -710,15 +750,15 @@ __global__ void k_l2p(const uint32_t *d_nb, const uint64_t *bkey, const uint32_t
         if (n < p) {
           const T in1 = it[n + 1];
           const T2 Lz = Lw[hidx(n + 1, m)];
-          Gz += wm * in1 * (T)cK.gz[n][m] * (Lz.x * R.x - Lz.y * R.y);
+          Gz += wm * in1 * CK<T>::gz(n, m) * (Lz.x * R.x - Lz.y * R.y);
           if (m >= 1) {
             const T2 La = Lw[hidx(n + 1, m - 1)];
-            const T ca = in1 * (T)cK.ga[n][m];
+            const T ca = in1 * CK<T>::ga(n, m);
             Gpr += ca * (La.x * R.x - La.y * R.y);
             Gpi += ca * (La.x * R.y + La.y * R.x);
           }
           const T2 Lb = Lw[hidx(n + 1, m + 1)];
-          const T cb = in1 * (T)cK.gb[n][m];
+          const T cb = in1 * CK<T>::gb(n, m);
           // - conj(Lb R)
           Gpr -= cb * (Lb.x * R.x - Lb.y * R.y);
           Gpi += cb * (Lb.x * R.y + Lb.y * R.x);

@@ -404,6 +404,7 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
   extern __shared__ double asm_sm[];
   double *Sf = asm_sm;  // [(KT+1)^2 * 4]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}
   __shared__ double smm[PMAX + 1], rdf[PMAX + 1];
+  __shared__ double fa[KHALF_MAX], fb[KHALF_MAX];  // prefactor A(o, i) = fa[o] fb[i]
   const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   for (int e = threadIdx.x; e < (KT + 1) * (KT + 1) * 4; e += blockDim.x) {
     const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
@@ -417,6 +418,15 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     for (int n = 1; n <= p; ++n) rdf[n] = rdf[n - 1] / (2.0 * n + 1.0);  // 1/(2n+1)!!
   }
   __syncthreads();
+  // fa[o] = smm(m) st^{n-m} / (2n+1)!!,  fb[i] = smm(mu) (-st)^{nu-mu} / ((2nu+1)!! 4 pi h)
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    int n, m;
+    hdecode(e, n, m);
+    const bool odd = (n - m) & 1;
+    fa[e] = smm[m] * rdf[n] * (odd ? (double)D.st : 1.0);
+    fb[e] = smm[m] * rdf[n] * (odd ? -(double)D.st : 1.0) * (0.25 / PI) / D.h;
+  }
+  __syncthreads();
   const int NS = p + 2;
   const size_t KK = (size_t)K * K;
   T *P = out + D.dst + (size_t)cls * D.ntypes * 2 * KK;
@@ -426,9 +436,7 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     hdecode(o, n, m);
     hdecode(i, nu, mu);
     const int ij = 2 * ((n - m) & 1) + ((nu - mu) & 1);
-    double A = smm[m] * smm[mu] * (0.25 / PI) * rdf[n] * rdf[nu] / D.h;
-    if ((n - m) & 1) A *= D.st;                 // st^{n-m}
-    if ((nu - mu) & 1) A *= -D.st;              // (-st)^{nu-mu}
+    const double A = fa[o] * fb[i];
     const int smax = (n - m + 1) / 2 + (nu - mu + 1) / 2;
     const double *cf = D.coef + (size_t)e * NS;
     const int dp = mu - m, dm = mu + m;  // |d| for +mu and -mu
@@ -441,14 +449,16 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
       accp += c * Sf[((Kk * (KT + 1)) + adp) * 4 + ij];
       accm += c * Sf[((Kk * (KT + 1)) + dm) * 4 + ij];
     }
-    if (dp < 0 && (adp & 1)) accp = -accp;
-    if (dm > 0 && (dm & 1)) accm = -accm;   // d = -mu - m < 0
+    // signs: (-1)^|d| for d = mu - m < 0 and for d = -mu - m < 0; (-1)^mu of the -mu term
+    const unsigned long long SGN = 0x8000000000000000ull;
+    const bool fp = dp < 0 && (adp & 1), fm = ((dm > 0 && (dm & 1)) != ((mu & 1) != 0));
+    const double X = __longlong_as_double(__double_as_longlong(accp) ^ (fp ? SGN : 0ull));
+    const double Y = __longlong_as_double(__double_as_longlong(accm) ^ (fm ? SGN : 0ull));
     double Pv, Qv;
-    if (mu == 0) { Pv = A * accp; Qv = 0.0; }
+    if (mu == 0) { Pv = A * X; Qv = 0.0; }
     else {
-      const double sg = (mu & 1) ? -1.0 : 1.0;
-      Pv = A * (accp + sg * accm);
-      Qv = A * (accp - sg * accm);
+      Pv = A * (X + Y);
+      Qv = A * (X - Y);
     }
     P[(size_t)D.tau * 2 * KK + (size_t)o * K + i] = (T)Pv;
     P[(size_t)D.tau * 2 * KK + KK + (size_t)o * K + i] = (T)Qv;
