@@ -198,47 +198,71 @@ __device__ __forceinline__ void rot_of_octant(uint64_t ckey, int m, const T *rot
   s = rot4[(dir * (PMAX + 1) + m) * 2 + 1];
 }
 
+// One CTA per (parent, source type), one thread per output row.  All children's rotated
+// multipoles are staged at once; a thread reads each operator row once per z-half (child octant
+// bit cz) and applies it to the (at most four) children with that cz.
+constexpr int M2M_THREADS = 96;  // >= K for p <= 12 handled in one pass; larger K loops
 template <typename T>
-__global__ void k_m2m(const uint32_t *d_np, const uint32_t *pstart, const uint32_t *pcount, const uint64_t *ckey,
-                      int ntypes, const typename C2<T>::t *Mc, typename C2<T>::t *Mp, const T *ops, const T *rot4,
-                      int K) {
+__global__ void __launch_bounds__(M2M_THREADS) k_m2m(const uint32_t *d_np, const uint32_t *pstart,
+                                                     const uint32_t *pcount, const uint64_t *ckey, int ntypes,
+                                                     const typename C2<T>::t *Mc, typename C2<T>::t *Mp,
+                                                     const T *ops, const T *rot4, int K) {
   typedef typename C2<T>::t T2;
-  __shared__ T xr[KHALF_MAX], xi[KHALF_MAX];
+  __shared__ T xr[8][KHALF_MAX], xi[8][KHALF_MAX];
+  __shared__ int slot[2][4], nslot[2];
+  __shared__ uint64_t ck_s[8];
   const uint32_t box = blockIdx.x, type = blockIdx.y;
   if (box >= *d_np) return;
   const size_t KK = (size_t)K * K;
-  T ar[2] = {0, 0}, ai[2] = {0, 0};
-  const uint32_t c0 = pstart[box], nc = pcount[box];
-  for (uint32_t c = c0; c < c0 + nc; ++c) {
-    const uint64_t ck = ckey[c];
-    const int cz = (int)(ck & 1ull);
-    const T *P = ops + ((size_t)type * 2 + cz) * 2 * KK, *Q = P + KK;
-    for (int e = threadIdx.x; e < K; e += blockDim.x) {
-      T cs, sn;
-      rot_of_octant(ck, cK.mof[e], rot4, cs, sn);
-      const T2 v = Mc[((size_t)c * ntypes + type) * K + e];
-      xr[e] = cs * v.x - sn * v.y;
-      xi[e] = sn * v.x + cs * v.y;
+  const uint32_t c0 = pstart[box], nc = min(pcount[box], 8u);
+  if (threadIdx.x < nc) ck_s[threadIdx.x] = ckey[c0 + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    nslot[0] = nslot[1] = 0;
+    for (uint32_t c = 0; c < nc; ++c) {
+      const int cz = (int)(ck_s[c] & 1ull);
+      slot[cz][nslot[cz]++] = (int)c;
     }
-    __syncthreads();
-    for (int r = 0; r < 2; ++r) {
-      const int i = threadIdx.x + r * blockDim.x;
-      if (i >= K) break;
-      T yr = 0, yi = 0;
-      for (int k = 0; k < K; ++k) {
-        yr += P[(size_t)i * K + k] * xr[k];
-        yi += Q[(size_t)i * K + k] * xi[k];
-      }
-      T cs, sn;
-      rot_of_octant(ck, cK.mof[i], rot4, cs, sn);
-      ar[r] += cs * yr + sn * yi;
-      ai[r] += cs * yi - sn * yr;
-    }
-    __syncthreads();
   }
-  for (int r = 0; r < 2; ++r) {
-    const int i = threadIdx.x + r * blockDim.x;
-    if (i < K) Mp[((size_t)box * ntypes + type) * K + i] = T2{ar[r], ai[r]};
+  for (uint32_t e = threadIdx.x; e < nc * (uint32_t)K; e += blockDim.x) {
+    const int c = (int)(e / K), k = (int)(e % K);
+    T cs, sn;
+    rot_of_octant(ck_s[c], cK.mof[k], rot4, cs, sn);
+    const T2 v = Mc[((size_t)(c0 + c) * ntypes + type) * K + k];
+    xr[c][k] = cs * v.x - sn * v.y;
+    xi[c][k] = sn * v.x + cs * v.y;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const int m = cK.mof[i];
+    T ar = 0, ai = 0;
+    for (int cz = 0; cz < 2; ++cz) {
+      const int ns = nslot[cz];
+      if (ns == 0) continue;
+      const T *P = ops + ((size_t)type * 2 + cz) * 2 * KK + (size_t)i * K, *Q = P + KK;
+      T yr[4] = {0, 0, 0, 0}, yi[4] = {0, 0, 0, 0};
+      int sl[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sl[j] = j < ns ? slot[cz][j] : slot[cz][0];
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        const T pv = P[k], qv = Q[k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          yr[j] += pv * xr[sl[j]][k];
+          yi[j] += qv * xi[sl[j]][k];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= ns) break;
+        T cs, sn;
+        rot_of_octant(ck_s[sl[j]], m, rot4, cs, sn);
+        ar += cs * yr[j] + sn * yi[j];
+        ai += cs * yi[j] - sn * yr[j];
+      }
+    }
+    Mp[((size_t)box * ntypes + type) * K + i] = T2{ar, ai};
   }
 }
 
@@ -1302,8 +1326,10 @@ static void make_tables(Ctx &c) {
 }
 
 void upload_gl16();
+void upload_an();
 void init_fmm_tables(Ctx &c) {
   upload_gl16();
+  upload_an();
   make_tables(c);
   upload_consts(c.stream);
 }
@@ -1754,14 +1780,14 @@ static void upward_t(Ctx &c, Group &g, int parts) {
   }
   for (int l = D; l >= 3; --l) {
     if (dofree && g.T.lev[l - 1].n) {
-      k_m2m<T><<<dim3((unsigned)g.T.lev[l - 1].n, 1), 128, 0, c.stream>>>(
+      k_m2m<T><<<dim3((unsigned)g.T.lev[l - 1].n, 1), M2M_THREADS, 0, c.stream>>>(
           g.T.lev[l - 1].d_n, g.T.lev[l - 1].start, g.T.lev[l - 1].count, g.T.lev[l].key, 1, (const T2 *)g.Mfree[l],
           (T2 *)g.Mfree[l - 1], (const T *)g.op_m2m_t[l], (const T *)tb.rot4, K);
       LPB_LAUNCH();
       c.launches++;
     }
     if (doreact && g.I.lev[l - 1].n) {
-      k_m2m<T><<<dim3((unsigned)g.I.lev[l - 1].n, g.ntypes), 128, 0, c.stream>>>(
+      k_m2m<T><<<dim3((unsigned)g.I.lev[l - 1].n, g.ntypes), M2M_THREADS, 0, c.stream>>>(
           g.I.lev[l - 1].d_n, g.I.lev[l - 1].start, g.I.lev[l - 1].count, g.I.lev[l].key, g.ntypes,
           (const T2 *)g.Mimg[l], (T2 *)g.Mimg[l - 1], (const T *)g.op_m2m_i[l], (const T *)tb.rot4, K);
       LPB_LAUNCH();

@@ -342,13 +342,31 @@ static NDesc node_desc(int KT, double tol, double Lam, double Lamp) {
   return N;
 }
 
-// forward recurrence in d (Sec. 3.5 eq. recurrence1), one warp per class
+// a_n = sqrt(n (n+1)) and 1/a_n for n <= 2 KMAX_TAB + 1 (host, long double), for the recurrence
+__constant__ double c_an[2 * KMAX_TAB + 2], c_ian[2 * KMAX_TAB + 2];
+static bool g_an_ready = false;
+void upload_an() {
+  if (g_an_ready) return;
+  double a[2 * KMAX_TAB + 2], ia[2 * KMAX_TAB + 2];
+  for (int n = 0; n < 2 * KMAX_TAB + 2; ++n) {
+    const long double v = sqrtl((long double)n * (n + 1));
+    a[n] = (double)v;
+    ia[n] = n ? (double)(1.0L / v) : 0.0;
+  }
+  LPB_CUDA(cudaMemcpyToSymbol(c_an, a, sizeof a));
+  LPB_CUDA(cudaMemcpyToSymbol(c_ian, ia, sizeof ia));
+  g_an_ready = true;
+}
+
+// forward recurrence in d (Sec. 3.5 eq. recurrence1), one warp per class:
+//   S_{K,d+1} = (2d / a_{K+d}) (1/rho) S_{K-1,d} - (a_{K-d} / a_{K+d}) S_{K,d-1}
 __global__ void k_stab_recur(const RDesc *descs, int KT) {
   const RDesc D = descs[blockIdx.y];
   const int cls = blockIdx.x;
   if (D.used && !D.used[cls]) return;
   const int ri = cls / NKK;
   const double rh = sqrt(c_rho2[ri]);
+  const double irh = rh > 0.0 ? 1.0 / rh : 0.0;
   double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   const int lane = threadIdx.x;
   for (int d = 1; d < KT; ++d) {
@@ -357,8 +375,8 @@ __global__ void k_stab_recur(const RDesc *descs, int KT) {
       if (K < d + 1) continue;
       double v = 0.0;
       if (rh > 0.0) {
-        const double apd = sqrt(double(K + d) * (K + d + 1)), amd = sqrt(double(K - d) * (K - d + 1));
-        v = (2.0 * d / apd) / rh * S[stab_index(KT, K - 1, d, ij)] - (amd / apd) * S[stab_index(KT, K, d - 1, ij)];
+        const double ia = c_ian[K + d];
+        v = (2.0 * d * ia * irh) * S[stab_index(KT, K - 1, d, ij)] - (c_an[K - d] * ia) * S[stab_index(KT, K, d - 1, ij)];
       }
       S[stab_index(KT, K, d + 1, ij)] = v;
     }
