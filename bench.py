@@ -30,6 +30,27 @@ N_DEFAULT = 1000000
 P_DEFAULT = 10
 
 
+def rank_seed(rank):
+    """Seed of rank r's independent system (weak scaling: every rank evaluates its own N charges)."""
+    from paper_2002_01334_gb300 import inputs
+    return inputs.BASE_SEED + 2 + 1000 * rank
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (ms); the job's time is that of its slowest rank."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n, steps, ms):
+    """Targets per second of the whole job: world ranks x n targets x steps in ms."""
+    return world * n * steps / (ms / 1000.0)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,7 +188,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = inputs.workload("three_layer", n=args.n, seed=inputs.BASE_SEED + 2 + 1000 * rank)
+    w = inputs.workload("three_layer", n=args.n, seed=rank_seed(rank))
     m = w["medium"]
     q = torch.tensor(w["q"], device=dev)
     x = torch.tensor(w["xyz"], device=dev)
@@ -203,12 +224,8 @@ def run_ours(args, rank, world, local_rank):
                 phase_ms[nm] = phase_ms.get(nm, 0.0) + ms
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = job_throughput(world, n, args.steps, total_ms)
 
     # end to end through the public call with host buffers (pinned), copies inside the timed region
     hq = torch.tensor(w["q"]).pin_memory()
@@ -230,12 +247,8 @@ def run_ours(args, rank, world, local_rank):
         hfld.copy_(fld, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = world * n * e2e_steps / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e2e_val = job_throughput(world, n, e2e_steps, e2e_ms)
 
     # accuracy gate and the FP64 comparator (same tree rule, same inputs), untimed by the driver's clock
     accuracy, fp64_value = None, None

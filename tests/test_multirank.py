@@ -1,0 +1,58 @@
+"""Multi-rank host logic of bench.py on CPU with the gloo backend (world size 2): every rank
+evaluates its own independent system (distinct seeds, no collective on the data path), the job
+time is the slowest rank's, and throughput counts the targets of all ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+from paper_2002_01334_gb300 import inputs
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = inputs.workload("three_layer", n=64, seed=bench.rank_seed(rank))
+        local_ms = 10.0 + 5.0 * rank  # rank 1 is the slower one
+        ms = bench.max_over_ranks(local_ms, dist, "cpu")
+        out[rank] = (ms, float(np.sum(w["q"])), bench.job_throughput(world, 64, 3, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_rank_and_distinct_systems():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        out = man.dict()
+        procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 15.0
+    assert res[0][1] != res[1][1]  # independent systems per rank
+    assert res[0][2] == pytest.approx(2 * 64 * 3 / 0.015)
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(7.5, None, "cpu") == 7.5
+    assert bench.job_throughput(1, 1000, 2, 1000.0) == 2000.0
