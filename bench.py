@@ -271,6 +271,8 @@ def run_ours(args, rank, world, local_rank):
                     "gate": 1e-6}
         ctx64.close()
 
+    device_status = ctx.status()  # 0 unless a bounded device wait ran out during the run
+
     # rooflines of the heaviest kernels, from their CUDA-event intervals (per evaluation)
     K = (args.p + 1) * (args.p + 2) // 2
     R = 2 * K - (args.p + 1)  # real coordinates of an expansion
@@ -326,7 +328,8 @@ def run_ours(args, rank, world, local_rank):
                 "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
                         "d2h_bytes_per_step": n * (8 + 24)},
                 "gpu_launches": launches_per_step * args.steps, "roofline": roof_main, "rooflines": roofs,
-                "phases_ms_per_eval": {k: v / args.steps for k, v in phase_ms.items()}, "cpu_baseline": cpu,
+                "phases_ms_per_eval": {k: v / args.steps for k, v in phase_ms.items()}, "device_status": device_status,
+                "cpu_baseline": cpu,
                 "fp64_fmm_value": fp64_value, "accuracy": accuracy, "counts": counts}
         print(json.dumps(line), flush=True)
     if dist:

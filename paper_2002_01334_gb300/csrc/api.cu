@@ -331,6 +331,14 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     }
   }
   for (auto &g : c.groups) build_group_lists(c, g, parts);
+  {
+    double lmin = 1e300, hmin = 1e300;
+    for (int k = 0; k <= L; ++k) lmin = std::min(lmin, c.md.lam[k]);
+    for (auto &g : c.groups)
+      if (g.I.np) hmin = std::min(hmin, g.h(g.D));
+    c.stab_lmin = hmin < 1e300 ? lmin * hmin : lmin;
+    c.stab_bes = nullptr;
+  }
   for (auto &g : c.groups) {
     build_operators(c, g, parts);
     if ((parts & 2) && g.ureact) {

@@ -114,6 +114,9 @@ struct Ctx {
   double *tpoly = nullptr;   // [K][TPK] Legendre-product coefficients
   double *sfac = nullptr;    // [KMAX_TAB+1][KMAX_TAB+1]: sqrt((K+d)! (K-d)!) for d <= K
   double *phat_dir = nullptr;  // [72][(2p+1)(2p+2)/2]: Phat_q^k(cos theta) of the operator directions
+  // per evaluation: grading of the shared Sommerfeld node set and its Bessel columns
+  double stab_lmin = 0.0;
+  double *stab_bes = nullptr;
   int tpk = 0;
   int *status = nullptr;     // device status word
   int *h_status = nullptr;   // pinned

@@ -198,8 +198,31 @@ struct NDesc {
   double umax, wmax, lmin;
   double ucut[3];  // truncation point for zeta = 1, 2, 3 (zeta = k_t + k_s + 1)
   int npan, nq;
-  double *nodes;  // [nq][NDF]
+  double *nodes;        // [nq][NDF]
+  const double *bes;    // shared J0, J1 columns of this node set [nq][2 NRHO], or null (computed here)
 };
+
+// J0(u rho_r), J1(u rho_r) at the nodes of one node set, shared by every descriptor using it
+__global__ void k_stab_bessel(NDesc N, double *bes) {
+  __shared__ double pu[MAXPANEL], pw[MAXPANEL];
+  __shared__ int npan;
+  if (threadIdx.x == 0) make_panels(N.umax, N.wmax, N.lmin, pu, pw, &npan);
+  __syncthreads();
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N.nq; j += gridDim.x * blockDim.x) {
+    double *o = bes + (size_t)j * 2 * NRHO;
+    if (j >= npan * 16) {
+      for (int k = 0; k < 2 * NRHO; ++k) o[k] = 0.0;
+      continue;
+    }
+    const int pi_ = j >> 4, gi = 15 - (j & 15);  // ascending abscissae
+    const double u = pu[pi_] + 0.5 * pw[pi_] * (c_glx[gi] + 1.0);
+    for (int r = 0; r < NRHO; ++r) {
+      const double x = u * sqrt(c_rho2[r]);
+      o[r] = j0(x);
+      o[NRHO + r] = j1(x);
+    }
+  }
+}
 
 __global__ void k_stab_nodes(const RDesc *descs, const NDesc *nds, Medium md) {
   const RDesc D = descs[blockIdx.y];
@@ -227,10 +250,15 @@ __global__ void k_stab_nodes(const RDesc *descs, const NDesc *nds, Medium md) {
       o[4 + k] = exp(-uz * (k + 0.5));
       o[7 + k] = exp(-uzp * (k + 0.5));
     }
-    for (int r = 0; r < NRHO; ++r) {
-      const double x = u * sqrt(c_rho2[r]);
-      o[10 + r] = j0(x);
-      o[10 + NRHO + r] = j1(x);
+    if (N.bes) {
+      const double *b = N.bes + (size_t)j * 2 * NRHO;
+      for (int r = 0; r < 2 * NRHO; ++r) o[10 + r] = b[r];
+    } else {
+      for (int r = 0; r < NRHO; ++r) {
+        const double x = u * sqrt(c_rho2[r]);
+        o[10 + r] = j0(x);
+        o[10 + NRHO + r] = j1(x);
+      }
     }
   }
 }
@@ -339,6 +367,7 @@ static NDesc node_desc(int KT, double tol, double Lam, double Lamp) {
   N.npan = count_panels(N.umax, N.wmax, N.lmin);
   N.nq = N.npan * 16;
   N.nodes = nullptr;
+  N.bes = nullptr;
   return N;
 }
 
@@ -631,8 +660,19 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
     const double tol = fmax(c.tol, 1e-16);
     std::vector<NDesc> nv;
     int maxq = 0;
+    // one node set for the whole evaluation (graded to the smallest Lambda of all reaction
+    // groups), so the Bessel columns are evaluated once and shared
+    if (!c.stab_bes) {
+      const NDesc N0 = node_desc(KT, tol, c.stab_lmin, c.stab_lmin);
+      c.stab_bes = c.arena.get<double>((size_t)N0.nq * 2 * NRHO);
+      k_stab_bessel<<<(unsigned)((N0.nq + 255) / 256), 256, 0, c.stream>>>(N0, c.stab_bes);
+      LPB_LAUNCH();
+      c.launches++;
+    }
     for (auto &d : rd) {
-      NDesc N = node_desc(KT, tol, d.Lam, d.Lamp);
+      (void)d;
+      NDesc N = node_desc(KT, tol, c.stab_lmin, c.stab_lmin);
+      N.bes = c.stab_bes;
       N.nodes = c.arena.get<double>((size_t)N.nq * NDF);
       maxq = std::max(maxq, N.nq);
       nv.push_back(N);

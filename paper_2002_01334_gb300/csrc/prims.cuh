@@ -80,6 +80,33 @@ __global__ void k_scan_add(uint32_t *out, const uint32_t *sums, int64_t n) {
     if (base + k < n) out[base + k] += add;
 }
 
+// one block for short arrays: chunks of blockDim * SCAN_ITEMS with a running carry; the exclusive
+// scan of in[0..n) into out (in place allowed), the total into *total (may be null)
+__global__ void k_scan_one(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total) {
+  __shared__ uint32_t sm[32];
+  uint32_t carry = 0;
+  const int64_t chunk = (int64_t)blockDim.x * SCAN_ITEMS;
+  for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+    const int64_t base = c0 + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      v[k] = (base + k < n) ? in[base + k] : 0u;
+      s += v[k];
+    }
+    uint32_t tot;
+    uint32_t run = carry + block_exclusive_scan(s, sm, &tot);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      if (base + k < n) out[base + k] = run;
+      run += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
 // ---------------------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits.  Tile = 256 threads x 8 rounds; within a tile the
 // items are visited round-major (item = round*256 + thread), so ranks follow the input order.

@@ -11,6 +11,12 @@ namespace lpb {
 // scan / sort wrappers
 // ---------------------------------------------------------------------------------------
 void scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total) {
+  if (n <= 8192) {  // one launch, one chunk
+    k_scan_one<<<1, 1024, 0, c.stream>>>(in, out, n, d_total);
+    LPB_LAUNCH();
+    c.launches++;
+    return;
+  }
   const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   uint32_t *sums = c.arena.get<uint32_t>(tiles + 1);
   if (n > 0) {
@@ -61,17 +67,26 @@ __device__ __forceinline__ unsigned long long wmax(unsigned long long v) {
   return v;
 }
 
-__global__ void k_validate(int64_t n, const double *q, const double *xyz, const int32_t *layer, Medium md,
-                           double thr, Stats *st) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  bool ok = false;
-  int lay = -1;
-  double x = 0, y = 0, z = 0;
-  if (i < n) {
-    x = xyz[3 * i]; y = xyz[3 * i + 1]; z = xyz[3 * i + 2];
+// Grid-stride validation: every thread keeps its own extremes (order-preserving integers of
+// the FP64 coordinates) and per-layer counts; they are reduced per warp by shuffles, per block
+// in shared memory, and merged into the global statistics with one atomic per block and field.
+constexpr int VAL_THREADS = 256;
+__global__ void __launch_bounds__(VAL_THREADS) k_validate(int64_t n, const double *q, const double *xyz,
+                                                          const int32_t *layer, Medium md, double thr, Stats *st) {
+  const unsigned long long HI = ~0ull, LO = 0ull;
+  unsigned long long xlo = HI, xhi = LO, ylo = HI, yhi = LO, zlo[MAXLAYER], zhi[MAXLAYER];
+  unsigned cnt[MAXLAYER];
+#pragma unroll
+  for (int k = 0; k < MAXLAYER; ++k) {
+    zlo[k] = HI;
+    zhi[k] = LO;
+    cnt[k] = 0;
+  }
+  int code_seen = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     const double qq = q[i];
-    lay = layer[i];
+    const int lay = layer[i];
     int code = 0;
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qq)) {
       code = LPBFMM_ERR_NONFINITE;
@@ -82,21 +97,54 @@ __global__ void k_validate(int64_t n, const double *q, const double *xyz, const 
         if (fabs(z - md.d[k]) < thr) code = LPBFMM_ERR_ON_INTERFACE;
       if (!code && l != lay) code = LPBFMM_ERR_LAYER_MISMATCH;
     }
-    if (code) atomicCAS(&st->status, 0, code);
-    ok = (code == 0);
+    if (code) {
+      if (!code_seen) atomicCAS(&st->status, 0, code);
+      code_seen = 1;
+      continue;
+    }
+    const unsigned long long ox = ord_of(x), oy = ord_of(y), oz = ord_of(z);
+    xlo = min(xlo, ox); xhi = max(xhi, ox);
+    ylo = min(ylo, oy); yhi = max(yhi, oy);
+#pragma unroll
+    for (int k = 0; k < MAXLAYER; ++k)
+      if (k == lay) {
+        zlo[k] = min(zlo[k], oz);
+        zhi[k] = max(zhi[k], oz);
+        ++cnt[k];
+      }
   }
-  const unsigned long long HI = ~0ull, LO = 0ull;
-  unsigned long long v;
-  v = wmin(ok ? ord_of(x) : HI); if (lane == 0 && v != HI) atomicMin(&st->xlo, v);
-  v = wmax(ok ? ord_of(x) : LO); if (lane == 0 && v != LO) atomicMax(&st->xhi, v);
-  v = wmin(ok ? ord_of(y) : HI); if (lane == 0 && v != HI) atomicMin(&st->ylo, v);
-  v = wmax(ok ? ord_of(y) : LO); if (lane == 0 && v != LO) atomicMax(&st->yhi, v);
-  for (int k = 0; k <= md.L; ++k) {
-    const bool in = ok && lay == k;
-    const unsigned cntk = __popc(__ballot_sync(0xffffffffu, in));
-    if (lane == 0 && cntk) atomicAdd(&st->cnt[k], (unsigned long long)cntk);
-    v = wmin(in ? ord_of(z) : HI); if (lane == 0 && v != HI) atomicMin(&st->zlo[k], v);
-    v = wmax(in ? ord_of(z) : LO); if (lane == 0 && v != LO) atomicMax(&st->zhi[k], v);
+  __shared__ unsigned long long red[VAL_THREADS / 32][4 + 3 * MAXLAYER];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long v[4 + 3 * MAXLAYER];
+  v[0] = wmin(xlo); v[1] = wmax(xhi); v[2] = wmin(ylo); v[3] = wmax(yhi);
+#pragma unroll
+  for (int k = 0; k < MAXLAYER; ++k) {
+    v[4 + k] = wmin(zlo[k]);
+    v[4 + MAXLAYER + k] = wmax(zhi[k]);
+    unsigned c = cnt[k];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    v[4 + 2 * MAXLAYER + k] = c;
+  }
+  if (lane == 0)
+    for (int f = 0; f < 4 + 3 * MAXLAYER; ++f) red[warp][f] = v[f];
+  __syncthreads();
+  if (threadIdx.x < 4 + 3 * MAXLAYER) {
+    const int f = threadIdx.x;
+    const bool is_min = f == 0 || f == 2 || (f >= 4 && f < 4 + MAXLAYER);
+    const bool is_cnt = f >= 4 + 2 * MAXLAYER;
+    unsigned long long a = is_min ? HI : LO;
+    for (int w2 = 0; w2 < nw; ++w2) {
+      const unsigned long long b = red[w2][f];
+      a = is_cnt ? a + b : (is_min ? min(a, b) : max(a, b));
+    }
+    unsigned long long *dst = f == 0 ? &st->xlo : f == 1 ? &st->xhi : f == 2 ? &st->ylo : f == 3 ? &st->yhi
+                            : f < 4 + MAXLAYER ? &st->zlo[f - 4]
+                            : f < 4 + 2 * MAXLAYER ? &st->zhi[f - 4 - MAXLAYER]
+                            : &st->cnt[f - 4 - 2 * MAXLAYER];
+    if (is_cnt) { if (a) atomicAdd(dst, a); }
+    else if (is_min) { if (a != HI) atomicMin(dst, a); }
+    else if (a != LO) atomicMax(dst, a);
   }
 }
 
@@ -104,8 +152,8 @@ void launch_validate(Ctx &c, int64_t n, const double *q, const double *xyz, cons
   double scale = 1.0;
   for (int k = 0; k < c.md.L; ++k) scale = fmax(scale, fabs(c.md.d[k]));
   const double thr = 1e-12 * scale;
-  const unsigned blocks = (unsigned)((n + 255) / 256);
-  k_validate<<<blocks, 256, 0, c.stream>>>(n, q, xyz, layer, c.md, thr, st);
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + VAL_THREADS - 1) / VAL_THREADS, 152 * 4));
+  k_validate<<<blocks, VAL_THREADS, 0, c.stream>>>(n, q, xyz, layer, c.md, thr, st);
   LPB_LAUNCH();
   c.launches++;
 }

@@ -105,6 +105,11 @@ class Context:
                                C.byref(o), C.byref(h)), "lpbfmm_create")
         self.h = h
 
+    def status(self):
+        """Read and clear the device status word (0, or an error code such as a timed-out
+        device wait); synchronizes the context's stream."""
+        return int(lib().lpbfmm_status(self.h))
+
     def close(self):
         if getattr(self, "h", None) and self.h.value:
             lib().lpbfmm_destroy(self.h)

@@ -200,7 +200,8 @@ def test_mixed_precision_gate(w3000):
     w, _ = w3000
     for p in (8, 10):
         _, a, fa = run(w, p, prec=F.FP64)
-        _, b, fb = run(w, p, prec=F.MIXED)
+        ctx, b, fb = run(w, p, prec=F.MIXED)
+        assert ctx.status() == 0  # no bounded device wait ran out
         assert rel(b, a) < 1e-6 and rel(fb, fa) < 1e-6, (p, rel(b, a), rel(fb, fa))
 
 
