@@ -121,7 +121,7 @@ struct RDesc {
   double h, Lam, Lamp;
   const uint8_t *used;   // [NREACT_CLS]
   double *stab;          // [NREACT_CLS][ntypes][TS]
-  double *coef;          // [K*K][NS]
+  float2 *coef;          // [K*K][NS] double-float (hi, lo) coefficients C_s
   int64_t dst;           // element offset of class 0, type tau in the op array
 };
 
@@ -439,8 +439,29 @@ __global__ void k_react_coef(const RDesc *descs, const double *tpoly, int tpk, i
       if (kp < 0 || kp > k2) continue;
       acc += tpoly[o * tpk + k] * tpoly[i * tpk + kp] * pl[n - m - 2 * k + 1] * plp[nu - mu - 2 * kp + 1];
     }
-    D.coef[(size_t)e * NS + s] = acc;
+    const float h = (float)acc;
+    D.coef[(size_t)e * NS + s] = make_float2(h, (float)(acc - (double)h));
   }
+}
+
+// double-float arithmetic (value = hi + lo, two FP32 numbers; about 44 significant bits) on
+// the FP32 pipes: exact products by FMA, sums by the two-sum of Knuth, then renormalised.
+// The _rn intrinsics keep the compiler from contracting the error-free transformations.
+__device__ __forceinline__ float2 df_split(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ void df_fma(float2 a, float2 b, float2 &acc) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);  // rounding error of p, exactly
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(acc.x, p);
+  const float v = __fsub_rn(s, acc.x);
+  float t = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, v)), __fsub_rn(p, v));
+  t = __fadd_rn(t, __fadd_rn(acc.y, e));
+  const float hi = __fadd_rn(s, t);
+  acc = make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
 }
 
 template <typename T>
@@ -449,13 +470,13 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
   const int cls = blockIdx.x;
   if (D.used && !D.used[cls]) return;
   extern __shared__ double asm_sm[];
-  double *Sf = asm_sm;  // [(KT+1)^2 * 4]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}
+  float2 *Sf = (float2 *)asm_sm;  // [(KT+1)^2 * 4]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}, double-float
   __shared__ double smm[PMAX + 1], rdf[PMAX + 1];
   __shared__ double fa[KHALF_MAX], fb[KHALF_MAX];  // prefactor A(o, i) = fa[o] fb[i]
   const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   for (int e = threadIdx.x; e < (KT + 1) * (KT + 1) * 4; e += blockDim.x) {
     const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
-    Sf[e] = (d <= Kk) ? sfac[Kk * (KMAX_TAB + 1) + d] * S[e] : 0.0;
+    Sf[e] = df_split((d <= Kk) ? sfac[Kk * (KMAX_TAB + 1) + d] * S[e] : 0.0);
   }
   if (threadIdx.x == 0) {
     double s = 1.0;
@@ -485,17 +506,18 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     const int ij = 2 * ((n - m) & 1) + ((nu - mu) & 1);
     const double A = fa[o] * fb[i];
     const int smax = (n - m + 1) / 2 + (nu - mu + 1) / 2;
-    const double *cf = D.coef + (size_t)e * NS;
+    const float2 *cf = D.coef + (size_t)e * NS;
     const int dp = mu - m, dm = mu + m;  // |d| for +mu and -mu
     const int adp = dp < 0 ? -dp : dp;
-    double accp = 0.0, accm = 0.0;
+    float2 ap = make_float2(0.f, 0.f), am = make_float2(0.f, 0.f);
     for (int s = 0; s <= smax; ++s) {
       const int Kk = 1 + m + mu + 2 * s;
       if (Kk > KT) break;
-      const double c = cf[s];
-      accp += c * Sf[((Kk * (KT + 1)) + adp) * 4 + ij];
-      accm += c * Sf[((Kk * (KT + 1)) + dm) * 4 + ij];
+      const float2 c = cf[s];
+      df_fma(c, Sf[((Kk * (KT + 1)) + adp) * 4 + ij], ap);
+      df_fma(c, Sf[((Kk * (KT + 1)) + dm) * 4 + ij], am);
     }
+    const double accp = (double)ap.x + (double)ap.y, accm = (double)am.x + (double)am.y;
     // signs: (-1)^|d| for d = mu - m < 0 and for d = -mu - m < 0; (-1)^mu of the -mu term
     const unsigned long long SGN = 0x8000000000000000ull;
     const bool fp = dp < 0 && (adp & 1), fm = ((dm > 0 && (dm & 1)) != ((mu & 1) != 0));
@@ -639,7 +661,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
     const double h = g.h(l);
     g.stab[l] = c.arena.get<double>((size_t)NREACT_CLS * g.ntypes * TS);
     g.op_react[l] = c.arena.get<T>((size_t)NREACT_CLS * g.ntypes * 2 * KK);
-    double *coef = c.arena.get<double>((size_t)g.ntypes * KK * NS);
+    float2 *coef = c.arena.get<float2>((size_t)g.ntypes * KK * NS);
     for (int t = 0; t < g.ntypes; ++t) {
       int lp, bb;
       type_decode(t, lp, bb);
