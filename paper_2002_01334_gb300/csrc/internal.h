@@ -141,7 +141,7 @@ struct Stats {
   unsigned long long zlo[MAXLAYER], zhi[MAXLAYER];
 };
 void scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total);
-void radix_sort(Ctx &c, uint64_t *&keys, uint32_t *&vals, int64_t n, int bits);
+void radix_sort(Ctx &c, uint64_t *&keys, uint32_t *&vals, int64_t n, int bits, int lo);
 void launch_validate(Ctx &c, int64_t n, const double *q, const double *xyz, const int32_t *layer, Stats *st);
 void build_group_targets(Ctx &c, Group &g, int64_t n, const double *q, const double *xyz, const int32_t *layer,
                          uint32_t *const *rank, const int64_t *cnt);

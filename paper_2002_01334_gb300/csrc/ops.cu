@@ -451,6 +451,14 @@ __device__ __forceinline__ float2 df_split(double v) {
   const float h = (float)v;
   return make_float2(h, (float)(v - (double)h));
 }
+// hi + lo of (a.hi + a.lo) + (b.hi + b.lo) rounded to one FP32 number, without losing the low parts
+// to cancellation between a and b
+__device__ __forceinline__ float df_sum_f(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float v = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
+  return __fadd_rn(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
 __device__ __forceinline__ void df_fma(float2 a, float2 b, float2 &acc) {
   const float p = __fmul_rn(a.x, b.x);
   float e = fmaf(a.x, b.x, -p);  // rounding error of p, exactly
@@ -473,6 +481,7 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
   float2 *Sf = (float2 *)asm_sm;  // [(KT+1)^2 * 4]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}, double-float
   __shared__ double smm[PMAX + 1], rdf[PMAX + 1];
   __shared__ double fa[KHALF_MAX], fb[KHALF_MAX];  // prefactor A(o, i) = fa[o] fb[i]
+  __shared__ float faf[KHALF_MAX], fbf[KHALF_MAX];  // the same in FP32 (FP32 operators, p <= 12)
   const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   for (int e = threadIdx.x; e < (KT + 1) * (KT + 1) * 4; e += blockDim.x) {
     const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
@@ -493,8 +502,12 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     const bool odd = (n - m) & 1;
     fa[e] = smm[m] * rdf[n] * (odd ? (double)D.st : 1.0);
     fb[e] = smm[m] * rdf[n] * (odd ? -(double)D.st : 1.0) * (0.25 / PI) / D.h;
+    faf[e] = (float)fa[e];
+    fbf[e] = (float)fb[e];
   }
   __syncthreads();
+  // FP32 epilogue for FP32 operators while the prefactors stay well inside the FP32 range
+  const bool f32_out = sizeof(T) == 4 && p <= 12;
   const int NS = p + 2;
   const size_t KK = (size_t)K * K;
   T *P = out + D.dst + (size_t)cls * D.ntypes * 2 * KK;
@@ -504,7 +517,6 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     hdecode(o, n, m);
     hdecode(i, nu, mu);
     const int ij = 2 * ((n - m) & 1) + ((nu - mu) & 1);
-    const double A = fa[o] * fb[i];
     const int smax = (n - m + 1) / 2 + (nu - mu + 1) / 2;
     const float2 *cf = D.coef + (size_t)e * NS;
     const int dp = mu - m, dm = mu + m;  // |d| for +mu and -mu
@@ -517,20 +529,26 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
       df_fma(c, Sf[((Kk * (KT + 1)) + adp) * 4 + ij], ap);
       df_fma(c, Sf[((Kk * (KT + 1)) + dm) * 4 + ij], am);
     }
-    const double accp = (double)ap.x + (double)ap.y, accm = (double)am.x + (double)am.y;
+
     // signs: (-1)^|d| for d = mu - m < 0 and for d = -mu - m < 0; (-1)^mu of the -mu term
-    const unsigned long long SGN = 0x8000000000000000ull;
     const bool fp = dp < 0 && (adp & 1), fm = ((dm > 0 && (dm & 1)) != ((mu & 1) != 0));
-    const double X = __longlong_as_double(__double_as_longlong(accp) ^ (fp ? SGN : 0ull));
-    const double Y = __longlong_as_double(__double_as_longlong(accm) ^ (fm ? SGN : 0ull));
-    double Pv, Qv;
-    if (mu == 0) { Pv = A * X; Qv = 0.0; }
-    else {
-      Pv = A * (X + Y);
-      Qv = A * (X - Y);
+    const float2 Xd = fp ? make_float2(-ap.x, -ap.y) : ap, Yd = fm ? make_float2(-am.x, -am.y) : am;
+    T *dP = P + (size_t)D.tau * 2 * KK + (size_t)o * K + i, *dQ = dP + KK;
+    if (f32_out) {
+      const float Af = faf[o] * fbf[i];
+      if (mu == 0) {
+        *dP = (T)(Af * df_sum_f(Xd, make_float2(0.f, 0.f)));
+        *dQ = (T)0;
+      } else {
+        *dP = (T)(Af * df_sum_f(Xd, Yd));
+        *dQ = (T)(Af * df_sum_f(Xd, make_float2(-Yd.x, -Yd.y)));
+      }
+    } else {
+      const double A = fa[o] * fb[i];
+      const double X = (double)Xd.x + (double)Xd.y, Y = (double)Yd.x + (double)Yd.y;
+      *dP = (T)(mu == 0 ? A * X : A * (X + Y));
+      *dQ = (T)(mu == 0 ? 0.0 : A * (X - Y));
     }
-    P[(size_t)D.tau * 2 * KK + (size_t)o * K + i] = (T)Pv;
-    P[(size_t)D.tau * 2 * KK + KK + (size_t)o * K + i] = (T)Qv;
   }
 }
 static size_t assemble_smem(int KT) { return sizeof(double) * (size_t)(KT + 1) * (KT + 1) * 4; }

@@ -32,14 +32,16 @@ void scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_
   c.launches += 2 + (tiles > 1) + (n > 0 ? 0 : -1);
 }
 
-void radix_sort(Ctx &c, uint64_t *&keys, uint32_t *&vals, int64_t n, int bits) {
+// stable sort by key bits [lo, bits): lower bits must not matter for the order (zero, or a
+// field equal within a run that the caller does not need sorted)
+void radix_sort(Ctx &c, uint64_t *&keys, uint32_t *&vals, int64_t n, int bits, int lo) {
   if (n <= 1) return;
   const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
   uint64_t *k2 = c.arena.get<uint64_t>(n);
   uint32_t *v2 = c.arena.get<uint32_t>(n);
   uint32_t *hist = c.arena.get<uint32_t>((size_t)256 * nblocks);
   uint32_t *offs = c.arena.get<uint32_t>((size_t)256 * nblocks);
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = lo; shift < bits; shift += 8) {
     k_radix_hist<<<nblocks, RS_THREADS, 0, c.stream>>>(keys, n, shift, hist, nblocks);
     LPB_LAUNCH();
     scan_u32(c, hist, offs, (int64_t)256 * nblocks, nullptr);
@@ -296,7 +298,7 @@ void build_group_targets(Ctx &c, Group &g, int64_t n, const double *q, const dou
   k_make_targets<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, xyz, layer, rk, gg, g.T.key, g.T.src);
   LPB_LAUNCH();
   c.launches++;
-  radix_sort(c, g.T.key, g.T.src, g.T.np, DMAX * 3 + 4);
+  radix_sort(c, g.T.key, g.T.src, g.T.np, DMAX * 3 + 4, 4);  // target keys: low 4 bits are zero
   gather(c, g, g.T, 0, q, xyz, layer);
 }
 
@@ -320,7 +322,7 @@ void build_group_images(Ctx &c, Group &g, int64_t n, const double *q, const doub
                                                                    g.I.src);
   LPB_LAUNCH();
   c.launches++;
-  radix_sort(c, g.I.key, g.I.src, g.I.np, g.D * 3 + 4);
+  radix_sort(c, g.I.key, g.I.src, g.I.np, g.D * 3 + 4, 0);
   gather(c, g, g.I, 1, q, xyz, layer);
 }
 
