@@ -1441,7 +1441,7 @@ struct TJob {
 };
 constexpr int TC_MAXSTEP = 49 * 2 * MAXLAYER;
 
-constexpr int TC_ROWS = 128, TC_THREADS = 256;
+constexpr int TC_ROWS = 128, TC_WORKERS = 256, TC_THREADS = TC_WORKERS + 32;
 constexpr int TC_WAIT = 1 << 22;  // mbarrier polls before the kernel reports a timeout
 
 __host__ __device__ constexpr int tc_nst(int NC) { return NC <= 5 ? 3 : 2; }
@@ -1461,7 +1461,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   __shared__ int remap_s[N], mcol[N];  // coordinate -> half index code; m of that coefficient
   __shared__ int nsteps;
   __shared__ unsigned hasmask[2];
-  __shared__ uint64_t mbar[NST], accbar[2];
+  // full[b]: the workers have staged buffer b (TC_WORKERS arrivals); empty[b]: its MMAs are done;
+  // accbar[a]: a step's MMAs into accumulator a are done; foldbar[a]: the workers have read it
+  __shared__ uint64_t full[NST], empty[NST], accbar[2], foldbar[2];
   __shared__ uint32_t tbase;
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
@@ -1474,9 +1476,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   const int64_t ti = local / M2L_NSLICE;
   const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
   if (J.pstart ? (ti >> 3) * TC_ROWS >= J.npar : ti * TC_ROWS >= ntl) return;
-  // thread = (row, half): row = target slot and TMEM lane, half = which 4 of a chunk's 8 units and
-  // which half of the accumulator columns it handles
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, row = tid & (TC_ROWS - 1), hf = tid >> 7;
+  // worker thread (tid < TC_WORKERS) = (row, half): row = target slot and TMEM lane, half = which
+  // 4 of a chunk's 8 units and which half of the accumulator columns it handles; the last warp
+  // issues the MMAs (lane 0)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, row = tid & (TC_ROWS - 1), hf = (tid >> 7) & 1;
+  const bool worker = tid < TC_WORKERS;
   const int ntypes = J.ntypes;
   for (int c = tid; c < N; c += TC_THREADS) {
     const int code = tc_remap(c, K, p);
@@ -1525,17 +1529,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   if (ns == 0) return;
   if (warp == 0) tc::tmem_alloc(&tbase, TCOLS);
   if (tid == 0) {
-    for (int b = 0; b < NST; ++b) tc::mbar_init(&mbar[b], 1);
-    tc::mbar_init(&accbar[0], 1);
-    tc::mbar_init(&accbar[1], 1);
+    for (int b = 0; b < NST; ++b) {
+      tc::mbar_init(&full[b], TC_WORKERS);
+      tc::mbar_init(&empty[b], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&accbar[a], 1);
+      tc::mbar_init(&foldbar[a], TC_WORKERS);
+    }
     tc::mbar_fence_init();
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tmem = tbase, lanebase = (uint32_t)(warp * 32) << 16;
+  // a warp reads the TMEM lanes of its quarter, 32 (warp % 4) .. + 31
+  const uint32_t tmem = tbase, lanebase = (uint32_t)((warp & 3) * 32) << 16;
   const int S = ns * NC;  // stages: (step, K-chunk)
-  const int myt = tid_[row];
+  const int myt = worker ? tid_[row] : -1;
   const int NI2 = 2 * (K - (p + 1));  // columns holding (Re, Im) pairs
   constexpr uint32_t IDESC = tc::idesc_tf32(TC_ROWS, N);
   constexpr int NH = N / 2;  // accumulator columns per thread
@@ -1572,48 +1582,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     return ok;
   };
   bool fail = false;
-  int committed = -1;  // last stage whose MMAs were committed
-  int cur_o = -1, my_src = -1;
-  // stage s is copied at iteration s and consumed (rotated, split, multiplied) at iteration s + 1, so
-  // the MMAs of a stage have until iteration s + NST - 1 before its buffer is refilled
-  for (int s = 0; s < S + 1; ++s) {
-    if (s < S) {
-      const int b = s % NST;
-      if (s >= NST) {
-        const bool ok = tc::mbar_wait(&mbar[b], (uint32_t)((s / NST - 1) & 1), TC_WAIT);
-        if (__syncthreads_or(!ok)) {
+  if (worker) {
+    int cur_o = -1, my_src = -1;
+    // stage s is copied at iteration s and rotated / split at iteration s + 1; the MMA thread takes
+    // it from there, so a buffer is refilled NST stages later, once its MMAs are done
+    for (int s = 0; s < S + 1; ++s) {
+      if (s < S) {
+        const int b = s % NST;
+        if (s >= NST && !tc::mbar_wait(&empty[b], (uint32_t)((s / NST - 1) & 1), TC_WAIT)) {
           fail = true;
           break;
         }
-      }
-      const int o = steps[s / NC] >> 4, tau = steps[s / NC] & 15, kc = s % NC;
-      if (o != cur_o) {
-        cur_o = o;
-        my_src = myt >= 0 ? J.vlist[(size_t)myt * NOFF + o] : -1;
-      }
-      unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
-      unsigned char *Ah = st, *Al = st + SA, *Bh = st + 2 * SA, *Bl = st + 2 * SA + SB;
-      // B and this thread's source row chunk, both asynchronous
-      {
-        const size_t ct = (size_t)J.cls_of[o] * ntypes + tau;
-        const float *wh = J.whi + ct * N * N + kc * 32, *wl = J.wlo + ct * N * N + kc * 32;
-        for (int e = tid; e < N * 8; e += TC_THREADS) {
-          const int r = e >> 3, u = e & 7;
-          cp_async16(Bh + tc::swz16(r, u), wh + (size_t)r * N + 4 * u, true);
-          cp_async16(Bl + tc::swz16(r, u), wl + (size_t)r * N + 4 * u, true);
+        const int o = steps[s / NC] >> 4, tau = steps[s / NC] & 15, kc = s % NC;
+        if (o != cur_o) {
+          cur_o = o;
+          my_src = myt >= 0 ? J.vlist[(size_t)myt * NOFF + o] : -1;
+        }
+        unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
+        unsigned char *Ah = st, *Bh = st + 2 * SA, *Bl = st + 2 * SA + SB;
+        {
+          const size_t ct = (size_t)J.cls_of[o] * ntypes + tau;
+          const float *wh = J.whi + ct * N * N + kc * 32, *wl = J.wlo + ct * N * N + kc * 32;
+          for (int e = tid; e < N * 8; e += TC_WORKERS) {
+            const int r = e >> 3, u = e & 7;
+            cp_async16(Bh + tc::swz16(r, u), wh + (size_t)r * N + 4 * u, true);
+            cp_async16(Bl + tc::swz16(r, u), wl + (size_t)r * N + 4 * u, true);
+          }
+        }
+        {
+          // this thread's source row chunk, unrotated, into the A-hi slots (rotated next iteration)
+          const bool v = my_src >= 0;
+          const float *g = J.raw + ((size_t)(v ? my_src : 0) * ntypes + tau) * N + kc * 32;
+#pragma unroll
+          for (int u = hf * 4; u < hf * 4 + 4; ++u) cp_async16(Ah + tc::swz16(row, u), g + 4 * u, v);
         }
       }
-      {
-        // this thread's source row chunk, unrotated, into the A-hi slots (rotated at consumption)
-        const bool v = my_src >= 0;
-        const float *g = J.raw + ((size_t)(v ? my_src : 0) * ntypes + tau) * N + kc * 32;
-#pragma unroll
-        for (int u = hf * 4; u < hf * 4 + 4; ++u) cp_async16(Ah + tc::swz16(row, u), g + 4 * u, v);
-      }
-    }
-    cp_commit();
-    const int sc = s - 1;
-    if (sc >= 0) {
+      cp_commit();
+      const int sc = s - 1;
+      if (sc < 0) continue;
       asm volatile("cp.async.wait_group 1;\n" ::);
       const int si = sc / NC, kc = sc % NC;
       {
@@ -1653,60 +1659,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
           *(float4 *)(Al + tc::swz16(row, u)) = l4v;
         }
       }
+      // this thread's copies (B part, its A row) and its stores are in place: hand over to the tensor core
       tc::fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after();
-        const int b = sc % NST;
-        unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
-        const uint32_t ah = tc::smem_u32(st), al = ah + (uint32_t)SA, bh = ah + 2 * (uint32_t)SA,
-                       bl = bh + (uint32_t)SB;
-        const uint32_t dacc = tmem + (uint32_t)((si & 1) * N);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t off = kk * 32;
-          tc::mma_tf32(dacc, tc::sdesc(ah + off), tc::sdesc(bh + off), IDESC, (kc | kk) ? 1u : 0u);
-          tc::mma_tf32(dacc, tc::sdesc(ah + off), tc::sdesc(bl + off), IDESC, 1u);
-          tc::mma_tf32(dacc, tc::sdesc(al + off), tc::sdesc(bh + off), IDESC, 1u);
-        }
-        tc::commit(&mbar[b]);
-        if (kc == NC - 1) tc::commit(&accbar[si & 1]);
-      }
-      committed = sc;
-      // step si is queued in full: fold step si - 1, whose accumulator step si + 1 reuses
+      tc::mbar_arrive(&full[sc % NST]);
+      // step si is handed over in full: fold step si - 1 (its accumulator is reused by step si + 1)
       if (kc == NC - 1 && si >= 1) {
-        if (__syncthreads_or(!fold(si - 1))) {
+        if (!fold(si - 1)) {
           fail = true;
           break;
         }
+        tc::mbar_arrive(&foldbar[(si - 1) & 1]);
       }
     }
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::);
-  if (!fail) {
-    if (__syncthreads_or(!fold(ns - 1))) fail = true;
-  } else if (committed >= 0) {
-    // drain: every MMA has completed once the last committed stage's barrier phase completes
-    tc::mbar_wait(&mbar[committed % NST], (uint32_t)((committed / NST) & 1), TC_WAIT);
-  }
-  if (fail) {
-    if (tid == 0) atomicExch(status, LPBFMM_ERR_TIMEOUT);
-  } else {
-    const int t = tid_[row];
-    if (t >= 0) {
-      float2 *Lrow = J.L + ((size_t)t * M2L_NSLOT + J.slot0 + slice) * K;
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    if (!fail && !fold(ns - 1)) fail = true;
+    if (!fail) {
+      const int t = tid_[row];
+      if (t >= 0) {
+        float2 *Lrow = J.L + ((size_t)t * M2L_NSLOT + J.slot0 + slice) * K;
 #pragma unroll
-      for (int j = 0; j < NH; ++j) {
-        const int code = remap_s[hf * NH + j];
-        if (code >= 0) {
-          Lrow[code].x = racc[j];
-          if (mcol[hf * NH + j] == 0) Lrow[code].y = 0.f;
-        } else if (code <= -2) {
-          Lrow[-code - 2].y = racc[j];
+        for (int j = 0; j < NH; ++j) {
+          const int code = remap_s[hf * NH + j];
+          if (code >= 0) {
+            Lrow[code].x = racc[j];
+            if (mcol[hf * NH + j] == 0) Lrow[code].y = 0.f;
+          } else if (code <= -2) {
+            Lrow[-code - 2].y = racc[j];
+          }
         }
       }
     }
+  } else if (tid == TC_WORKERS) {
+    // the MMA thread: stage after stage, once the workers have staged it; a step's first chunk
+    // waits until the workers have read the accumulator two steps back
+    int last = -1;
+    for (int sc = 0; sc < S; ++sc) {
+      const int b = sc % NST, si = sc / NC, kc = sc % NC;
+      if (!tc::mbar_wait(&full[b], (uint32_t)((sc / NST) & 1), TC_WAIT)) {
+        fail = true;
+        break;
+      }
+      if (kc == 0 && si >= 2 && !tc::mbar_wait(&foldbar[si & 1], (uint32_t)(((si - 2) >> 1) & 1), TC_WAIT)) {
+        fail = true;
+        break;
+      }
+      tc::fence_after();
+      unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
+      const uint32_t ah = tc::smem_u32(st), al = ah + (uint32_t)SA, bh = ah + 2 * (uint32_t)SA,
+                     bl = bh + (uint32_t)SB;
+      const uint32_t dacc = tmem + (uint32_t)((si & 1) * N);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t off = kk * 32;
+        tc::mma_tf32(dacc, tc::sdesc(ah + off), tc::sdesc(bh + off), IDESC, (kc | kk) ? 1u : 0u);
+        tc::mma_tf32(dacc, tc::sdesc(ah + off), tc::sdesc(bl + off), IDESC, 1u);
+        tc::mma_tf32(dacc, tc::sdesc(al + off), tc::sdesc(bh + off), IDESC, 1u);
+      }
+      tc::commit(&empty[b]);
+      if (kc == NC - 1) tc::commit(&accbar[si & 1]);
+      last = sc;
+    }
+    // every MMA has completed once the last committed stage's barrier phase completes
+    if (last >= 0) tc::mbar_wait(&empty[last % NST], (uint32_t)((last / NST) & 1), TC_WAIT);
   }
+  if (fail) atomicExch(status, LPBFMM_ERR_TIMEOUT);
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_free(tmem, TCOLS);

@@ -52,6 +52,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
 }
 __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;"); }
+// one arrival of this thread (release semantics for its prior shared-memory writes)
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(mbar)) : "memory");
+}
 
 // wait for the completion of the mbarrier phase with the given parity; false after max_iter polls
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int max_iter) {
