@@ -19,7 +19,10 @@
  * memory on the context's device; the caller owns all input and output arrays and the
  * library never frees them.  Work is issued on the context's stream; lpbfmm_eval returns
  * after the results are complete on that stream (it synchronizes the stream internally
- * several times to size its work).
+ * several times to size its work).  A context lives on the device current at lpbfmm_create
+ * (ordinal below 64); call its entry points with that device current.  Contexts on several
+ * devices may coexist in one process; one context must not be used by two host threads at
+ * once.
  */
 #ifndef LPBFMM_H
 #define LPBFMM_H

@@ -416,6 +416,7 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     c->opts = o;
     c->stream = (cudaStream_t)o.stream;
     LPB_CUDA(cudaGetDevice(&c->device));
+    if (c->device < 0 || c->device >= LPB_MAX_DEVICES) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
     std::vector<double> G = gaunt_table(p);
     std::vector<double> tp = tpoly_table(p, c->tpk);
     LPB_CUDA(cudaMalloc(&c->gaunt, sizeof(double) * G.size()));

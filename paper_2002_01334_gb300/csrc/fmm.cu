@@ -7,6 +7,8 @@
 #include "internal.h"
 #include "tc.cuh"
 
+#include <mutex>
+
 namespace lpb {
 
 // recurrence and gradient constants (index [n][m], n <= PMAX + 1)
@@ -1266,11 +1268,11 @@ struct Tables {
   int32_t *cls_free, *cls_react;  // [343], [2][3][343]
   void *rot, *rot4;               // per precision
 };
-Tables g_tab_d, g_tab_f;
-static bool g_tab_ready = false;
+Tables g_tab_d[LPB_MAX_DEVICES], g_tab_f[LPB_MAX_DEVICES];  // per device
+static std::atomic<uint64_t> g_tab_ready{0};
 
 static void make_tables(Ctx &c) {
-  if (g_tab_ready) return;
+  if (!not_done_on_device(g_tab_ready)) return;
   std::vector<int32_t> cf(NOFF, -1), cr(2 * 3 * NOFF, -1);
   const int r2v[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
   auto rho_idx = [&](int dx, int dy) {
@@ -1319,15 +1321,16 @@ static void make_tables(Ctx &c) {
   LPB_CUDA(cudaMemcpy(r4d, rot4.data(), sizeof(double) * rot4.size(), cudaMemcpyHostToDevice));
   LPB_CUDA(cudaMemcpy(rf, rotf.data(), sizeof(float) * rotf.size(), cudaMemcpyHostToDevice));
   LPB_CUDA(cudaMemcpy(r4f, rot4f.data(), sizeof(float) * rot4f.size(), cudaMemcpyHostToDevice));
-  g_tab_d = Tables{dcf, dcr, rd, r4d};
-  g_tab_f = Tables{dcf, dcr, rf, r4f};
-  g_tab_ready = true;
-  (void)c;
+  g_tab_d[c.device] = Tables{dcf, dcr, rd, r4d};
+  g_tab_f[c.device] = Tables{dcf, dcr, rf, r4f};
+  mark_done_on_device(g_tab_ready);
 }
 
 void upload_gl16();
 void upload_an();
 void init_fmm_tables(Ctx &c) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
   upload_gl16();
   upload_an();
   make_tables(c);
@@ -1732,14 +1735,10 @@ template <typename T, int TPT, int NR>
 static void launch_m2l_t(Ctx &c, const std::vector<XJob> &jobs, int64_t items) {
   constexpr int TT = 16 * TPT, KR = 16 * NR;
   const size_t smem = sizeof(T) * (2 * KR * M2L_KC + 2 * M2L_KC * TT) + sizeof(int) * 2 * TT;
-  static bool attr = false;
-  if (!attr) {
-    LPB_CUDA(cudaFuncSetAttribute(k_m2l<T, TPT, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  LPB_ATTR_ONCE((k_m2l<T, TPT, NR>), smem);
   XJob *dj = c.arena.get<XJob>(jobs.size());
   LPB_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(XJob) * jobs.size(), cudaMemcpyHostToDevice, c.stream));
-  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d[c.device] : g_tab_f[c.device];
   k_m2l<T, TPT, NR><<<(unsigned)items, 256, smem, c.stream>>>(dj, (int)jobs.size(), (const T *)tb.rot, c.K);
   LPB_LAUNCH();
   c.launches++;
@@ -1769,7 +1768,7 @@ template <typename T>
 static void upward_t(Ctx &c, Group &g, int parts) {
   typedef typename C2<T>::t T2;
   const int K = c.K, D = g.D;
-  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d[c.device] : g_tab_f[c.device];
   const bool dofree = g.is_free && (parts & 1);
   const bool doreact = (parts & 2) && g.I.np > 0;
   LamTab lt_t, lt_i;
@@ -1817,7 +1816,7 @@ template <typename T>
 static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
   constexpr int TPT = sizeof(T) == 4 ? 4 : 2;
   constexpr int TT = 16 * TPT;
-  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d[c.device] : g_tab_f[c.device];
   std::vector<XJob> jobs;
   int64_t items = 0;
   typedef typename C2<T>::t T2;
@@ -1923,12 +1922,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     switch (tc_nc) {
 #define LPB_TC_CASE(NCV)                                                                                     \
   case NCV: {                                                                                                \
-    static bool attr = false;                                                                                \
-    if (!attr) {                                                                                             \
-      LPB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NCV>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                    (int)tc_smem(NCV)));                                                     \
-      attr = true;                                                                                           \
-    }                                                                                                        \
+    LPB_ATTR_ONCE(k_m2l_tc<NCV>, tc_smem(NCV));                                                              \
     k_m2l_tc<NCV><<<(unsigned)titems, TC_THREADS, tc_smem(NCV), c.stream>>>(dj, (int)tjobs.size(), c.K, c.p, c.status); \
     break;                                                                                                   \
   }
@@ -1958,12 +1952,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
       it += m2l_tiles(j, F32_TT) * M2L_NSLICE;
     }
     const size_t smem = m2l_f32_smem(c.K);
-    static bool attr = false;
-    if (!attr) {  // the largest K of this kernel
-      LPB_CUDA(cudaFuncSetAttribute(k_m2l_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)m2l_f32_smem(F32_KR)));
-      attr = true;
-    }
+    LPB_ATTR_ONCE(k_m2l_f32, m2l_f32_smem(F32_KR));  // the largest K of this kernel
     XJob *dj = c.arena.get<XJob>(jobs.size());
     LPB_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(XJob) * jobs.size(), cudaMemcpyHostToDevice, c.stream));
     k_m2l_f32<<<(unsigned)it, 256, smem, c.stream>>>(dj, (int)jobs.size(), (const float *)tb.rot, c.K);
@@ -1984,7 +1973,7 @@ template <typename T>
 static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) {
   typedef typename C2<T>::t T2;
   const int K = c.K, D = g.D;
-  const Tables &tb = sizeof(T) == 8 ? g_tab_d : g_tab_f;
+  const Tables &tb = sizeof(T) == 8 ? g_tab_d[c.device] : g_tab_f[c.device];
   const bool dofree = g.is_free && (parts & 1);
   const bool doreact = (parts & 2) && g.I.np > 0;
   const bool react_near = doreact && !(parts & 4);

@@ -1,5 +1,6 @@
 // Internal declarations of the lpbfmm library (host orchestration + kernels).
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -31,6 +32,32 @@ struct CudaError {
     if (_e != cudaSuccess) throw ::lpb::CudaError{_e, #x}; \
   } while (0)
 #define LPB_LAUNCH() LPB_CUDA(cudaGetLastError())
+
+// Per-device one-time set-up (constant memory, kernel attributes and the offset tables are
+// per device).  LPB_MAX_DEVICES bounds the device ordinals a process may use.
+constexpr int LPB_MAX_DEVICES = 64;
+inline int current_device() {
+  int d = 0;
+  LPB_CUDA(cudaGetDevice(&d));
+  return d;
+}
+// true until mark_done() has been called for the current device
+inline bool not_done_on_device(const std::atomic<uint64_t> &mask) {
+  return !(mask.load() & (1ull << (current_device() & (LPB_MAX_DEVICES - 1))));
+}
+inline void mark_done_on_device(std::atomic<uint64_t> &mask) {
+  mask.fetch_or(1ull << (current_device() & (LPB_MAX_DEVICES - 1)));
+}
+// kernel attribute for the current device: set before the first launch on it (a race between
+// host threads can only repeat the call)
+#define LPB_ATTR_ONCE(kernel, bytes)                                                            \
+  do {                                                                                          \
+    static std::atomic<uint64_t> _m{0};                                                         \
+    if (not_done_on_device(_m)) {                                                               \
+      LPB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
+      mark_done_on_device(_m);                                                                  \
+    }                                                                                           \
+  } while (0)
 
 struct StatusError {
   int code;

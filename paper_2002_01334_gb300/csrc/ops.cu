@@ -149,9 +149,9 @@ __device__ void make_panels(double umax, double wmax, double lmin, double *pu, d
 
 // Gauss-Legendre 16-point rule on [-1,1] (nodes by Newton iteration on the host)
 __constant__ double c_glx[16], c_glw[16];
-static bool g_gl_ready = false;
+static std::atomic<uint64_t> g_gl_ready{0};
 void upload_gl16() {
-  if (g_gl_ready) return;
+  if (!not_done_on_device(g_gl_ready)) return;
   double x[16], w[16];
   for (int i = 0; i < 16; ++i) {
     long double z = cosl(3.14159265358979323846264338L * (i + 0.75L) / 16.5L), dp = 1;
@@ -171,7 +171,7 @@ void upload_gl16() {
   }
   LPB_CUDA(cudaMemcpyToSymbol(c_glx, x, sizeof x));
   LPB_CUDA(cudaMemcpyToSymbol(c_glw, w, sizeof w));
-  g_gl_ready = true;
+  mark_done_on_device(g_gl_ready);
 }
 __device__ __forceinline__ void gl16(double *x, double *w) {
   for (int i = 0; i < 16; ++i) { x[i] = c_glx[i]; w[i] = c_glw[i]; }
@@ -373,9 +373,9 @@ static NDesc node_desc(int KT, double tol, double Lam, double Lamp) {
 
 // a_n = sqrt(n (n+1)) and 1/a_n for n <= 2 KMAX_TAB + 1 (host, long double), for the recurrence
 __constant__ double c_an[2 * KMAX_TAB + 2], c_ian[2 * KMAX_TAB + 2];
-static bool g_an_ready = false;
+static std::atomic<uint64_t> g_an_ready{0};
 void upload_an() {
-  if (g_an_ready) return;
+  if (!not_done_on_device(g_an_ready)) return;
   double a[2 * KMAX_TAB + 2], ia[2 * KMAX_TAB + 2];
   for (int n = 0; n < 2 * KMAX_TAB + 2; ++n) {
     const long double v = sqrtl((long double)n * (n + 1));
@@ -384,7 +384,7 @@ void upload_an() {
   }
   LPB_CUDA(cudaMemcpyToSymbol(c_an, a, sizeof a));
   LPB_CUDA(cudaMemcpyToSymbol(c_ian, ia, sizeof ia));
-  g_an_ready = true;
+  mark_done_on_device(g_an_ready);
 }
 
 // forward recurrence in d (Sec. 3.5 eq. recurrence1), one warp per class:
@@ -723,12 +723,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
     LPB_LAUNCH();
     {
       const size_t sm = stab_quad_smem(KT);
-      static bool attr = false;
-      if (!attr) {  // the largest table any order needs
-        LPB_CUDA(cudaFuncSetAttribute(k_stab_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)stab_quad_smem(KMAX_TAB)));
-        attr = true;
-      }
+      LPB_ATTR_ONCE(k_stab_quad, stab_quad_smem(KMAX_TAB));  // the largest table any order needs
       k_stab_quad<<<dim3(NREACT_CLS, nd), SQ_CHUNK, sm, c.stream>>>(dr, dn, KT, c.sfac);
       LPB_LAUNCH();
     }
@@ -743,12 +738,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       const int l = rd[first].pad;
       size_t last = first;
       while (last < rd.size() && rd[last].pad == l) ++last;
-      static bool attr = false;
-      if (!attr) {
-        LPB_CUDA(cudaFuncSetAttribute(k_react_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)assemble_smem(KMAX_TAB)));
-        attr = true;
-      }
+      LPB_ATTR_ONCE(k_react_assemble<T>, assemble_smem(KMAX_TAB));
       k_react_assemble<T><<<dim3(NREACT_CLS, (unsigned)(last - first)), 256, assemble_smem(KT), c.stream>>>(
           dr + first, p, K, KT, c.sfac, (T *)g.op_react[l]);
       LPB_LAUNCH();
