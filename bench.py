@@ -51,6 +51,20 @@ def job_throughput(world, n, steps, ms):
     return world * n * steps / (ms / 1000.0)
 
 
+def profiled_traffic(kernel, path=None):
+    """DRAM bytes per evaluation of a kernel at the benchmark size, from the committed ncu summary
+    (a line 'traffic_bytes_per_eval <kernel> <bytes>'), or None when none is recorded."""
+    path = path or os.path.join(ROOT, "profiles", "traffic_three_layer_1M_p10.md")
+    try:
+        for line in open(path):
+            f = line.split()
+            if len(f) == 3 and f[0] == "traffic_bytes_per_eval" and f[1] == kernel:
+                return int(f[2])
+    except OSError:
+        pass
+    return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -286,11 +300,7 @@ def run_ours(args, rank, world, local_rank):
     tf32_peak = (bf16 if bf16 else 1900.0) * 1.1 / 2.25  # measured bf16 burst x nominal TF32/BF16 ratio
     per = lambda nm: phase_ms.get(nm, float("nan")) / args.steps
 
-    def traffic_of(kernel):
-        try:
-            return json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
-        except Exception:
-            return None
+    traffic_of = profiled_traffic
 
     def roof(kernel, bound, flops, t, peak, unit_note):
         a = flops / (t / 1e3) / 1e12

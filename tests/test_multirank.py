@@ -56,3 +56,12 @@ def test_two_gloo_ranks_take_the_slowest_rank_and_distinct_systems():
 def test_single_rank_needs_no_process_group():
     assert bench.max_over_ranks(7.5, None, "cpu") == 7.5
     assert bench.job_throughput(1, 1000, 2, 1000.0) == 2000.0
+
+
+def test_profiled_traffic_reads_the_committed_summary(tmp_path):
+    assert bench.profiled_traffic("k_p2p_free_f32") == 134246400
+    assert bench.profiled_traffic("k_m2l_tc") is None
+    f = tmp_path / "t.md"
+    f.write_text("text\ntraffic_bytes_per_eval k_x 42\n")
+    assert bench.profiled_traffic("k_x", str(f)) == 42
+    assert bench.profiled_traffic("k_x", str(tmp_path / "missing.md")) is None
