@@ -65,6 +65,20 @@ def profiled_traffic(kernel, path=None):
     return None
 
 
+def per_layer_errors(a, ref, layer, nlayers):
+    """Per layer k: relative L2 error ||a - ref|| / ||ref|| and relative max error
+    max|a - ref| / max|ref| over the targets in layer k (the paper's Err_2 / Err_max form)."""
+    out = []
+    for k in range(nlayers):
+        sel = layer == k
+        if not bool(sel.any()):
+            out.append(None)
+            continue
+        d, r = (a[sel] - ref[sel]).abs(), ref[sel].abs()
+        out.append({"layer": k, "err2": float(d.norm() / r.norm()), "errmax": float(d.max() / r.max())})
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,7 +296,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         accuracy = {"relL2_phi_mixed_vs_fp64": float(torch.linalg.norm(phi - p64) / torch.linalg.norm(p64)),
                     "relL2_field_mixed_vs_fp64": float(torch.linalg.norm(fld - f64) / torch.linalg.norm(f64)),
-                    "gate": 1e-6}
+                    "gate": 1e-6,
+                    "per_layer_phi": per_layer_errors(phi, p64, l, len(m["eps"]))}
         ctx64.close()
 
     device_status = ctx.status()  # 0 unless a bounded device wait ran out during the run

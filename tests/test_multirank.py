@@ -65,3 +65,14 @@ def test_profiled_traffic_reads_the_committed_summary(tmp_path):
     f.write_text("text\ntraffic_bytes_per_eval k_x 42\n")
     assert bench.profiled_traffic("k_x", str(f)) == 42
     assert bench.profiled_traffic("k_x", str(tmp_path / "missing.md")) is None
+
+
+def test_per_layer_errors_match_their_definition():
+    ref = torch.tensor([1.0, -2.0, 4.0, 0.5, 3.0], dtype=torch.float64)
+    a = ref + torch.tensor([0.1, 0.0, -0.2, 0.05, 0.0], dtype=torch.float64)
+    layer = torch.tensor([0, 0, 1, 1, 2], dtype=torch.int32)
+    e = bench.per_layer_errors(a, ref, layer, 4)
+    assert e[0]["err2"] == pytest.approx(0.1 / np.sqrt(5.0))
+    assert e[0]["errmax"] == pytest.approx(0.1 / 2.0)
+    assert e[1]["err2"] == pytest.approx(np.sqrt(0.04 + 0.0025) / np.sqrt(16.25))
+    assert e[2]["err2"] == 0.0 and e[3] is None
