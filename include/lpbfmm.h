@@ -55,7 +55,8 @@ extern "C" {
 
 /* precision modes */
 #define LPBFMM_FP64 0  /* every step in FP64                                                  */
-#define LPBFMM_MIXED 1 /* FP32 P2P, P2M/M2M/M2L/L2L/L2P; FP64 tables, operators and final sums */
+#define LPBFMM_MIXED 1 /* FP32 P2P, P2M/M2M/L2L/L2P; M2L on the tensor cores in 3xTF32 for
+                          p <= 10 (FP32 otherwise); FP64 tables, operators and final sums  */
 
 typedef struct lpbfmm_ctx *lpbfmm_t;
 
@@ -75,7 +76,8 @@ void lpbfmm_default_opts(lpbfmm_opts *opts);
  * Create a context for one medium and truncation order (Sec. 2.1 medium; Sec. 3.1 and 3.4
  * expansions truncated at degree p).  Host arrays: z_iface[n_iface] (strictly descending),
  * eps[n_iface+1] > 0, lambda[n_iface+1] > 0.  tol is the truncation tolerance of the
- * Sommerfeld integrals (Sec. 3.5, end: "decayed to a user specified tolerance"), in (0, 1e-3].
+ * Sommerfeld integrals (Sec. 3.5: the integration range ends where the integrand has fallen
+ * below a tolerance the user chooses), in (0, 1e-3].
  * The context allocates device tables for Gaunt coefficients and Legendre-product expansion
  * coefficients on the current device.  opts may be NULL (defaults).  On success *out holds a
  * new context that must be released with lpbfmm_destroy.

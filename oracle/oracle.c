@@ -8,8 +8,8 @@
  *
  * Contents (each function cites the passage it follows):
  *   orc_layer_response   reaction densities sigma^{ab}_{l l'}(lambda_rho) from the
- *                        transmission conditions (Sec. 2.1, eq. after "transmission
- *                        conditions"; the paper gives only L=2 explicitly, so the general
+ *                        transmission conditions (Sec. 2.1, the interface conditions on
+ *                        the densities; the paper gives only L=2 explicitly, so the general
  *                        L-layer densities are read as the solution of those conditions).
  *   orc_green_react      G^R_{l l'}(r,r') and grad_r by adaptive quadrature of the
  *                        alpha-integrated Sommerfeld integrals (Sec. 2.1, eqs.

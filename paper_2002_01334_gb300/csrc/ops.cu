@@ -9,7 +9,7 @@
 //    S^K S_{K d, ij} (eq. M2Ltable) by composite Gauss-Legendre quadrature for d = 0, 1,
 //    the forward recurrence (eq. recurrence1) for d >= 2, and a Legendre-product expansion
 //    of the two plane-wave factors (eq. metoletableform), in this library's own derivation.
-// Scaling (Sec. 3.5, "scaling"): with h the box size, multipole coefficients are stored as
+// Scaling (Sec. 3.5, the rescaled expansions): with h the box size, multipole coefficients are stored as
 // M~_n = M_n (2n+1)!!/(lambda h)^n and local ones as L~_n = c L_n (lambda h)^n/(2n+1)!!
 // (c = lambda/(2 pi^2 eps) for the free-space part, 1 for reaction parts), so that
 // phi = sum L~_nm itilde_n(lambda r) R_n^m(r/h) with R_n^m = r^n Y_n^m.
