@@ -89,6 +89,45 @@ def charges_in_boxes(seed, counts, zboxes, xy=(-0.5, 0.5), interleave=True):
     return q, xyz, layer
 
 
+# The irregular bodies of the paper's three-layer example (Sec. 4): around a centre on the z axis
+# the surface is r(theta) = 0.5 - a + (a/8)(35 cos^4 theta - 30 cos^2 theta + 3), with
+# (a, centre z) below for layers 0, 1, 2; 912 + 640 + 1296 charges in the accuracy test.
+PAPER_BODIES = [(0.10, 0.6), (0.15, -0.6), (0.05, -1.8)]
+PAPER_COUNTS = (912, 640, 1296)
+
+
+def body_radius(a, cos_t):
+    """Radius of the body surface in the direction with cos(theta) = cos_t."""
+    c2 = cos_t * cos_t
+    return 0.5 - a + (a / 8.0) * (35.0 * c2 * c2 - 30.0 * c2 + 3.0)
+
+
+def charges_in_bodies(seed, counts, bodies=PAPER_BODIES, batch=4096):
+    """q ~ U[-1,1]; the charges of layer k are uniform points of the cube
+    [-0.5,0.5]^2 x [zc-0.5, zc+0.5] kept when inside body k (the body fits in that cube), drawn in
+    batches until counts[k] are kept.  Layers are interleaved round-robin like charges_in_boxes."""
+    n = int(sum(counts))
+    s = Stream(seed)
+    q = s.u(n, -1.0, 1.0)
+    per = []
+    for (a, zc), cnt in zip(bodies, counts):
+        kept = np.empty((0, 3))
+        while len(kept) < cnt:
+            raw = s.u(3 * batch).reshape(batch, 3) - 0.5
+            r = np.sqrt((raw * raw).sum(axis=1))
+            cos_t = np.where(r > 0, raw[:, 2] / np.where(r > 0, r, 1.0), 1.0)
+            inside = r <= body_radius(a, cos_t)
+            kept = np.concatenate([kept, raw[inside]])
+        pts = kept[:cnt].copy()
+        pts[:, 2] += zc
+        per.append(pts)
+    nl = len(counts)
+    labels = np.repeat(np.arange(nl, dtype=np.int32), counts)
+    rank = np.concatenate([np.arange(c, dtype=np.int64) * nl + k for k, c in enumerate(counts)])
+    order = np.argsort(rank, kind="stable")
+    return q, np.concatenate(per)[order], labels[order]
+
+
 def even_split(n, nl):
     base = n // nl
     return [base + (1 if k < n - base * nl else 0) for k in range(nl)]
@@ -111,6 +150,16 @@ def workload(name, n=None, seed=None):
         seed = BASE_SEED + 4 if seed is None else seed
         q, xyz, layer = charges_in_boxes(seed, even_split(n, 4), FOUR_LAYER_BOXES)
         return dict(medium=MEDIA["four_layer"], q=q, xyz=xyz, layer=layer, p=8, depth=None)
+    if name == "paper_irregular":
+        # the paper's accuracy-test workload; n scales the three counts in proportion
+        counts = list(PAPER_COUNTS)
+        if n is not None:
+            tot = sum(PAPER_COUNTS)
+            counts = [int(round(n * c / tot)) for c in PAPER_COUNTS]
+            counts[-1] = n - sum(counts[:-1])
+        seed = BASE_SEED + 5 if seed is None else seed
+        q, xyz, layer = charges_in_bodies(seed, counts)
+        return dict(medium=MEDIA["paper_three_layer"], q=q, xyz=xyz, layer=layer, p=10, depth=None)
     raise KeyError(name)
 
 

@@ -1,0 +1,47 @@
+"""Seeded input generators (no GPU): the irregular bodies of the paper's three-layer example
+(Sec. 4) and the box workloads keep their charges where the recipe puts them, reproducibly."""
+import numpy as np
+
+from paper_2002_01334_gb300 import inputs
+
+
+def test_body_radius_closed_form():
+    for a in (0.05, 0.1, 0.15):
+        assert inputs.body_radius(a, 1.0) == 0.5  # poles: 35 - 30 + 3 = 8
+        assert inputs.body_radius(a, -1.0) == 0.5
+        # the minimum, at cos^2 = 3/7: 35 (9/49) - 30 (3/7) + 3 = -24/7
+        assert np.isclose(inputs.body_radius(a, np.sqrt(3.0 / 7.0)), 0.5 - 10.0 * a / 7.0)
+        assert np.isclose(inputs.body_radius(a, 0.0), 0.5 - a + 3.0 * a / 8.0)
+
+
+def test_paper_irregular_workload_geometry():
+    w = inputs.workload("paper_irregular")
+    q, xyz, layer = w["q"], w["xyz"], w["layer"]
+    assert w["medium"] == inputs.MEDIA["paper_three_layer"]
+    assert [int((layer == k).sum()) for k in range(3)] == list(inputs.PAPER_COUNTS)
+    assert np.all(np.abs(q) <= 1.0)
+    d = w["medium"]["d"]
+    for k, (a, zc) in enumerate(inputs.PAPER_BODIES):
+        p = xyz[layer == k] - np.array([0.0, 0.0, zc])
+        r = np.linalg.norm(p, axis=1)
+        cos_t = np.where(r > 0, p[:, 2] / np.maximum(r, 1e-300), 1.0)
+        assert np.all(r <= inputs.body_radius(a, cos_t) + 1e-15)
+        z = xyz[layer == k, 2]
+        lo = d[k] if k < len(d) else -np.inf
+        hi = d[k - 1] if k > 0 else np.inf
+        assert np.all((z > lo + 0.0999) & (z < hi - 0.0999))  # 0.1 from the interfaces
+    assert len(set(layer[:3].tolist())) == 3  # interleaved, not sorted by layer
+
+
+def test_generators_are_reproducible():
+    a = inputs.workload("paper_irregular", seed=7)
+    b = inputs.workload("paper_irregular", seed=7)
+    c = inputs.workload("paper_irregular", seed=8)
+    assert np.array_equal(a["xyz"], b["xyz"]) and np.array_equal(a["q"], b["q"])
+    assert not np.array_equal(a["xyz"], c["xyz"])
+    s = inputs.workload("paper_irregular", n=10000)
+    assert len(s["q"]) == 10000
+    t = inputs.workload("three_layer", n=3000, seed=3)
+    for k, (lo, hi) in enumerate(inputs.THREE_LAYER_BOXES):
+        z = t["xyz"][t["layer"] == k, 2]
+        assert np.all((z >= lo) & (z <= hi))
