@@ -307,7 +307,9 @@ __global__ void k_l2l(const uint32_t *d_nc, const uint32_t *cparent, const uint6
 // (job, tile of target boxes, slice dx of the 343 offsets).  For every offset of its slice
 // the class operator (P, Q) and the phase-rotated multipoles of the tile's sources are staged
 // in shared memory in K-chunks and multiplied as a small GEMM (rows = output coefficients,
-// columns = target boxes); the tile's partial local expansions are added atomically.
+// columns = target boxes); each target's partial local expansion of the slice is written to
+// its own slot [box][slot] and the slots are summed in a fixed order (k_m2l_reduce), so the
+// result does not depend on scheduling.  (FP64 mode and p > 10; the mixed mode uses k_m2l_tc.)
 // ---------------------------------------------------------------------------------------
 constexpr int M2L_KC = 32;
 constexpr int M2L_NSLICE = 7;  // offsets with dx = -3..3, 49 each
@@ -350,12 +352,6 @@ __device__ __forceinline__ int m2l_target(const XJob &J, int64_t ti, int j, int 
   return t < ntl ? (J.tlist ? J.tlist[t] : (int)t) : -1;
 }
 constexpr int M2L_NSLOT = 2 * M2L_NSLICE;  // free-space slices, then reaction slices
-
-template <typename T>
-__device__ __forceinline__ void atomic_add2(typename C2<T>::t *p, T x, T y) {
-  atomicAdd(&p->x, x);
-  atomicAdd(&p->y, y);
-}
 
 template <typename T, int TPT, int NR>
 __global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const T *rot, int K) {
@@ -489,7 +485,7 @@ __global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const 
 // every step copies the class operator (P, Q, K x K) and the tile's source multipoles into a
 // shared-memory stage with cp.async while the previous step is multiplied.  After a stage lands
 // the multipoles are rotated by e^{i mu phi} in place; the product is rotated by e^{-i m phi}
-// into the register accumulators, which are added atomically at the end.
+// into the register accumulators, which are written to the slice's partial slots at the end.
 constexpr int F32_TPT = 6, F32_TT = 16 * F32_TPT, F32_NR = 5, F32_KR = 16 * F32_NR;
 constexpr int F32_MAXSTEP = 49 * 2 * MAXLAYER;
 
