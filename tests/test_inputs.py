@@ -45,3 +45,22 @@ def test_generators_are_reproducible():
     for k, (lo, hi) in enumerate(inputs.THREE_LAYER_BOXES):
         z = t["xyz"][t["layer"] == k, 2]
         assert np.all((z >= lo) & (z <= hi))
+
+
+def test_paper_irregular_oracle_fixture_matches_the_oracle():
+    """The stored reference (tests/golden/make_paper_irregular_oracle.py) is reproduced by the
+    oracle on the regenerated workload, so generator and fixture stay in step."""
+    import json
+    import os
+
+    import oracle
+
+    oracle.build()
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_irregular_oracle.json")))
+    w = inputs.workload("paper_irregular")
+    md = oracle.Medium(**w["medium"])
+    pick = [0, 101, 250, 355]
+    tg = np.array([g["targets"][k] for k in pick])
+    phi, fld = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=tg)
+    assert np.allclose(phi, [g["phi"][k] for k in pick], rtol=1e-12, atol=0)
+    assert np.allclose(fld, [g["field"][k] for k in pick], rtol=1e-12, atol=1e-15)
