@@ -197,7 +197,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.n, args.p, "fp64 direct sum (CPU oracle)"), "cpu_baseline": info,
+            "config": dict(workload_config(args.n, args.p, "fp64 direct sum (CPU oracle)"),
+                           l2="not applicable (host cores)"), "cpu_baseline": info,
             "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
