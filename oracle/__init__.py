@@ -5,7 +5,9 @@ Wang, Zhang & Cai, arXiv 2002.01334.  Only tests/, ``__graft_entry__.smoke()`` a
 CPU-baseline leg of ``bench.py`` may import this package; the product path never does.
 
 Parity status of each function is stated in tests/test_oracle_pins.py, which pins it
-against closed forms, the paper's printed formulas, invariants and brute force.
+against closed forms, the paper's printed formulas, invariants and brute force.  The
+submodule ``expansions`` restates the truncated expansions of Sec. 3 (numpy/scipy);
+tests/test_expansion_pins.py checks that they converge in p to this package's direct values.
 """
 import ctypes as C
 import os

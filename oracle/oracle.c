@@ -27,8 +27,10 @@
  *                        bit-exact tree/list parity test.
  *
  * Parity: every function above is pinned by tests/test_oracle_pins.py except where noted
- * there.  Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no FMA contraction so
- * that the tree keys are the exact IEEE results of the stated formula).
+ * there; orc_green_react_ab is also the limit that the truncated reaction ME, LE and M2L of
+ * Sec. 3.4 (expansions.py) must converge to, in tests/test_expansion_pins.py.
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no FMA contraction so that the
+ * tree keys are the exact IEEE results of the stated formula).
  */
 #include <math.h>
 #include <stdint.h>
