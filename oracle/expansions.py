@@ -19,7 +19,12 @@ Contents (each cites the passage it follows):
   reaction_le          LE of a reaction component about a target centre (Sec. 3.4, eqs.
                        lelayerimage and lecoeffimage).
   reaction_m2l         the M2L operator T of a reaction component (Sec. 3.4, eqs. metoleimage1
-                       and metoleimage2).
+                       and metoleimage2), by direct quadrature.
+  legendre_product_coeffs, reaction_m2l_tables
+                       the same operator by the table route of Sec. 3.5: products of two
+                       Legendre functions as polynomials in lambda_rho (exact rational
+                       coefficients), contracted with the Sommerfeld-type integrals S_{N M, ij}
+                       of eq. M2Ltable (eqs. uniformintegral, coefintable, metoletableform).
 
 The alpha-integrals of the Sommerfeld-type integrals are done in closed form with the Bessel
 identity of Sec. 3.5 (J_n as an integral over the circle): for a horizontal offset with polar
@@ -35,12 +40,13 @@ source offset (the printed 1b superscript is a typo).
 """
 import functools
 import math
+from fractions import Fraction
 
 import numpy as np
 from numpy.polynomial import legendre as npleg
 from scipy import integrate, special
 
-from . import layer_response
+from . import S_table, layer_response
 
 
 # ------------------------------------------------------------------------------------------
@@ -320,3 +326,89 @@ def reaction_m2l(md, l, lp, a, b, rct, rcs, p, P, tol=1e-13):
         return (pre * base * np.outer(pt, ps) * special.jv(k, lr * d)).ravel().view(float)
 
     return _quad(f, tol).view(complex).reshape(len(ti), len(si))
+
+
+# ------------------------------------------------------------------------------------------
+# The table form of the reaction M2L (Sec. 3.5): Legendre products as polynomials in lambda_rho
+# and Sommerfeld-type integrals S_{N M, ij} (eqs. uniformintegral, coefintable, M2Ltable,
+# metoletableform)
+
+def _legendre_power(n):
+    """Exact power-basis coefficients of the Legendre polynomial P_n (index = power of x)."""
+    c = [Fraction(0)] * (n + 1)
+    for k in range(n // 2 + 1):
+        c[n - 2 * k] = Fraction((-1) ** k * math.comb(n, k) * math.comb(2 * n - 2 * k, n), 2 ** n)
+    return c
+
+
+@functools.lru_cache(maxsize=None)
+def _phat_t_poly(n, m):
+    """phat_n^m(x) at x = lz/lam (lz = sqrt(lam^2 + lr^2)) written as
+    (-1)^m c_nm (-i)^|m| (lr/lam)^|m| (lam/lz)^i sum_u e_u (lr/lam)^{2u},
+    with i = (n + |m|) mod 2 and exact rationals e_u.  With x^2 = 1 + t, t = (lr/lam)^2:
+    d^|m| P_n / dx^|m| has the parity of n - |m|; for odd parity one factor x is taken out as
+    x = x^2 / x = (1 + t) (lam/lz), and x^{2q} = (1 + t)^q is expanded binomially.
+    Returns (i, e) with e a tuple of Fractions."""
+    am = abs(m)
+    c = _legendre_power(n)
+    for _ in range(am):  # differentiate |m| times
+        c = [c[k + 1] * (k + 1) for k in range(len(c) - 1)] or [Fraction(0)]
+    i = (n + am) % 2
+    # multiply by x when odd so that only even powers remain
+    if i:
+        c = [Fraction(0)] + c
+    e = [Fraction(0)] * (len(c) // 2 + 1)
+    for k in range(0, len(c), 2):
+        q = k // 2
+        for u in range(q + 1):
+            e[u] += c[k] * math.comb(q, u)
+    while len(e) > 1 and e[-1] == 0:
+        e.pop()
+    return i, tuple(e)
+
+
+def _phat_lr_coeffs(n, m, lam):
+    """Complex g_u with phat_n^m(lz/lam) = (lam/lz)^i lr^|m| sum_u g_u lr^{2u}; returns (i, g)."""
+    am = abs(m)
+    i, e = _phat_t_poly(n, m)
+    sign = (-1.0) ** am * ((-1.0) ** am if m < 0 else 1.0)
+    pre = sign * _norm(n, am) * (-1j) ** am / lam ** am
+    return i, np.array([pre * float(eu) / lam ** (2 * u) for u, eu in enumerate(e)])
+
+
+def legendre_product_coeffs(n, m, nu, mu, lam, lamp):
+    """C^s of Sec. 3.5: phat_n^m(lz/lam) phat_nu^mu(lz'/lam') =
+    sum_s C^s lr^{|m| + |mu| + 2s} (lam/lz)^i (lam'/lz')^j; returns (i, j, C)."""
+    i, g = _phat_lr_coeffs(n, m, lam)
+    j, gp = _phat_lr_coeffs(nu, mu, lamp)
+    return i, j, np.convolve(g, gp)
+
+
+def reaction_m2l_tables(md, l, lp, a, b, rct, rcs, p, P, tol=1e-13):
+    """M2L operator T (n <= p, nu <= P) by the table route of Sec. 3.5: T = sign e^{i(mu-m)phi}
+    I_{nm,nu mu} (eq. coefintable), I = i^{mu-m} sum_s C~^s S_{N, mu-m, ij} (eq. metoletableform)
+    with N = |m| + |mu| + 2s + 1 and C~^s = sqrt((N + mu - m)! (N - mu + m)!) C^s, the tables S
+    by the oracle's direct quadrature (orc_S_table, unscaled), and S_{N,-M} = (-1)^M S_{N,M}."""
+    c = _Comp(md, l, lp, a, b)
+    rct = np.asarray(rct, float)
+    rcs = np.asarray(rcs, float)
+    d, phd = _polar(rct[0] - rcs[0], rct[1] - rcs[1])
+    if a == 1:
+        zt, zs = rct[2] - c.dI, c.dI - rcs[2]
+    else:
+        zt, zs = c.dI - rct[2], rcs[2] - c.dI
+    S = S_table(md, l, lp, a, b, 1.0, d, zt, zs, p + P + 3, tol)
+    ti, si = _nm(p), _nm(P)
+    T = np.zeros((len(ti), len(si)), complex)
+    for x, (n, m) in enumerate(ti):
+        for y, (nu, mu) in enumerate(si):
+            i, j, C = legendre_product_coeffs(n, m, nu, mu, c.lam, c.lamp)
+            M = mu - m
+            acc = 0j
+            for s, Cs in enumerate(C):
+                N = abs(m) + abs(mu) + 2 * s + 1
+                Ct = math.sqrt(math.factorial(N + M) * math.factorial(N - M)) * Cs
+                acc += Ct * S[N, abs(M), i, j] * ((-1.0) ** abs(M) if M < 0 else 1.0)
+            sgn = (-1.0) ** n if a == 1 else (-1.0) ** (nu + m + mu)
+            T[x, y] = sgn * np.exp(1j * M * phd) * (1j) ** M * acc
+    return T

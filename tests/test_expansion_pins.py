@@ -187,3 +187,32 @@ def test_me_convergence_fixture_matches_the_oracle():
         s = E.reaction_me(md, 1, 1, a, b, row["target"], rimg, np.array(row["centre"]), fx["pmax"])
         err = np.abs(s - u) / abs(u)
         assert np.abs(err - np.array(row["rel_err"])).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,m,nu,mu,lam,lamp", [(3, 1, 2, -2, 0.5, 1.2), (7, -4, 6, 3, 0.8, 0.8),
+                                                (10, 0, 9, 9, 2.1, 0.5), (10, 7, 10, -10, 1.0, 0.3)])
+def test_legendre_product_as_polynomial_in_lambda_rho(n, m, nu, mu, lam, lamp):
+    """Sec. 3.5: phat_n^m(lz/lam) phat_nu^mu(lz'/lam') = sum_s C^s lr^{|m|+|mu|+2s}
+    (lam/lz)^i (lam'/lz')^j with i, j the parities of n + |m|, nu + |mu|."""
+    i, j, C = E.legendre_product_coeffs(n, m, nu, mu, lam, lamp)
+    assert (i, j) == ((n + abs(m)) % 2, (nu + abs(mu)) % 2)
+    for lr in (0.01, 0.7, 3.3, 12.0):
+        lz, lzp = math.hypot(lam, lr), math.hypot(lamp, lr)
+        ex = E.phat(n, m, lz / lam) * E.phat(nu, mu, lzp / lamp)
+        v = sum(Cs * lr ** (abs(m) + abs(mu) + 2 * s) for s, Cs in enumerate(C)) * (lam / lz) ** i * (lamp / lzp) ** j
+        assert abs(v - ex) <= 1e-10 * abs(ex)
+
+
+@pytest.mark.parametrize("ab", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_m2l_table_route_matches_direct_quadrature(ab):
+    """The M2L operator by the table route of Sec. 3.5 (eqs. coefintable, metoletableform with the
+    oracle's S-tables of eq. M2Ltable, reading the garbled symbol in C~ as a factorial) equals the
+    operator by direct quadrature of eq. metoleimage2, entry by entry."""
+    md = e1_medium()
+    a, b = ab
+    rimg = image(md, 1, a, 1, b, E1_SOURCE)
+    rcs = rimg + np.array([-0.03, 0.08, 0.06 if a == 1 else -0.06])
+    rct = np.array([0.57, 0.575, -0.56])
+    Td = E.reaction_m2l(md, 1, 1, a, b, rct, rcs, 6, 6)
+    Tt = E.reaction_m2l_tables(md, 1, 1, a, b, rct, rcs, 6, 6)
+    assert np.all(np.abs(Tt - Td) <= 1e-11 * np.abs(Td) + 1e-300)
