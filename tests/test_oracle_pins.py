@@ -8,7 +8,9 @@ Parity status of the oracle's functions:
   layer_response  pinned: paper's printed 3-layer densities (Sec. 2.1), homogeneous medium,
                   two half-spaces closed form.
   green_react     pinned: homogeneous medium (P6), two half-spaces images (P7), reciprocity (P8),
-                  finite differences of the field.
+                  finite differences of the field; each component agrees with a second,
+                  independent quadrature (scipy) and with the limit of its truncated ME/LE
+                  (tests/test_expansion_pins.py).
   direct          pinned: equals the sum of green_react / closed forms; reciprocity of the
                   assembled potential.
   S_table         pinned: Sommerfeld identity closed forms for K=1,d=0 and K=2,d=1 in a
@@ -163,6 +165,55 @@ def test_field_is_minus_gradient():
         gp, _ = oracle.green_react(md, 2, r + e, 1, rp)
         gm, _ = oracle.green_react(md, 2, r - e, 1, rp)
         assert abs(-(gp - gm) / (2 * h) - f[k]) < 1e-8 * np.abs(f).max()
+
+
+def _scipy_component(md, l, r, lp, rp, a, b):
+    """u^{ab}_{l l'}(r, r') and -grad_r of eq. generalcomponents (Sec. 2.2) after the alpha
+    integral, by scipy's QUADPACK on [0, X]: (1/4 pi) int lr J0(lr rho) e^{-lz h - lz' h'}
+    sigma / lz d lr, with h, h' the exponents' distances of eq. zexponential."""
+    from scipy import integrate, special
+    d = md.d
+    h = r[2] - d[l] if a == 1 else d[l - 1] - r[2]
+    hp = rp[2] - d[lp] if b == 1 else d[lp - 1] - rp[2]
+    dx, dy = r[0] - rp[0], r[1] - rp[1]
+    rho = np.hypot(dx, dy)
+    X = 80.0 / (h + hp)
+    pts = list(np.arange(np.pi / rho, X, np.pi / rho)) if rho > 0 else None
+
+    def g(lr, k):
+        lz = np.hypot(md.lam[l], lr)
+        lzp = np.hypot(md.lam[lp], lr)
+        e = np.exp(-lz * h - lzp * hp) * oracle.sigma(md, lr, l, lp, a, b) / lz / (4 * np.pi)
+        if k == 0:
+            return lr * special.j0(lr * rho) * e
+        if k == 1:  # -d/dx and -d/dy share lr^2 J1(lr rho) / rho
+            return lr * lr * (special.j1(lr * rho) / rho if rho > 0 else 0.5 * lr) * e
+        return lr * special.j0(lr * rho) * e * lz * (1.0 if a == 1 else -1.0)
+
+    v = [integrate.quad(g, 0.0, X, args=(k,), points=pts, limit=4000, epsabs=0.0, epsrel=1e-13)[0]
+         for k in range(3)]
+    return v[0], np.array([dx * v[1], dy * v[1], v[2]])
+
+
+@pytest.mark.parametrize("medium", ["three_layer", "four_layer"])
+def test_green_react_ab_agrees_with_a_second_quadrature(medium):
+    """Two independent quadratures of the same component integral (the oracle's adaptive
+    Gauss-Kronrod in C, scipy's QUADPACK here) agree for every component type."""
+    m = inputs.MEDIA[medium]
+    md = oracle.Medium(m["d"], m["eps"], m["lam"])
+    rng = np.random.default_rng(11)
+    L = md.L
+    mids = [md.d[0] + 0.6] + [0.5 * (md.d[k - 1] + md.d[k]) for k in range(1, L)] + [md.d[L - 1] - 0.6]
+    for l in range(L + 1):
+        for lp in range(L + 1):
+            for a in ((1,) if l == 0 else (2,) if l == L else (1, 2)):
+                for b in ((1,) if lp == 0 else (2,) if lp == L else (1, 2)):
+                    r = np.array([*rng.uniform(-0.4, 0.4, 2), mids[l] + rng.uniform(-0.1, 0.1)])
+                    rp = np.array([*rng.uniform(-0.4, 0.4, 2), mids[lp] + rng.uniform(-0.1, 0.1)])
+                    u, f = oracle.green_react_ab(md, l, r, lp, rp, a, b)
+                    us, fs = _scipy_component(md, l, r, lp, rp, a, b)
+                    assert abs(u - us) <= 1e-11 * abs(us), (l, lp, a, b, u, us)
+                    assert np.abs(f - fs).max() <= 1e-10 * np.abs(fs).max(), (l, lp, a, b, f, fs)
 
 
 def test_direct_matches_pairwise_definition():
