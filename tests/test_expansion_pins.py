@@ -16,8 +16,10 @@ import os
 import numpy as np
 import pytest
 
-import oracle
-from oracle import expansions as E
+pytest.importorskip("scipy")
+
+import oracle  # noqa: E402
+from oracle import expansions as E  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
