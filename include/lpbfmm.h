@@ -221,6 +221,40 @@ void lpbfmm_destroy(lpbfmm_t h);
  */
 int lpbfmm_last_profile(lpbfmm_t h, int cap, const char **names, float *ms, int *launches);
 
+/*
+ * The host-side tables that lpbfmm_create computes for order p and uploads to the device, computed
+ * here on the host alone: no context, no device, no CUDA call.  Intended for tests of the table
+ * construction.  which selects the table; all entries are FP64.  Index helpers:
+ * f(n, m) = n^2 + n + m (full, |m| <= n), h(n, m) = n(n+1)/2 + m (half, 0 <= m <= n).
+ *   LPBFMM_TABLE_GAUNT     G[f(n,a)][f(nu,g)][q], n, nu <= p, q <= 2p: the integral over the unit
+ *                          sphere of Y_n^a Y_q^{g-a} conj(Y_nu^g), the Gaunt coefficients of the
+ *                          free-space translation theorems (Sec. 3.1, Thm. 2-3); Y_n^m as in
+ *                          Sec. 3.1 (equal to the Condon-Shortley harmonics).  Zero where
+ *                          |g - a| > q or n + nu + q is odd.
+ *   LPBFMM_TABLE_TPOLY     c[h(n,m)][k], k < p/2 + 2 (row stride p/2 + 2): the ratio of normalized
+ *                          Legendre functions phat_n^m(x) / phat_m^m(x) written as
+ *                          x^{-i} sum_k c_k t^k with t = x^2 - 1, i = (n - m) mod 2.  These are the
+ *                          Legendre-product expansions behind the reaction M2L operators of
+ *                          Sec. 3.5 (eqs. metoletableform and the product formula before it).
+ *   LPBFMM_TABLE_PHAT_DIR  P[dir][h(q,k)], q <= 2p: phat_q^k(cos theta) of the 72 translation
+ *                          directions: dir = 7 ri + dz + 3 (ri indexes rho^2 in {0, 1, 2, 4, 5, 8,
+ *                          9, 10, 13, 18}, dz in -3..3) with cos theta = -dz / sqrt(rho^2 + dz^2)
+ *                          (1 when both vanish), and dir 70, 71 with cos theta = -1/sqrt(3),
+ *                          +1/sqrt(3) (child-to-parent shifts).
+ *   LPBFMM_TABLE_SFAC      s[K][d], K, d < 36 (row stride 36): sqrt((K+d)! (K-d)!) for d <= K, else
+ *                          0; the normalization of the Sommerfeld-type integrals (Sec. 3.5, eq.
+ *                          M2Ltable).  Independent of p.
+ * If out is NULL only *count (the number of doubles) is set; otherwise out must hold cap >= *count
+ * doubles and receives the table.  Returns LPBFMM_ERR_ARG for a null count, an unknown table or a
+ * short buffer, LPBFMM_ERR_P for p outside [LPBFMM_P_MIN, LPBFMM_P_MAX], LPBFMM_ERR_OOM if host
+ * memory runs out.
+ */
+#define LPBFMM_TABLE_GAUNT 0
+#define LPBFMM_TABLE_TPOLY 1
+#define LPBFMM_TABLE_PHAT_DIR 2
+#define LPBFMM_TABLE_SFAC 3
+int lpbfmm_host_table(int which, int p, double *out, int64_t cap, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -412,3 +412,13 @@ def reaction_m2l_tables(md, l, lp, a, b, rct, rcs, p, P, tol=1e-13):
             sgn = (-1.0) ** n if a == 1 else (-1.0) ** (nu + m + mu)
             T[x, y] = sgn * np.exp(1j * M * phd) * (1j) ** M * acc
     return T
+
+
+def phat_ratio_t_coeffs(n, m):
+    """phat_n^m(x) / phat_m^m(x) = x^{-i} sum_k c_k t^k with t = x^2 - 1 and i = (n - m) mod 2,
+    0 <= m <= n (Sec. 3.1 normalization; the ratio is a polynomial in x, free of the square-root
+    branch).  From the definition: the ratio is N_nm d^m P_n / (N_mm d^m P_m) with d^m P_m the
+    constant (2m)! / (2^m m!), expanded exactly as in _phat_t_poly.  Returns (i, c) floats."""
+    i, e = _phat_t_poly(n, m)
+    scale = _norm(n, m) / (_norm(m, m) * math.factorial(2 * m) / (2 ** m * math.factorial(m)))
+    return i, [float(ek) * scale for ek in e]

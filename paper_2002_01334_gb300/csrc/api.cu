@@ -786,4 +786,27 @@ int lpbfmm_stable_noalloc(lpbfmm_t h, int l, int a, int lp, int b, double hbox, 
   return LPBFMM_OK;
 }
 
+int lpbfmm_host_table(int which, int p, double *out, int64_t cap, int64_t *count) {
+  if (!count) return LPBFMM_ERR_ARG;
+  if (p < LPBFMM_P_MIN || p > LPBFMM_P_MAX) return LPBFMM_ERR_P;
+  std::vector<double> t;
+  try {
+    int tpk = 0;
+    switch (which) {
+      case LPBFMM_TABLE_GAUNT: t = gaunt_table(p); break;
+      case LPBFMM_TABLE_TPOLY: t = tpoly_table(p, tpk); break;
+      case LPBFMM_TABLE_PHAT_DIR: t = phat_dir_table(p); break;
+      case LPBFMM_TABLE_SFAC: t = sfac_table(); break;
+      default: return LPBFMM_ERR_ARG;
+    }
+  } catch (const std::bad_alloc &) {
+    return LPBFMM_ERR_OOM;
+  }
+  *count = (int64_t)t.size();
+  if (!out) return LPBFMM_OK;
+  if (cap < *count) return LPBFMM_ERR_ARG;
+  std::copy(t.begin(), t.end(), out);
+  return LPBFMM_OK;
+}
+
 }  // extern "C"

@@ -64,6 +64,7 @@ def lib():
         L.lpbfmm_destroy.restype = None
         L.lpbfmm_last_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_float),
                                           C.POINTER(C.c_int)]
+        L.lpbfmm_host_table.argtypes = [C.c_int, C.c_int, dp, i64, C.POINTER(i64)]
         _lib = L
     return _lib
 
@@ -212,6 +213,22 @@ class Context:
         _check(lib().lpbfmm_stable_noalloc(self.h, l, a, lp, b, float(h), float(rho), float(zt), float(zs), Kmax,
                                            C.c_void_p(out.data_ptr())), "lpbfmm_stable_noalloc")
         return out
+
+
+TABLE_GAUNT, TABLE_TPOLY, TABLE_PHAT_DIR, TABLE_SFAC = 0, 1, 2, 3
+
+
+def host_table(which, p):
+    """lpbfmm_host_table: one host-side table of lpbfmm_create for order p, as a flat float64
+    numpy array (computed on the host; no device needed)."""
+    import numpy as np
+    L = lib()
+    n = C.c_int64()
+    _check(L.lpbfmm_host_table(which, p, None, 0, C.byref(n)), "lpbfmm_host_table")
+    out = np.zeros(n.value)
+    _check(L.lpbfmm_host_table(which, p, out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)),
+           "lpbfmm_host_table")
+    return out
 
 
 def eval_batched(ctxs, offsets, q, xyz, layer, field=True):
