@@ -218,3 +218,26 @@ def test_m2l_table_route_matches_direct_quadrature(ab):
     Td = E.reaction_m2l(md, 1, 1, a, b, rct, rcs, 6, 6)
     Tt = E.reaction_m2l_tables(md, 1, 1, a, b, rct, rcs, 6, 6)
     assert np.all(np.abs(Tt - Td) <= 1e-11 * np.abs(Td) + 1e-300)
+
+
+@pytest.mark.parametrize("ab", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_m2l_operator_is_real_at_zero_azimuth(ab):
+    """With the horizontal offset along +x the reaction M2L operator is real: the i^{mu-m} of
+    the Bessel identity cancels the (-i)^{|m|+|mu|} of the Legendre branch (Prop. 1).  This is
+    what lets an operator class be stored as two real matrices (for Re and Im of the source
+    coefficients) with the azimuth applied as phases."""
+    md = e1_medium()
+    a, b = ab
+    dI = md.d[1] if a == 1 else md.d[0]
+    h = 0.25
+    rct = np.array([0.8, 0.1, dI + (1.5 * h if a == 1 else -1.5 * h)])
+    rcs = np.array([0.3, 0.1, dI + (-0.5 * h if a == 1 else 0.5 * h)])
+    T = E.reaction_m2l(md, 1, 1, a, b, rct, rcs, 6, 6)
+    assert np.abs(T.imag).max() <= 1e-14 * np.abs(T).max()
+    # rotating the offset by phi multiplies entry (nm, nu mu) by e^{i (mu - m) phi}
+    c, s = np.cos(0.7), np.sin(0.7)
+    rct2 = rcs + np.array([0.5 * c, 0.5 * s, rct[2] - rcs[2]])
+    T2 = E.reaction_m2l(md, 1, 1, a, b, rct2, rcs, 6, 6)
+    ti, si = E._nm(6), E._nm(6)
+    ph = np.exp(1j * 0.7 * np.array([[mu - m for _, mu in si] for _, m in ti]))
+    assert np.abs(T2 - ph * T).max() <= 1e-12 * np.abs(T).max()
