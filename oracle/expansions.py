@@ -20,6 +20,9 @@ Contents (each cites the passage it follows):
                        lelayerimage and lecoeffimage).
   reaction_m2l         the M2L operator T of a reaction component (Sec. 3.4, eqs. metoleimage1
                        and metoleimage2), by direct quadrature.
+  gaunt_all, free_shat, free_s, free_m2m, free_m2l, free_l2l
+                       the free-space translations of Sec. 3.1 (Thm. 2-3, eqs. metome, metole);
+                       the printed prefactor of Thm. 3 is off by -pi/2 (see free_s).
   legendre_product_coeffs, reaction_m2l_tables
                        the same operator by the table route of Sec. 3.5: products of two
                        Legendre functions as polynomials in lambda_rho (exact rational
@@ -422,3 +425,109 @@ def phat_ratio_t_coeffs(n, m):
     i, e = _phat_t_poly(n, m)
     scale = _norm(n, m) / (_norm(m, m) * math.factorial(2 * m) / (2 ** m * math.factorial(m)))
     return i, [float(ek) * scale for ek in e]
+
+
+# ------------------------------------------------------------------------------------------
+# Free-space translations (Sec. 3.1, Thm. 2-3, eqs. metole and metome)
+
+@functools.lru_cache(maxsize=None)
+def gaunt_all(p):
+    """G[f(n,m), f(nu,mu), q] = int Y_n^m Y_nu^mu conj(Y_q^{m+mu}) over the unit sphere for
+    n, nu <= p and q <= 2p (f(n, m) = n^2 + n + m), by a product rule exact for these
+    band-limited integrands: Gauss-Legendre in cos(theta) (2p + 2 nodes, degree <= 4p) times
+    the trapezoid rule in phi (4p + 2 points, frequencies |k| <= 4p).  This is the Gaunt
+    coefficient G(n, m; nu, mu; q) of Thm. 2-3 under the reading of it that makes Thm. 2 hold."""
+    nt, nph = 2 * p + 2, 4 * p + 2
+    x, w = np.polynomial.legendre.leggauss(nt)
+    th = np.arccos(x)
+    ph = 2 * math.pi * np.arange(nph) / nph
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    W = (w[:, None] * np.full(nph, 2 * math.pi / nph)[None, :]).ravel()
+    Y = {(n, m): ylm(n, m, TH, PH).ravel() for n in range(2 * p + 1) for m in range(-n, n + 1)}
+    NF = (p + 1) ** 2
+    G = np.zeros((NF, NF, 2 * p + 1))
+    for n, m in _nm(p):
+        for nu, mu in _nm(p):
+            a = W * Y[(n, m)] * Y[(nu, mu)]
+            for q in range(abs(n - nu), n + nu + 1):
+                if abs(m + mu) <= q and (n + nu + q) % 2 == 0:
+                    G[n * n + n + m, nu * nu + nu + mu, q] = (a * np.conj(Y[(q, m + mu)])).sum().real
+    return G
+
+
+def _gf(G, n, m, nu, mu, q):
+    return G[n * n + n + m, nu * nu + nu + mu, q]
+
+
+def _radial_angular(lam, b, qmax, kind):
+    """i_q or k_q of lam |b| and conj Y_q^k(b) for q <= qmax, |k| <= q."""
+    Bn, TB, PB = sph(b)
+    f = special.spherical_in if kind == "i" else special.spherical_kn
+    rad = [f(q, lam * Bn) for q in range(qmax + 1)]
+    ang = {(q, k): np.conj(ylm(q, k, TB, PB)) for q in range(qmax + 1) for k in range(-q, q + 1)}
+    return rad, ang
+
+
+def free_shat(lam, b, p, P):
+    """Shat_{n nu}^{m mu}(b) of Thm. 2 (eq. spmhat3d), n <= p, nu <= P, as a complex matrix
+    [(n, m), (nu, mu)]: i_n Y_n^m(r1 + b) = sum Shat i_nu Y_nu^mu(r1)."""
+    G = gaunt_all(max(p, P))
+    rad, ang = _radial_angular(lam, b, p + P, "i")
+    out = np.zeros(((p + 1) ** 2, (P + 1) ** 2), complex)
+    for x, (n, m) in enumerate(_nm(p)):
+        for y, (nu, mu) in enumerate(_nm(P)):
+            s = 0j
+            for q in range(abs(n - nu), n + nu + 1):
+                if abs(mu - m) <= q:
+                    s += (-1.0) ** (nu - n + m + q) * rad[q] * ang[(q, mu - m)] * _gf(G, n, m, nu, -mu, q)
+            out[x, y] = 4 * math.pi * s
+    return out
+
+
+def free_s(lam, b, p, P, printed_prefactor=False):
+    """S_{n nu}^{m mu}(b) of Thm. 3 (eq. singularseparation), n <= p, nu <= P:
+    k_n Y_n^m(r1 + b) = sum S i_nu Y_nu^mu(r1) for |r1| < |b|.  The printed prefactor
+    2 pi^2 (-1)^{m+nu+1} is off by the factor -pi/2 (with the Gaunt coefficient of Thm. 2 and
+    any normalization of k, which appears on both sides); the identity holds with
+    4 pi (-1)^{m+nu}.  printed_prefactor=True uses the printed constant."""
+    G = gaunt_all(max(p, P))
+    rad, ang = _radial_angular(lam, b, p + P, "k")
+    out = np.zeros(((p + 1) ** 2, (P + 1) ** 2), complex)
+    for x, (n, m) in enumerate(_nm(p)):
+        for y, (nu, mu) in enumerate(_nm(P)):
+            s = 0j
+            for q in range(abs(n - nu), n + nu + 1):
+                if abs(mu - m) <= q:
+                    s += rad[q] * ang[(q, mu - m)] * _gf(G, n, m, nu, -mu, q)
+            pref = 2 * math.pi ** 2 * (-1.0) ** (m + nu + 1) if printed_prefactor else 4 * math.pi * (-1.0) ** (m + nu)
+            out[x, y] = pref * s
+    return out
+
+
+def free_me_coeffs(lam, rsrc, rc, p):
+    """M_nm = 4 pi i_n(lam r's) conj Y_n^m(theta's, phi's) of one unit source (eq. melecoeffree)."""
+    R, T, P = sph(np.asarray(rsrc, float) - rc)
+    return np.array([4 * math.pi * special.spherical_in(n, lam * R) * np.conj(ylm(n, m, T, P)) for n, m in _nm(p)])
+
+
+def free_me_eval(lam, M, rc, r, p):
+    """sum M_nm k_n(lam r_s) Y_n^m(theta_s, phi_s) about rc (eq. freespace3dmulexp)."""
+    R, T, P = sph(np.asarray(r, float) - rc)
+    return sum(Mnm * special.spherical_kn(n, lam * R) * ylm(n, m, T, P) for (n, m), Mnm in zip(_nm(p), M)).real
+
+
+def free_m2l(lam, M, rcs, rct, p, P):
+    """LE coefficients about rct (degree <= P) of the ME M (degree <= p) about rcs (eq. metole,
+    with Thm. 3 applied to each k_n Y_n^m of the ME): L_{nu mu} = sum_{nm} M_nm S_{n nu}^{m mu}(b),
+    b = rct - rcs."""
+    return free_s(lam, np.asarray(rct, float) - rcs, p, P).T @ M
+
+
+def free_m2m(lam, M, rcs, rcs_new, p):
+    """ME about rcs shifted to rcs_new (eq. metome): M~_nm = sum conj(Shat_{n nu}^{m mu}(rcs - rcs_new)) M_{nu mu}."""
+    return np.conj(free_shat(lam, np.asarray(rcs, float) - rcs_new, p, p)) @ M
+
+
+def free_l2l(lam, L, rct, rct_new, p):
+    """LE about rct shifted to rct_new (eq. metome): L~_nm = sum Shat_{nu n}^{mu m}(rct_new - rct) L_{nu mu}."""
+    return free_shat(lam, np.asarray(rct_new, float) - rct, p, p).T @ L

@@ -18,6 +18,8 @@ import pytest
 
 pytest.importorskip("scipy")
 
+from scipy import special  # noqa: E402
+
 import oracle  # noqa: E402
 from oracle import expansions as E  # noqa: E402
 
@@ -40,7 +42,6 @@ def image(md, l, a, lp, b, rp):
 
 def test_spherical_harmonics_match_scipy():
     """Y_n^m of Sec. 3.1 (with its (-1)^m in front) equals scipy's Condon-Shortley harmonics."""
-    special = pytest.importorskip("scipy.special")
     if not hasattr(special, "sph_harm_y"):
         pytest.skip("scipy without sph_harm_y")
     rng = np.random.default_rng(3)
@@ -241,3 +242,79 @@ def test_m2l_operator_is_real_at_zero_azimuth(ab):
     ti, si = E._nm(4), E._nm(4)
     ph = np.exp(1j * 0.7 * np.array([[mu - m for _, mu in si] for _, m in ti]))
     assert np.abs(T2 - ph * T).max() <= 1e-12 * np.abs(T).max()
+
+
+# ---- free-space translations (Sec. 3.1, Thm. 2-3, eqs. metole and metome) ----------------
+
+FREE_LAM = 0.8
+R1 = np.array([0.12, -0.05, 0.09])
+BVEC = np.array([0.7, 0.4, -0.9])
+
+
+def test_gaunt_coefficients_match_sympy():
+    wigner = pytest.importorskip("sympy.physics.wigner")
+    G = E.gaunt_all(6)
+    for (n, m, nu, mu, q) in [(2, 1, 3, -2, 3), (4, -3, 2, 2, 4), (6, 0, 6, 5, 8), (5, 5, 6, -6, 1), (3, 0, 3, 0, 6)]:
+        # int Y_n^m Y_nu^mu conj(Y_q^{m+mu}) = (-1)^{m+mu} int Y_n^m Y_nu^mu Y_q^{-m-mu}
+        ex = (-1) ** (m + mu) * float(wigner.gaunt(n, nu, q, m, mu, -m - mu))
+        assert abs(G[n * n + n + m, nu * nu + nu + mu, q] - ex) < 1e-14
+
+
+def _basis(P, lam, r):
+    R, T, Ph = E.sph(r)
+    return np.array([special.spherical_in(nu, lam * R) * E.ylm(nu, mu, T, Ph) for nu, mu in E._nm(P)])
+
+
+def test_thm2_regular_translation_is_exact():
+    """Thm. 2 (eq. spmhat3d) as printed: i_n Y_n^m(r1 + b) = sum Shat i_nu Y_nu^mu(r1); the
+    series in nu is finite (nu <= n + q ranges are cut by the Gaunt selection rules)."""
+    Sh = E.free_shat(FREE_LAM, BVEC, 4, 12)
+    R2, T2, P2 = E.sph(R1 + BVEC)
+    bas = _basis(12, FREE_LAM, R1)
+    for x, (n, m) in enumerate(E._nm(4)):
+        ex = special.spherical_in(n, FREE_LAM * R2) * E.ylm(n, m, T2, P2)
+        assert abs(Sh[x] @ bas - ex) <= 1e-13 * abs(ex)
+
+
+def test_thm3_singular_translation_and_its_printed_prefactor():
+    """Thm. 3 (eq. singularseparation): k_n Y_n^m(r1 + b) = sum S i_nu Y_nu^mu(r1) for |r1| < |b|,
+    converging in nu.  The identity holds with the prefactor 4 pi (-1)^{m+nu}; the printed
+    2 pi^2 (-1)^{m+nu+1} gives the series times -pi/2 (a misprint: k appears on both sides, so no
+    normalization of k can account for it)."""
+    R2, T2, P2 = E.sph(R1 + BVEC)
+    errs = []
+    for P in (6, 12):
+        S = E.free_s(FREE_LAM, BVEC, 3, P)
+        bas = _basis(P, FREE_LAM, R1)
+        err = 0.0
+        for x, (n, m) in enumerate(E._nm(3)):
+            ex = special.spherical_kn(n, FREE_LAM * R2) * E.ylm(n, m, T2, P2)
+            err = max(err, abs(S[x] @ bas - ex) / abs(ex))
+        errs.append(err)
+    assert errs[1] < 1e-9 and errs[0] > 100 * errs[1], errs
+    Sp = E.free_s(FREE_LAM, BVEC, 3, 12, printed_prefactor=True)
+    bas = _basis(12, FREE_LAM, R1)
+    ratio = (Sp[5] @ bas) / (E.free_s(FREE_LAM, BVEC, 3, 12)[5] @ bas)
+    assert abs(ratio - (-math.pi / 2)) < 1e-12
+
+
+def test_free_m2m_m2l_l2l_reproduce_the_kernel():
+    """ME about a source centre, shifted (M2M, eq. metome), translated (M2L, eq. metole with the
+    Thm. 3 operator), shifted again (L2L, eq. metome) and evaluated (eq. freespace3dlocexp):
+    converges to k_0(lam |r - r'|) as p grows."""
+    rs = np.array([0.05, 0.02, -0.04])
+    rcs, rcs2 = np.zeros(3), np.array([0.1, -0.1, 0.1])
+    rct = np.array([0.9, -0.3, 0.5])
+    rct2 = rct + np.array([0.03, 0.0, -0.02])
+    r = rct + np.array([0.06, 0.05, -0.07])
+    ex = E.k0(FREE_LAM, np.linalg.norm(r - rs))
+    errs = []
+    for p in (4, 8):
+        M = E.free_me_coeffs(FREE_LAM, rs, rcs, p)
+        M2 = E.free_m2m(FREE_LAM, M, rcs, rcs2, p)
+        L = E.free_m2l(FREE_LAM, M2, rcs2, rct, p, p)
+        L2 = E.free_l2l(FREE_LAM, L, rct, rct2, p)
+        errs.append(abs(E.le_eval(FREE_LAM, L2, rct2, r, p)[-1] - ex) / ex)
+        # M2M alone keeps the potential (within the shifted ME's truncation)
+        assert abs(E.free_me_eval(FREE_LAM, M2, rcs2, r, p) - ex) / ex < 10 * 0.2 ** (p + 1)
+    assert errs[1] < 1e-8 and errs[0] > 100 * errs[1], errs
