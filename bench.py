@@ -79,6 +79,32 @@ def per_layer_errors(a, ref, layer, nlayers):
     return out
 
 
+def load_oracle_fixture(n, seed, path=None):
+    """The oracle's stored potential and field at sampled targets of this workload (a committed
+    fixture written from the oracle alone), or None when none is stored for (n, seed)."""
+    path = path or os.path.join(ROOT, "tests", "golden", "three_layer_1M_oracle.json")
+    try:
+        with open(path) as f:
+            fx = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return fx if fx.get("n") == n and fx.get("seed") == seed else None
+
+
+def oracle_fixture_errors(sampled, fx):
+    """Relative L2 errors against the oracle at the fixture's targets; sampled maps a name to
+    (phi, field) host arrays at those targets, in the fixture's order."""
+    ref_phi = np.asarray(fx["phi"], float)
+    ref_fld = np.asarray(fx["field"], float)
+    out = {"targets": len(fx["targets"]),
+           "sample": "%d targets per layer, drawn without replacement (seed %d); oracle direct sum, FP64"
+                     % (fx["per_layer"], fx["seed"])}
+    for name, (ph, fl) in sampled.items():
+        out[name] = {"relL2_phi": float(np.linalg.norm(np.asarray(ph) - ref_phi) / np.linalg.norm(ref_phi)),
+                     "relL2_field": float(np.linalg.norm(np.asarray(fl) - ref_fld) / np.linalg.norm(ref_fld))}
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +327,20 @@ def run_ours(args, rank, world, local_rank):
                     "per_layer_phi": per_layer_errors(phi, p64, l, len(m["eps"]))}
         ctx64.close()
 
+    # both FMMs against the oracle's stored values at sampled targets (no oracle run here)
+    vs_oracle = None
+    if rank == 0:
+        try:
+            fx = load_oracle_fixture(n, rank_seed(rank))
+            if fx is not None:
+                idx = torch.tensor(fx["targets"], dtype=torch.int64, device=dev)
+                sampled = {"mixed": (phi[idx].cpu().numpy(), fld[idx].cpu().numpy())}
+                if accuracy is not None:
+                    sampled["fp64"] = (p64[idx].cpu().numpy(), f64[idx].cpu().numpy())
+                vs_oracle = oracle_fixture_errors(sampled, fx)
+        except Exception as e:  # a report only: never lose the measurement line over it
+            vs_oracle = {"error": repr(e)}
+
     device_status = ctx.status()  # 0 unless a bounded device wait ran out during the run
 
     # rooflines of the heaviest kernels, from their CUDA-event intervals (per evaluation)
@@ -356,7 +396,8 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": launches_per_step * args.steps, "roofline": roof_main, "rooflines": roofs,
                 "phases_ms_per_eval": {k: v / args.steps for k, v in phase_ms.items()}, "device_status": device_status,
                 "cpu_baseline": cpu,
-                "fp64_fmm_value": fp64_value, "accuracy": accuracy, "counts": counts}
+                "fp64_fmm_value": fp64_value, "accuracy": accuracy, "accuracy_vs_oracle": vs_oracle,
+                "counts": counts}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -64,3 +64,30 @@ def test_paper_irregular_oracle_fixture_matches_the_oracle():
     phi, fld = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=tg)
     assert np.allclose(phi, [g["phi"][k] for k in pick], rtol=1e-12, atol=0)
     assert np.allclose(fld, [g["field"][k] for k in pick], rtol=1e-12, atol=1e-15)
+
+
+def test_benchmark_oracle_fixture_matches_the_oracle_and_the_bench_workload():
+    """tests/golden/three_layer_1M_oracle.json (make_three_layer_1M_oracle.py, oracle only) is the
+    sample the benchmark compares its FMM results with: same workload as the benchmark's rank 0,
+    the stated target draw, and one stored target recomputed by the oracle."""
+    import importlib.util
+    import os
+
+    import bench
+    import oracle
+
+    here = os.path.dirname(__file__)
+    spec = importlib.util.spec_from_file_location("mk1m", os.path.join(here, "golden", "make_three_layer_1M_oracle.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    fx = bench.load_oracle_fixture(1000000, bench.rank_seed(0))
+    assert fx is not None and fx["seed"] == mk.SEED and bench.load_oracle_fixture(999, mk.SEED) is None
+    w = inputs.workload("three_layer", n=1000000, seed=bench.rank_seed(0))
+    assert fx["targets"] == mk.sample_targets(w["layer"], fx["per_layer"], fx["seed"])
+    assert len(fx["targets"]) == 24 and len(set(fx["targets"])) == 24
+    oracle.build()
+    md = oracle.Medium(**w["medium"])
+    k = 9  # one stored target, recomputed (about 40 s of one core)
+    phi, fld = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=np.array([fx["targets"][k]]))
+    assert abs(phi[0] - fx["phi"][k]) <= 1e-12 * abs(phi[0])
+    assert np.allclose(fld[0], fx["field"][k], rtol=1e-12, atol=1e-14)

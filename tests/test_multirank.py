@@ -76,3 +76,11 @@ def test_per_layer_errors_match_their_definition():
     assert e[0]["errmax"] == pytest.approx(0.1 / 2.0)
     assert e[1]["err2"] == pytest.approx(np.sqrt(0.04 + 0.0025) / np.sqrt(16.25))
     assert e[2]["err2"] == 0.0 and e[3] is None
+
+
+def test_oracle_fixture_errors_match_their_definition():
+    fx = {"targets": [3, 9], "per_layer": 1, "seed": 5, "phi": [1.0, -2.0], "field": [[1, 0, 0], [0, 2, 0]]}
+    got = bench.oracle_fixture_errors({"x": (np.array([1.1, -2.0]), np.array([[1, 0, 0], [0, 2, 0.2]]))}, fx)
+    assert got["targets"] == 2
+    assert abs(got["x"]["relL2_phi"] - 0.1 / np.sqrt(5.0)) < 1e-15
+    assert abs(got["x"]["relL2_field"] - 0.2 / np.sqrt(5.0)) < 1e-15
