@@ -5,9 +5,11 @@ Wang, Zhang & Cai, arXiv 2002.01334.  Only tests/, ``__graft_entry__.smoke()`` a
 CPU-baseline leg of ``bench.py`` may import this package; the product path never does.
 
 Parity status of each function is stated in tests/test_oracle_pins.py, which pins it
-against closed forms, the paper's printed formulas, invariants and brute force.  The
-submodule ``expansions`` restates the truncated expansions of Sec. 3 (numpy/scipy);
-tests/test_expansion_pins.py checks that they converge in p to this package's direct values.
+against closed forms, the paper's printed formulas, invariants and brute force.  Submodules:
+``expansions`` restates the truncated expansions and translations of Sec. 3 (numpy/scipy;
+tests/test_expansion_pins.py checks that they converge in p to this package's direct values),
+``adaptive`` the adaptive dual trees and their lists (tests/test_adaptive_tree.py), and ``fmm``
+a plain CPU free-space FMM built from them (tests/test_cpu_fmm.py).
 """
 import ctypes as C
 import os

@@ -80,7 +80,7 @@ def phat(n, m, x):
     am = abs(m)
     if am > n:
         return np.zeros(x.shape, complex)
-    der = npleg.legval(x, npleg.legder(np.eye(n + 1)[n], am)) if am > 0 else npleg.legval(x, np.eye(n + 1)[n])
+    der = npleg.legval(x, _legder(n, am))
     ax = np.abs(x)
     s = np.where(ax <= 1.0, np.sqrt(np.clip(1.0 - x * x, 0.0, None)) + 0j,
                  np.where(x > 0, -1j, 1j) * np.sqrt(np.clip(x * x - 1.0, 0.0, None)))
@@ -93,13 +93,20 @@ def _nm(p):
 
 
 @functools.lru_cache(maxsize=None)
+def _legder(n, am):
+    """Legendre-basis coefficients of d^am/dx^am P_n."""
+    c = np.eye(n + 1)[n]
+    return npleg.legder(c, am) if am > 0 else c
+
+
+@functools.lru_cache(maxsize=None)
 def _phat_table(p):
     """Per (n, m) of _nm(p): Legendre-basis coefficients of d^{|m|}/dx^{|m|} P_n, |m|, and the
     constant factor of phat (normalization and signs)."""
     idx = _nm(p)
     D = np.zeros((p + 1, len(idx)))
     for j, (n, m) in enumerate(idx):
-        c = npleg.legder(np.eye(n + 1)[n], abs(m)) if m else np.eye(n + 1)[n]
+        c = _legder(n, abs(m))
         D[:len(c), j] = c
     am = np.array([abs(m) for _, m in idx])
     fac = np.array([(-1.0) ** abs(m) * _norm(n, abs(m)) * ((-1.0) ** abs(m) if m < 0 else 1.0) for n, m in idx])
@@ -115,6 +122,19 @@ def phat_all(p, x):
     else:
         s = (-1j if x > 0 else 1j) * math.sqrt(x * x - 1.0)
     return fac * s ** am * npleg.legval(x, D)
+
+
+def ylm_all(p, theta, phi):
+    """Y_n^m(theta, phi) for every (n, m) of _nm(p) at arrays of angles: rows in _nm(p) order
+    (the same definition as ylm, all orders at once; |cos theta| <= 1)."""
+    D, am, fac = _phat_table(p)
+    x = np.cos(np.asarray(theta, float))
+    s = np.sqrt(np.clip(1.0 - x * x, 0.0, None))
+    ms = np.array([m for _, m in _nm(p)])
+    leg = npleg.legval(x, D)  # [K, ...]
+    sh = (-1,) + (1,) * x.ndim
+    return (fac.reshape(sh) * s[None] ** am.reshape(sh) * leg
+            * np.exp(1j * ms.reshape(sh) * np.asarray(phi, float)[None]))
 
 
 def ylm(n, m, theta, phi):
@@ -459,49 +479,53 @@ def _gf(G, n, m, nu, mu, q):
     return G[n * n + n + m, nu * nu + nu + mu, q]
 
 
-def _radial_angular(lam, b, qmax, kind):
-    """i_q or k_q of lam |b| and conj Y_q^k(b) for q <= qmax, |k| <= q."""
+def _translation(lam, b, p, P, kind):
+    """sum_q c_q f_q(lam |b|) conj Y_q^{mu-m}(b) G(n, m; nu, -mu; q) for all (n, m) <= p,
+    (nu, mu) <= P, with f = i (kind "i", Thm. 2 with its sign (-1)^{nu-n+m+q} in c_q) or k
+    (kind "k", Thm. 3, c_q = 1).  Vectorized over the entries; conj Y_q^k is taken as 0 for
+    |k| > q, where the Gaunt coefficient vanishes."""
     Bn, TB, PB = sph(b)
+    G = gaunt_all(max(p, P))
     f = special.spherical_in if kind == "i" else special.spherical_kn
-    rad = [f(q, lam * Bn) for q in range(qmax + 1)]
-    ang = {(q, k): np.conj(ylm(q, k, TB, PB)) for q in range(qmax + 1) for k in range(-q, q + 1)}
-    return rad, ang
+    qmax = p + P
+    ti, si = _nm(p), _nm(P)
+    n = np.array([a for a, _ in ti])[:, None]
+    m = np.array([c for _, c in ti])[:, None]
+    nu = np.array([a for a, _ in si])[None, :]
+    mu = np.array([c for _, c in si])[None, :]
+    fo = (n * n + n + m) * np.ones_like(nu)
+    fi = (nu * nu + nu - mu) * np.ones_like(n)
+    k = mu - m
+    yb = phat_all(qmax, math.cos(TB)) * np.exp(1j * np.array([kk for _, kk in _nm(qmax)]) * PB)
+    out = np.zeros((len(ti), len(si)), complex)
+    for q in range(qmax + 1):
+        ok = np.abs(k) <= q
+        ang = np.where(ok, np.conj(yb[q * q + q + np.clip(k, -q, q)]), 0.0)
+        g = G[fo, fi, q] if q < G.shape[2] else np.zeros(k.shape)
+        c = (-1.0) ** (nu - n + m + q) if kind == "i" else 1.0
+        out += c * f(q, lam * Bn) * ang * g
+    return out
 
 
 def free_shat(lam, b, p, P):
     """Shat_{n nu}^{m mu}(b) of Thm. 2 (eq. spmhat3d), n <= p, nu <= P, as a complex matrix
-    [(n, m), (nu, mu)]: i_n Y_n^m(r1 + b) = sum Shat i_nu Y_nu^mu(r1)."""
-    G = gaunt_all(max(p, P))
-    rad, ang = _radial_angular(lam, b, p + P, "i")
-    out = np.zeros(((p + 1) ** 2, (P + 1) ** 2), complex)
-    for x, (n, m) in enumerate(_nm(p)):
-        for y, (nu, mu) in enumerate(_nm(P)):
-            s = 0j
-            for q in range(abs(n - nu), n + nu + 1):
-                if abs(mu - m) <= q:
-                    s += (-1.0) ** (nu - n + m + q) * rad[q] * ang[(q, mu - m)] * _gf(G, n, m, nu, -mu, q)
-            out[x, y] = 4 * math.pi * s
-    return out
+    [(n, m), (nu, mu)]: i_n Y_n^m(r1 + b) = sum Shat i_nu Y_nu^mu(r1).  Entry by entry,
+    4 pi sum_q (-1)^{nu-n+m+q} i_q(lam b) conj Y_q^{mu-m}(b) G(n, m; nu, -mu; q)."""
+    return 4 * math.pi * _translation(lam, b, p, P, "i")
 
 
 def free_s(lam, b, p, P, printed_prefactor=False):
     """S_{n nu}^{m mu}(b) of Thm. 3 (eq. singularseparation), n <= p, nu <= P:
-    k_n Y_n^m(r1 + b) = sum S i_nu Y_nu^mu(r1) for |r1| < |b|.  The printed prefactor
-    2 pi^2 (-1)^{m+nu+1} is off by the factor -pi/2 (with the Gaunt coefficient of Thm. 2 and
-    any normalization of k, which appears on both sides); the identity holds with
-    4 pi (-1)^{m+nu}.  printed_prefactor=True uses the printed constant."""
-    G = gaunt_all(max(p, P))
-    rad, ang = _radial_angular(lam, b, p + P, "k")
-    out = np.zeros(((p + 1) ** 2, (P + 1) ** 2), complex)
-    for x, (n, m) in enumerate(_nm(p)):
-        for y, (nu, mu) in enumerate(_nm(P)):
-            s = 0j
-            for q in range(abs(n - nu), n + nu + 1):
-                if abs(mu - m) <= q:
-                    s += rad[q] * ang[(q, mu - m)] * _gf(G, n, m, nu, -mu, q)
-            pref = 2 * math.pi ** 2 * (-1.0) ** (m + nu + 1) if printed_prefactor else 4 * math.pi * (-1.0) ** (m + nu)
-            out[x, y] = pref * s
-    return out
+    k_n Y_n^m(r1 + b) = sum S i_nu Y_nu^mu(r1) for |r1| < |b|.  Entry by entry,
+    4 pi (-1)^{m+nu} sum_q k_q(lam b) conj Y_q^{mu-m}(b) G(n, m; nu, -mu; q).  The printed
+    prefactor 2 pi^2 (-1)^{m+nu+1} is off by the factor -pi/2 (with the Gaunt coefficient of
+    Thm. 2 and any normalization of k, which appears on both sides); printed_prefactor=True
+    uses the printed constant."""
+    ti, si = _nm(p), _nm(P)
+    m = np.array([c for _, c in ti])[:, None]
+    nu = np.array([a for a, _ in si])[None, :]
+    pref = 2 * math.pi ** 2 * (-1.0) ** (m + nu + 1) if printed_prefactor else 4 * math.pi * (-1.0) ** (m + nu)
+    return pref * _translation(lam, b, p, P, "k")
 
 
 def free_me_coeffs(lam, rsrc, rc, p):
