@@ -26,6 +26,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "targets/sec (potential+field) N=1M 3-layer @relL2<=1e-6: mixed vs FP64 FMM"
+# the paper's own workload (Sec. 4: charges in three irregular bodies, eps = (1, 8.6, 20.5),
+# lambda = (1.2, 0.5, 2.1)), for context beside its CPU timings; not the headline metric
+METRIC_PAPER = "targets/sec (potential+field) paper irregular-body 3-layer workload: mixed FMM"
+
+
+def metric_of(workload):
+    return METRIC if workload == "three_layer" else METRIC_PAPER
 N_DEFAULT = 1000000
 P_DEFAULT = 10
 
@@ -79,16 +86,17 @@ def per_layer_errors(a, ref, layer, nlayers):
     return out
 
 
-def load_oracle_fixture(n, seed, path=None):
+def load_oracle_fixture(n, seed, workload="three_layer", path=None):
     """The oracle's stored potential and field at sampled targets of this workload (a committed
-    fixture written from the oracle alone), or None when none is stored for (n, seed)."""
+    fixture written from the oracle alone), or None when none is stored for (workload, n, seed)."""
     path = path or os.path.join(ROOT, "tests", "golden", "three_layer_1M_oracle.json")
     try:
         with open(path) as f:
             fx = json.load(f)
     except (OSError, ValueError):
         return None
-    return fx if fx.get("n") == n and fx.get("seed") == seed else None
+    ok = fx.get("workload") == workload and fx.get("n") == n and fx.get("seed") == seed
+    return fx if ok else None
 
 
 def oracle_fixture_errors(sampled, fx):
@@ -111,6 +119,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="three_layer", choices=["three_layer", "paper_irregular"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--p", type=int, default=P_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -118,7 +127,15 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(n, p, precision):
+def workload_config(n, p, precision, workload="three_layer"):
+    if workload == "paper_irregular":
+        return {"workload": "paper irregular-body three-layer screened Coulomb (Sec. 4), N=%d, p=%d" % (n, p),
+                "n": n, "p": p, "layers": 3, "interfaces": [0.0, -1.2], "eps": [1.0, 8.6, 20.5],
+                "lambda": [1.2, 0.5, 2.1],
+                "charges": "q~U[-1,1], uniform in the bodies r(theta) = 0.5 - a + (a/8)(35 cos^4 - 30 cos^2 + 3), "
+                           "a = 0.1, 0.15, 0.05, centres z = 0.6, -0.6, -1.8, counts in the ratio 912:640:1296",
+                "precision": precision, "l2": "flushed between steps (256 MB write)",
+                "tree": "automatic depth, <=128 mean targets per leaf"}
     return {"workload": "three-layer screened Coulomb, N=%d, p=%d" % (n, p), "n": n, "p": p, "layers": 3,
             "interfaces": [0.0, -1.2], "eps": [1.0, 2.0, 5.0], "lambda": [0.5, 1.0, 0.8],
             "charges": "q~U[-1,1], uniform in three unit cubes (one per layer)", "precision": precision,
@@ -208,7 +225,7 @@ def run_reference(args, rank, world):
     from paper_2002_01334_gb300 import inputs
     import oracle
     oracle.build()
-    w = inputs.workload("three_layer", n=args.n)
+    w = inputs.workload(args.workload, n=args.n)
     cores = oracle.num_threads()
     nt, stride = max(2, cores), 20
     for _ in range(args.warmup):
@@ -220,10 +237,10 @@ def run_reference(args, rank, world):
         times.append(dt)
     value = args.steps * nt * (args.n // stride) / args.n / sum(times)
     info["value"] = value
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_of(args.workload), "value": value, "unit": "targets/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args.n, args.p, "fp64 direct sum (CPU oracle)"),
+            "config": dict(workload_config(args.n, args.p, "fp64 direct sum (CPU oracle)", args.workload),
                            l2="not applicable (host cores)"), "cpu_baseline": info,
             "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -243,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = inputs.workload("three_layer", n=args.n, seed=rank_seed(rank))
+    w = inputs.workload(args.workload, n=args.n, seed=rank_seed(rank))
     m = w["medium"]
     q = torch.tensor(w["q"], device=dev)
     x = torch.tensor(w["xyz"], device=dev)
@@ -331,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
     vs_oracle = None
     if rank == 0:
         try:
-            fx = load_oracle_fixture(n, rank_seed(rank))
+            fx = load_oracle_fixture(n, rank_seed(rank), args.workload)
             if fx is not None:
                 idx = torch.tensor(fx["targets"], dtype=torch.int64, device=dev)
                 sampled = {"mixed": (phi[idx].cpu().numpy(), fld[idx].cpu().numpy())}
@@ -387,10 +404,10 @@ def run_ours(args, rank, world, local_rank):
         cpu = info
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
+        line = {"metric": metric_of(args.workload), "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": workload_config(n, args.p, "mixed"), "clocks": clk.summary(),
+                "config": workload_config(n, args.p, "mixed", args.workload), "clocks": clk.summary(),
                 "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
                         "d2h_bytes_per_step": n * (8 + 24)},
                 "gpu_launches": launches_per_step * args.steps, "roofline": roof_main, "rooflines": roofs,

@@ -84,3 +84,15 @@ def test_oracle_fixture_errors_match_their_definition():
     assert got["targets"] == 2
     assert abs(got["x"]["relL2_phi"] - 0.1 / np.sqrt(5.0)) < 1e-15
     assert abs(got["x"]["relL2_field"] - 0.2 / np.sqrt(5.0)) < 1e-15
+
+
+def test_paper_workload_option_names_its_own_metric_and_config():
+    assert bench.metric_of("three_layer") == bench.METRIC
+    assert bench.metric_of("paper_irregular") != bench.METRIC
+    c = bench.workload_config(2861288, 5, "mixed", "paper_irregular")
+    assert c["eps"] == [1.0, 8.6, 20.5] and c["lambda"] == [1.2, 0.5, 2.1] and c["p"] == 5
+    assert bench.workload_config(1000000, 10, "mixed")["eps"] == [1.0, 2.0, 5.0]
+    # the stored oracle sample belongs to the three-layer workload only
+    seed = bench.rank_seed(0)
+    assert bench.load_oracle_fixture(1000000, seed) is not None
+    assert bench.load_oracle_fixture(1000000, seed, "paper_irregular") is None
