@@ -1,6 +1,6 @@
-"""A plain CPU FMM for the free-space part -- TEST INFRASTRUCTURE ONLY.
+"""A plain CPU FMM, free-space and reaction parts -- TEST INFRASTRUCTURE ONLY.
 
-The free-space Yukawa FMM of every layer (Sec. 3.1; Algorithm 2, first loop) on the uniform tree
+free_fmm: the free-space Yukawa FMM of every layer (Sec. 3.1; Algorithm 2, first loop) on the uniform tree
 of the layer's target group, written step by step from the paper's expansions and translations
 (oracle/expansions.py, each pinned against the closed-form kernel):
 
@@ -13,7 +13,10 @@ of the layer's target group, written step by step from the paper's expansions an
   L2P    phi = c sum L_nm i_n(lam r) Y_n^m (eq. freespace3dlocexp) and the field from the LE
          shifted onto the target (its n <= 1 coefficients, exact);
   P2P    the near lists at level D, closed form, j != i;
-with c = lam / (2 pi^2 eps) (k_0(lam r) = (pi/2) e^{-lam r} / (lam r)).  Every expansion is
+with c = lam / (2 pi^2 eps) (k_0(lam r) = (pi/2) e^{-lam r} / (lam r)).
+react_fmm: Algorithm 1 for every reaction component on the same group trees (images as sources,
+one ME per source type, M2L by T of eqs. metoleimage1-2 on a shared quadrature node set per
+component and level, near field by the component integral).  Every expansion is
 truncated at degree p and nothing else is approximated, so its result is the FMM's own value at
 that order and tree; against the direct sum it differs by the truncation error only.  Slow:
 meant for a few thousand charges.  Only tests/ may import it; it shares no code with the CUDA
@@ -148,3 +151,249 @@ def free_fmm(md, q, xyz, layer, p, D):
                 phi[i] += e.sum()
                 field[i] += ((e * (1 + lam * r) / (r * r))[:, None] * d).sum(0)
     return phi, field
+
+
+# ------------------------------------------------------------------------------------------
+# Reaction components (Sec. 3.3-3.4, Algorithm 1 for every component, Algorithm 2)
+
+def _heights(md, l, a, z):
+    """The target's distance to the interface of its side: z - d_l (a = 1), d_{l-1} - z (a = 2)."""
+    return z - md.d[l] if a == 1 else md.d[l - 1] - z
+
+
+def _source_heights(md, lp, b, z):
+    """The source's distance in the exponent of eq. zexponential: z' - d_l' (b = 1), d_{l'-1} - z' (b = 2)."""
+    return z - md.d[lp] if b == 1 else md.d[lp - 1] - z
+
+
+class ComponentRule:
+    """Composite 16-point Gauss-Legendre rule in lambda_rho for one component u^{ab}_{l l'}, with
+    its layer densities at the nodes: panels of width min(2/dmin, pi/rhomax, (lmin + x)/2) up to
+    x = 60/dmin, for pairs whose exponent distances sum to at least dmin and whose horizontal
+    distances are at most rhomax (the integrand then decays below e^-60 of its size at 0)."""
+
+    def __init__(self, md, l, lp, a, b, dmin, rhomax):
+        from . import sigma
+        self.l, self.lp, self.a, self.b = l, lp, a, b
+        gx, gw = np.polynomial.legendre.leggauss(16)
+        lmin = min(md.lam[l], md.lam[lp])
+        wmax = 2.0 / dmin
+        if rhomax > 0:
+            wmax = min(wmax, math.pi / rhomax)
+        xs, ws, x = [], [], 0.0
+        X = 60.0 / dmin
+        while x < X:
+            dw = min(wmax, 0.5 * (lmin + x), X - x)
+            xs.append(x + 0.5 * dw * (gx + 1.0))
+            ws.append(0.5 * dw * gw)
+            x += dw
+        self.x = np.concatenate(xs)
+        self.w = np.concatenate(ws)
+        self.lz = np.sqrt(md.lam[l] ** 2 + self.x ** 2)
+        self.lzp = np.sqrt(md.lam[lp] ** 2 + self.x ** 2)
+        self.sig = np.array([sigma(md, v, l, lp, a, b) for v in self.x])
+
+    def sum_at(self, md, r, src, q):
+        """sum_j q_j u^{ab}_{l l'}(r, r'_j) and its -grad_r, r one target, src[j] source positions
+        (eq. generalcomponents after the alpha integral: (1/4 pi) int lr J0(lr rho) e^{-lz h -
+        lz' h'} sigma / lz d lr)."""
+        ht = _heights(md, self.l, self.a, r[2])
+        hs = _source_heights(md, self.lp, self.b, src[:, 2])
+        dx, dy = r[0] - src[:, 0], r[1] - src[:, 1]
+        rho = np.hypot(dx, dy)
+        X = self.x[:, None]
+        e = (self.w * self.x * self.sig / self.lz / (4 * math.pi))[:, None] * np.exp(
+            -self.lz[:, None] * ht - self.lzp[:, None] * hs[None, :])
+        j0 = special.j0(X * rho[None, :])
+        # J1(x rho) / rho, with its limit x / 2 at rho = 0
+        j1r = np.where(rho[None, :] > 0, special.j1(X * rho[None, :]) / np.where(rho > 0, rho, 1.0)[None, :], 0.5 * X)
+        phi = (e * j0).sum(0) @ q
+        fr = (e * X * j1r).sum(0)
+        fz = (e * j0 * self.lz[:, None]).sum(0) * (1.0 if self.a == 1 else -1.0)
+        return phi, np.array([(q * fr * dx).sum(), (q * fr * dy).sum(), (q * fz).sum()])
+
+
+class ReactionM2L:
+    """M2L operators T of one component u^{ab}_{l l'} at one tree level (eqs. metoleimage1,
+    metoleimage2), by a composite Gauss-Legendre rule in lambda_rho shared by the level's classes.
+    A class is the horizontal offset rho (along +x) and the heights zt, zs of the target and source
+    centres above/below the interface; another azimuth phi multiplies entry (nm, nu mu) by
+    e^{i (mu - m) phi}.  Rule: panels of width min(2/dmin, pi/rhomax, (lmin + x)/2) up to
+    x = (70 + 2p)/dmin, dmin the smallest zt + zs of the level, rhomax its largest rho."""
+
+    def __init__(self, md, l, lp, a, b, p, dmin, rhomax):
+        from . import sigma
+        self.md, self.l, self.lp, self.a, self.b, self.p = md, l, lp, a, b, p
+        gx, gw = np.polynomial.legendre.leggauss(16)
+        lam, lamp = md.lam[l], md.lam[lp]
+        wmax = 2.0 / dmin
+        if rhomax > 0:
+            wmax = min(wmax, math.pi / rhomax)
+        xs, ws, x = [], [], 0.0
+        X = (70.0 + 2 * p) / dmin
+        while x < X:
+            dw = min(wmax, 0.5 * (min(lam, lamp) + x), X - x)
+            xs.append(x + 0.5 * dw * (gx + 1.0))
+            ws.append(0.5 * dw * gw)
+            x += dw
+        self.x = np.concatenate(xs)
+        w = np.concatenate(ws)
+        self.lz = np.sqrt(lam ** 2 + self.x ** 2)
+        self.lzp = np.sqrt(lamp ** 2 + self.x ** 2)
+        sig = np.array([sigma(md, v, l, lp, a, b) for v in self.x])
+        self.base = w * self.x / self.lz * sig
+        self.pt = np.array([E.phat_all(p, v / lam) for v in self.lz])    # [nodes, K]
+        self.ps = np.array([E.phat_all(p, v / lamp) for v in self.lzp])
+        idx = E._nm(p)
+        self.k = np.array([[mu - m for _, mu in idx] for _, m in idx])
+        n_ = np.array([n for n, _ in idx])[:, None]
+        m_ = np.array([m for _, m in idx])[:, None]
+        nu_ = np.array([n for n, _ in idx])[None, :]
+        mu_ = np.array([m for _, m in idx])[None, :]
+        self.sgn = ((-1.0) ** n_ * np.ones_like(nu_)) if a == 1 else (-1.0) ** (m_ + nu_ + mu_)
+        self.cache = {}
+
+    def T(self, rho, zt, zs):
+        """The operator at azimuth 0 for horizontal offset rho and heights zt, zs (cached)."""
+        key = (round(rho, 12), round(zt, 12), round(zs, 12))
+        if key not in self.cache:
+            e = self.base * np.exp(-self.lz * zt - self.lzp * zs)
+            p = self.p
+            J = special.jv(np.arange(-2 * p, 2 * p + 1)[None, :], self.x[:, None] * rho)  # [nodes, 4p + 1]
+            idx = E._nm(p)
+            m_row = np.array([m for _, m in idx])
+            mu_col = np.array([m for _, m in idx])
+            T = np.zeros(self.k.shape, complex)
+            for mv in range(-p, p + 1):
+                rows = m_row == mv
+                # entry (nm, nu mu) integrates e pt ps J_{mu - m}: one product per target order m
+                T[rows] = (self.pt[:, rows] * e[:, None]).T @ (self.ps * J[:, mu_col - mv + 2 * p])
+            self.cache[key] = self.sgn * (1j) ** self.k * T
+        return self.cache[key]
+
+    def apply(self, rct, rcs, M):
+        """L += T(rct, rcs) M for the target centre rct and polarization centre rcs."""
+        d = rct - rcs
+        rho, ph = math.hypot(d[0], d[1]), math.atan2(d[1], d[0])
+        dI = self.md.d[self.l] if self.a == 1 else self.md.d[self.l - 1]
+        zt, zs = (rct[2] - dI, dI - rcs[2]) if self.a == 1 else (dI - rct[2], rcs[2] - dI)
+        return (np.exp(1j * self.k * ph) * self.T(rho, zt, zs)) @ M
+
+
+def react_fmm(md, q, xyz, layer, p, D):
+    """Reaction part of phi and field of every charge: Algorithm 1 for every component, on the
+    uniform trees (depth D) of each target group (l, a).  Targets are the layer's charges; sources
+    are the polarization images (eq. eqpolarizedsource) of every charge, one ME per source type
+    (l', b) about each image box centre (eq. melayerupgoingimage, with lam_l'), shifted upward with
+    lam_l' (eq. metome), translated by T (eqs. metoleimage1-2) over the far lists at levels 2..D,
+    shifted down and evaluated with lam_l (eqs. metome, lelayerimage); the near lists at level D
+    are summed directly by the component integral (eq. generalcomponents), the charge's own image
+    included.  Returns (phi[n], field[n, 3])."""
+    from . import image_z
+    q = np.asarray(q, float)
+    xyz = np.asarray(xyz, float).reshape(-1, 3)
+    layer = np.asarray(layer, np.int32)
+    n = len(q)
+    phi = np.zeros(n)
+    field = np.zeros((n, 3))
+    Lm = md.L
+    K = (p + 1) ** 2
+    for l in range(Lm + 1):
+        if not np.any(layer == l):
+            continue
+        lam = md.lam[l]
+        for a in (1, 2):
+            if (a == 1 and l == Lm) or (a == 2 and l == 0):
+                continue
+            root = tree_root(md, xyz, layer, l, a)
+            tk, tsrc, _ = tree_keys(md, xyz, layer, l, a, D, root, 0)
+            ik, isrc, ityp = tree_keys(md, xyz, layer, l, a, D, root, 1)
+            if len(ik) == 0:
+                continue
+            ipos = xyz[isrc].copy()
+            for j in range(len(ik)):
+                lp, b = divmod(int(ityp[j]), 2)
+                ipos[j, 2] = image_z(md, l, a, lp, b + 1, xyz[isrc[j], 2])
+            types = sorted(set(int(t) for t in ityp))
+            tb = {lev: level_boxes(tk, D, lev) for lev in range(2, D + 1)}
+            ib = {lev: level_boxes(ik, D, lev) for lev in range(2, D + 1)}
+            geo = {lev: _Box(root, lev) for lev in range(2, D + 1)}
+            ileaf = np.searchsorted(ib[D], ik)
+            tleaf = np.searchsorted(tb[D], tk)
+            # upward pass on the image tree, one expansion per source type
+            M = {D: np.zeros((len(ib[D]), len(types), K), complex)}
+            for bi in range(len(ib[D])):
+                c = geo[D].centre(ib[D][bi])
+                for ti, t in enumerate(types):
+                    sel = np.nonzero((ileaf == bi) & (ityp == t))[0]
+                    if len(sel):
+                        M[D][bi, ti] = _me_of_points(md.lam[t // 2], ipos[sel], q[isrc[sel]], c, p)
+            for lev in range(D - 1, 1, -1):
+                M[lev] = np.zeros((len(ib[lev]), len(types), K), complex)
+                par = np.searchsorted(ib[lev], ib[lev + 1] >> np.uint64(3))
+                ops = {}
+                for ci, ck in enumerate(ib[lev + 1]):
+                    off = geo[lev + 1].centre(ck) - geo[lev].centre(ib[lev][par[ci]])
+                    for ti, t in enumerate(types):
+                        key = (tuple(np.sign(off).astype(int)), t // 2)
+                        if key not in ops:
+                            ops[key] = np.conj(E.free_shat(md.lam[t // 2], off, p, p))  # b = child - parent
+                        M[lev][par[ci], ti] += ops[key] @ M[lev + 1][ci, ti]
+            # far field
+            L = {lev: np.zeros((len(tb[lev]), K), complex) for lev in range(2, D + 1)}
+            for lev in range(2, D + 1):
+                off, idx = lists(tb[lev], ib[lev], lev, 0)
+                if len(idx) == 0:
+                    continue
+                h = geo[lev].size
+                ops = {t: ReactionM2L(md, l, t // 2, a, t % 2 + 1, p, h, math.sqrt(18.0) * h) for t in types}
+                for t_ in range(len(tb[lev])):
+                    ct = geo[lev].centre(tb[lev][t_])
+                    for s in idx[off[t_]:off[t_ + 1]]:
+                        cs = geo[lev].centre(ib[lev][s])
+                        for ti, t in enumerate(types):
+                            if np.any(M[lev][s, ti]):
+                                L[lev][t_] += ops[t].apply(ct, cs, M[lev][s, ti])
+            for lev in range(2, D):
+                par = np.searchsorted(tb[lev], tb[lev + 1] >> np.uint64(3))
+                ops = {}
+                for ci, ck in enumerate(tb[lev + 1]):
+                    d = geo[lev + 1].centre(ck) - geo[lev].centre(tb[lev][par[ci]])
+                    kd = tuple(np.sign(d).astype(int))
+                    if kd not in ops:
+                        ops[kd] = E.free_shat(lam, d, p, p).T
+                    L[lev + 1][ci] += ops[kd] @ L[lev][par[ci]]
+            # leaves: local expansion and near field
+            uoff, uidx = lists(tb[D], ib[D], D, 1)
+            hD = geo[D].size
+            rules = {}
+            tz = xyz[tsrc, 2]
+            for t in types:
+                lp, b = t // 2, t % 2 + 1
+                ht = _heights(md, l, a, tz).min()
+                hs = _source_heights(md, lp, b, xyz[isrc[ityp == t], 2]).min()
+                rules[t] = ComponentRule(md, l, lp, a, b, ht + hs, 2.0 * math.sqrt(2.0) * hD * 1.000001)
+            for bt in range(len(tb[D])):
+                mem = tsrc[tleaf == bt]
+                v, g = _le_at_points(lam, L[D][bt], geo[D].centre(tb[D][bt]), xyz[mem], p)
+                phi[mem] += v
+                field[mem] -= g
+                near = np.isin(ileaf, uidx[uoff[bt]:uoff[bt + 1]])
+                for t in types:
+                    sel = np.nonzero(near & (ityp == t))[0]
+                    if not len(sel):
+                        continue
+                    srcs = xyz[isrc[sel]]
+                    qs = q[isrc[sel]]
+                    for i in mem:
+                        ph, f = rules[t].sum_at(md, xyz[i], srcs, qs)
+                        phi[i] += ph
+                        field[i] += f
+    return phi, field
+
+
+def fmm(md, q, xyz, layer, p, D):
+    """phi and field of every charge (free part + reaction part), the sum of free_fmm and react_fmm."""
+    a, fa = free_fmm(md, q, xyz, layer, p, D)
+    b, fb = react_fmm(md, q, xyz, layer, p, D)
+    return a + b, fa + fb

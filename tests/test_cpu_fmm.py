@@ -41,3 +41,55 @@ def test_free_fmm_at_depth_2_is_the_direct_sum(w600):
     w, md, ref = w600
     phi, fld = fmm.free_fmm(md, w["q"], w["xyz"], w["layer"], 2, 2)
     assert rel(phi, ref[0]) < 1e-13 and rel(fld, ref[1]) < 1e-13
+
+
+def test_component_rule_matches_the_adaptive_pair_integral():
+    """The near-field sum of oracle/fmm.py (a fixed composite rule per component) equals the
+    oracle's adaptive quadrature of each pair, potential and field."""
+    w = inputs.workload("four_layer", n=400, seed=3)
+    md = oracle.Medium(**w["medium"])
+    rng = np.random.default_rng(0)
+    for (l, lp, a, b) in [(1, 1, 1, 1), (1, 2, 2, 2), (0, 3, 1, 2), (3, 0, 2, 1)]:
+        T = w["xyz"][w["layer"] == l][:2]
+        S = w["xyz"][w["layer"] == lp][:25]
+        qs = rng.uniform(-1, 1, len(S))
+        dmin = fmm._heights(md, l, a, T[:, 2]).min() + fmm._source_heights(md, lp, b, S[:, 2]).min()
+        R = fmm.ComponentRule(md, l, lp, a, b, dmin, 1.5)
+        for r in T:
+            phi, f = R.sum_at(md, r, S, qs)
+            ref = [oracle.green_react_ab(md, l, r, lp, s, a, b) for s in S]
+            rphi = sum(qj * g for qj, (g, _) in zip(qs, ref))
+            rf = sum(qj * gf for qj, (_, gf) in zip(qs, ref))
+            assert abs(phi - rphi) <= 1e-12 * abs(rphi) and np.abs(f - rf).max() <= 1e-12 * np.abs(rf).max()
+
+
+def test_reaction_m2l_shared_rule_matches_direct_quadrature():
+    """The reaction M2L operators of oracle/fmm.py (one node set per component and level, the
+    azimuth as phases) equal direct quadrature of eq. metoleimage2 (oracle/expansions.py)."""
+    from oracle import expansions as E
+    md = oracle.Medium([0.0, -1.2], [1.0, 8.6, 20.5], [1.2, 0.5, 2.1])
+    h = 0.25
+    M = np.random.default_rng(1).normal(size=25) + 1j * np.random.default_rng(2).normal(size=25)
+    for (l, lp, a, b) in [(1, 1, 1, 1), (1, 2, 2, 2), (0, 2, 1, 2)]:
+        dI = md.d[l] if a == 1 else md.d[l - 1]
+        sg = 1 if a == 1 else -1
+        R = fmm.ReactionM2L(md, l, lp, a, b, 4, h, np.sqrt(18) * h)
+        for (dx, dy, kt, ks) in [(2, 1, 0, 0), (-3, -3, 2, 0)]:
+            rct = np.array([0.1 + dx * h, 0.2 + dy * h, dI + sg * (kt + 0.5) * h])
+            rcs = np.array([0.1, 0.2, dI - sg * (ks + 0.5) * h])
+            ref = E.reaction_m2l(md, l, lp, a, b, rct, rcs, 4, 4) @ M
+            assert np.abs(R.apply(rct, rcs, M) - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_reaction_fmm_converges_in_p_to_the_direct_sum():
+    """Algorithm 1 for every component (oracle/fmm.py): geometric convergence in p of the
+    reaction part to the oracle's direct sum, potential and field."""
+    w = inputs.workload("three_layer", n=300, seed=21)
+    md = oracle.Medium(**w["medium"])
+    ref = oracle.direct(md, w["q"], w["xyz"], w["layer"], parts=2)
+    ep, ef = [], []
+    for p in (2, 4):
+        phi, fld = fmm.react_fmm(md, w["q"], w["xyz"], w["layer"], p, 3)
+        ep.append(rel(phi, ref[0]))
+        ef.append(rel(fld, ref[1]))
+    assert ep[0] > 8 * ep[1] and ef[0] > 5 * ef[1] and ep[1] < 3e-3 and ef[1] < 2e-2, (ep, ef)
