@@ -93,3 +93,25 @@ def test_reaction_fmm_converges_in_p_to_the_direct_sum():
         ep.append(rel(phi, ref[0]))
         ef.append(rel(fld, ref[1]))
     assert ep[0] > 8 * ep[1] and ef[0] > 5 * ef[1] and ep[1] < 3e-3 and ef[1] < 2e-2, (ep, ef)
+
+
+def test_paper_accuracy_table_is_the_oracle_fmm_and_decays_in_p():
+    """tests/golden/paper_accuracy_e2.json (make_paper_accuracy.py: the oracle's CPU FMM on the
+    paper's irregular-body workload against the direct sum, per layer, the paper's Err_2 and
+    Err_max) is reproduced for p = 2, and every layer's Err_2 falls at least 3x per two orders."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_accuracy_e2.json")) as f:
+        fx = json.load(f)
+    rows = fx["rows"]
+    for k in range(3):
+        e = [r["phi"][k]["err2"] for r in rows]
+        assert all(e[i] > 3 * e[i + 1] for i in range(len(e) - 1)), (k, e)
+    w = inputs.workload("paper_irregular")
+    md = oracle.Medium(**w["medium"])
+    ref_phi, _ = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    phi, _ = fmm.fmm(md, w["q"], w["xyz"], w["layer"], rows[0]["p"], fx["depth"])
+    for k in range(3):
+        s = w["layer"] == k
+        e2 = np.linalg.norm(phi[s] - ref_phi[s]) / np.linalg.norm(ref_phi[s])
+        assert abs(e2 - rows[0]["phi"][k]["err2"]) <= 1e-9 * e2
