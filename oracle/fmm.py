@@ -16,7 +16,9 @@ of the layer's target group, written step by step from the paper's expansions an
 with c = lam / (2 pi^2 eps) (k_0(lam r) = (pi/2) e^{-lam r} / (lam r)).
 react_fmm: Algorithm 1 for every reaction component on the same group trees (images as sources,
 one ME per source type, M2L by T of eqs. metoleimage1-2 on a shared quadrature node set per
-component and level, near field by the component integral).  Every expansion is
+component and level, near field by the component integral).
+free_fmm_adaptive: the free part on adaptive trees (oracle/adaptive.py), V by M2L and U/W/X
+pairs directly.  Every expansion is
 truncated at degree p and nothing else is approximated, so its result is the FMM's own value at
 that order and tree; against the direct sum it differs by the truncation error only.  Slow:
 meant for a few thousand charges.  Only tests/ may import it; it shares no code with the CUDA
@@ -397,3 +399,89 @@ def fmm(md, q, xyz, layer, p, D):
     a, fa = free_fmm(md, q, xyz, layer, p, D)
     b, fb = react_fmm(md, q, xyz, layer, p, D)
     return a + b, fa + fb
+
+
+def free_fmm_adaptive(md, q, xyz, layer, p, s):
+    """Free-space part of phi and field on adaptive trees: each layer's tree (the group root of the
+    uniform case, keys at depth 21) split while a box holds more than s charges
+    (oracle/adaptive.py).  Lists from the dual traversal of the tree with itself: V pairs by M2L
+    (Thm. 3), U, W and X pairs summed directly (closed form, j != i).  Expansions exist for the
+    boxes of level >= 2: P2M at leaves, M2M to parents, L2L to children, L2P at target leaves.
+    Returns (phi[n], field[n, 3])."""
+    from . import adaptive as A
+    q = np.asarray(q, float)
+    xyz = np.asarray(xyz, float).reshape(-1, 3)
+    layer = np.asarray(layer, np.int32)
+    n = len(q)
+    phi = np.zeros(n)
+    field = np.zeros((n, 3))
+    K = (p + 1) ** 2
+    for l in range(md.L + 1):
+        if not np.any(layer == l):
+            continue
+        a = 1 if l < md.L else 2
+        lam, eps = md.lam[l], md.eps[l]
+        cfac = lam / (2 * math.pi ** 2 * eps)
+        root = tree_root(md, xyz, layer, l, a)
+        keys, src, _ = tree_keys(md, xyz, layer, l, a, A.DMAX, root, 0)
+        T = A.Tree(keys, s)
+        lists_ = A.dual_lists(T, T)
+        H = root[3]
+        x0 = np.array([root[0] - H, root[1] - H, root[2] - H])
+
+        def centre(lev, key):
+            return x0 + (np.array(A._decode(int(key)), float) + 0.5) * (2.0 * H / (1 << lev))
+
+        def pts(lev, key):
+            return src[T.points(lev, key)]
+
+        levels = sorted(T.boxes)
+        M = {}
+        for lev in reversed(levels):
+            if lev < 2:
+                break
+            for key in T.boxes[lev]:
+                c = centre(lev, key)
+                if T.is_leaf(lev, key):
+                    mem = pts(lev, key)
+                    M[(lev, key)] = _me_of_points(lam, xyz[mem], q[mem], c, p)
+                else:
+                    acc = np.zeros(K, complex)
+                    for ch in T.children[(lev, key)]:
+                        acc += np.conj(E.free_shat(lam, centre(lev + 1, ch) - c, p, p)) @ M[(lev + 1, ch)]
+                    M[(lev, key)] = acc
+        L = {}
+        ops = {}
+        for (bt, bs) in lists_["V"]:
+            b = centre(*bt) - centre(*bs)
+            kb = (bt[0],) + tuple(np.round(b / (2.0 * H / (1 << bt[0]))).astype(int))
+            if kb not in ops:
+                ops[kb] = E.free_s(lam, b, p, p).T
+            L[bt] = L.get(bt, np.zeros(K, complex)) + ops[kb] @ M[bs]
+        for lev in levels:
+            if lev < 2:
+                continue
+            for key in T.boxes[lev]:
+                if (lev, key) not in L or T.is_leaf(lev, key):
+                    continue
+                c = centre(lev, key)
+                for ch in T.children[(lev, key)]:
+                    L[(lev + 1, ch)] = L.get((lev + 1, ch), np.zeros(K, complex)) + \
+                        E.free_shat(lam, centre(lev + 1, ch) - c, p, p).T @ L[(lev, key)]
+        for (lev, key) in T.leaves:
+            if (lev, key) in L:
+                mem = pts(lev, key)
+                v, g = _le_at_points(lam, L[(lev, key)], centre(lev, key), xyz[mem], p)
+                phi[mem] += cfac * v
+                field[mem] -= cfac * g
+        for kind in ("U", "W", "X"):
+            for (bt, bs) in lists_[kind]:
+                tm, sm = pts(*bt), pts(*bs)
+                for i in tm:
+                    js = sm[sm != i]
+                    d = xyz[i] - xyz[js]
+                    r = np.sqrt((d * d).sum(1))
+                    e = q[js] * np.exp(-lam * r) / (4 * math.pi * eps * r)
+                    phi[i] += e.sum()
+                    field[i] += ((e * (1 + lam * r) / (r * r))[:, None] * d).sum(0)
+    return phi, field

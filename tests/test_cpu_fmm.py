@@ -115,3 +115,23 @@ def test_paper_accuracy_table_is_the_oracle_fmm_and_decays_in_p():
         s = w["layer"] == k
         e2 = np.linalg.norm(phi[s] - ref_phi[s]) / np.linalg.norm(ref_phi[s])
         assert abs(e2 - rows[0]["phi"][k]["err2"]) <= 1e-9 * e2
+
+
+def test_adaptive_free_fmm_converges_in_p_to_the_direct_sum():
+    """The free-space FMM on adaptive trees (oracle/adaptive.py lists: V by M2L, U/W/X direct)
+    on the paper's irregular bodies, where the leaves sit at several levels and W/X pairs occur,
+    converges geometrically in p to the direct sum."""
+    from oracle import adaptive as A
+    w = inputs.workload("paper_irregular", n=1200)
+    md = oracle.Medium(**w["medium"])
+    root = oracle.tree_root(md, w["xyz"], w["layer"], 2, 2)
+    keys, _, _ = oracle.tree_keys(md, w["xyz"], w["layer"], 2, 2, A.DMAX, root, 0)
+    Ls = A.dual_lists(A.Tree(keys, 16), A.Tree(keys, 16))
+    assert Ls["W"] and Ls["X"]
+    ref = oracle.direct(md, w["q"], w["xyz"], w["layer"], parts=1)
+    ep, ef = [], []
+    for p in (2, 4, 6):
+        phi, fld = fmm.free_fmm_adaptive(md, w["q"], w["xyz"], w["layer"], p, 16)
+        ep.append(rel(phi, ref[0]))
+        ef.append(rel(fld, ref[1]))
+    assert ep[0] > 4 * ep[1] > 16 * ep[2] and ef[0] > 3 * ef[1] > 9 * ef[2] and ep[2] < 3e-4, (ep, ef)
