@@ -31,15 +31,7 @@ from scipy import special
 
 from . import level_boxes, lists, tree_keys, tree_root
 from . import expansions as E
-
-
-def _decode(key):
-    x = y = z = 0
-    for k in range(21):
-        z |= ((key >> (3 * k)) & 1) << k
-        y |= ((key >> (3 * k + 1)) & 1) << k
-        x |= ((key >> (3 * k + 2)) & 1) << k
-    return x, y, z
+from .adaptive import _decode
 
 
 class _Box:
@@ -262,9 +254,8 @@ class ReactionM2L:
             e = self.base * np.exp(-self.lz * zt - self.lzp * zs)
             p = self.p
             J = special.jv(np.arange(-2 * p, 2 * p + 1)[None, :], self.x[:, None] * rho)  # [nodes, 4p + 1]
-            idx = E._nm(p)
-            m_row = np.array([m for _, m in idx])
-            mu_col = np.array([m for _, m in idx])
+            m_row = np.array([m for _, m in E._nm(p)])
+            mu_col = m_row
             T = np.zeros(self.k.shape, complex)
             for mv in range(-p, p + 1):
                 rows = m_row == mv
@@ -430,7 +421,7 @@ def free_fmm_adaptive(md, q, xyz, layer, p, s):
         x0 = np.array([root[0] - H, root[1] - H, root[2] - H])
 
         def centre(lev, key):
-            return x0 + (np.array(A._decode(int(key)), float) + 0.5) * (2.0 * H / (1 << lev))
+            return x0 + (np.array(_decode(int(key)), float) + 0.5) * (2.0 * H / (1 << lev))
 
         def pts(lev, key):
             return src[T.points(lev, key)]
