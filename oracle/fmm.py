@@ -17,8 +17,8 @@ with c = lam / (2 pi^2 eps) (k_0(lam r) = (pi/2) e^{-lam r} / (lam r)).
 react_fmm: Algorithm 1 for every reaction component on the same group trees (images as sources,
 one ME per source type, M2L by T of eqs. metoleimage1-2 on a shared quadrature node set per
 component and level, near field by the component integral).
-free_fmm_adaptive: the free part on adaptive trees (oracle/adaptive.py), V by M2L and U/W/X
-pairs directly.  Every expansion is
+free_fmm_adaptive, react_fmm_adaptive: both parts on adaptive trees (oracle/adaptive.py), V by
+M2L and U/W/X pairs directly.  Every expansion is
 truncated at degree p and nothing else is approximated, so its result is the FMM's own value at
 that order and tree; against the direct sum it differs by the truncation error only.  Slow:
 meant for a few thousand charges.  Only tests/ may import it; it shares no code with the CUDA
@@ -475,4 +475,114 @@ def free_fmm_adaptive(md, q, xyz, layer, p, s):
                     e = q[js] * np.exp(-lam * r) / (4 * math.pi * eps * r)
                     phi[i] += e.sum()
                     field[i] += ((e * (1 + lam * r) / (r * r))[:, None] * d).sum(0)
+    return phi, field
+
+
+def react_fmm_adaptive(md, q, xyz, layer, p, s):
+    """Reaction part of phi and field on adaptive dual trees (oracle/adaptive.py): per target
+    group (l, a) the target tree of its charges and the source tree of its images, each split
+    while a box holds more than s of its points.  V pairs by M2L (T of eqs. metoleimage1-2, one
+    ME per source type), U, W and X pairs by the component integral directly; expansions for the
+    boxes of level >= 2 (P2M at image leaves, M2M with lam_l', L2L and L2P with lam_l).
+    Returns (phi[n], field[n, 3])."""
+    from . import adaptive as A
+    from . import image_z
+    q = np.asarray(q, float)
+    xyz = np.asarray(xyz, float).reshape(-1, 3)
+    layer = np.asarray(layer, np.int32)
+    n = len(q)
+    phi = np.zeros(n)
+    field = np.zeros((n, 3))
+    K = (p + 1) ** 2
+    for l in range(md.L + 1):
+        if not np.any(layer == l):
+            continue
+        lam = md.lam[l]
+        for a in (1, 2):
+            if (a == 1 and l == md.L) or (a == 2 and l == 0):
+                continue
+            root = tree_root(md, xyz, layer, l, a)
+            T, S, (tsrc, isrc, ityp) = A.group_trees(md, xyz, layer, l, a, root, s)
+            if not S.boxes or not T.boxes:
+                continue
+            H = root[3]
+            x0 = np.array([root[0] - H, root[1] - H, root[2] - H])
+
+            def centre(lev, key):
+                return x0 + (np.array(_decode(int(key)), float) + 0.5) * (2.0 * H / (1 << lev))
+
+            ipos = xyz[isrc].copy()
+            for j in range(len(isrc)):
+                lp, b = divmod(int(ityp[j]), 2)
+                ipos[j, 2] = image_z(md, l, a, lp, b + 1, xyz[isrc[j], 2])
+            types = sorted(set(int(t) for t in ityp))
+            Ls = A.dual_lists(T, S)
+            # upward pass on the image tree, one expansion per source type
+            M = {}
+            for lev in sorted(S.boxes, reverse=True):
+                if lev < 2:
+                    break
+                for key in S.boxes[lev]:
+                    c = centre(lev, key)
+                    Mb = np.zeros((len(types), K), complex)
+                    if S.is_leaf(lev, key):
+                        sel = S.points(lev, key)
+                        for ti, t in enumerate(types):
+                            st = sel[ityp[sel] == t]
+                            if len(st):
+                                Mb[ti] = _me_of_points(md.lam[t // 2], ipos[st], q[isrc[st]], c, p)
+                    else:
+                        for ch in S.children[(lev, key)]:
+                            off = centre(lev + 1, ch) - c
+                            for ti, t in enumerate(types):
+                                Mb[ti] += np.conj(E.free_shat(md.lam[t // 2], off, p, p)) @ M[(lev + 1, ch)][ti]
+                    M[(lev, key)] = Mb
+            # far field
+            L = {}
+            ops = {}
+            for (bt, bs) in Ls["V"]:
+                lev = bt[0]
+                h = 2.0 * H / (1 << lev)
+                for ti, t in enumerate(types):
+                    if not np.any(M[bs][ti]):
+                        continue
+                    if (lev, t) not in ops:
+                        ops[(lev, t)] = ReactionM2L(md, l, t // 2, a, t % 2 + 1, p, h, math.sqrt(18.0) * h)
+                    L[bt] = L.get(bt, np.zeros(K, complex)) + ops[(lev, t)].apply(centre(*bt), centre(*bs), M[bs][ti])
+            for lev in sorted(T.boxes):
+                if lev < 2:
+                    continue
+                for key in T.boxes[lev]:
+                    if (lev, key) not in L or T.is_leaf(lev, key):
+                        continue
+                    c = centre(lev, key)
+                    for ch in T.children[(lev, key)]:
+                        L[(lev + 1, ch)] = L.get((lev + 1, ch), np.zeros(K, complex)) + \
+                            E.free_shat(lam, centre(lev + 1, ch) - c, p, p).T @ L[(lev, key)]
+            for (lev, key) in T.leaves:
+                if (lev, key) in L:
+                    mem = tsrc[T.points(lev, key)]
+                    v, g = _le_at_points(lam, L[(lev, key)], centre(lev, key), xyz[mem], p)
+                    phi[mem] += v
+                    field[mem] -= g
+            # direct pairs
+            rules = {}
+            for t in types:
+                lp, b = t // 2, t % 2 + 1
+                ht = _heights(md, l, a, xyz[tsrc, 2]).min()
+                hs = _source_heights(md, lp, b, xyz[isrc[ityp == t], 2]).min()
+                rules[t] = ComponentRule(md, l, lp, a, b, ht + hs, 2.0 * math.sqrt(2.0) * H)
+            for kind in ("U", "W", "X"):
+                for (bt, bs) in Ls[kind]:
+                    tm = tsrc[T.points(*bt)]
+                    sm = S.points(*bs)
+                    for t in types:
+                        st = sm[ityp[sm] == t]
+                        if not len(st):
+                            continue
+                        srcs, qs = xyz[isrc[st]], q[isrc[st]]
+                        for i in tm:
+                            ph, f = rules[t].sum_at(md, xyz[i], srcs, qs)
+                            phi[i] += ph
+                            field[i] += f
     return phi, field

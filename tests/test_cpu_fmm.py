@@ -135,3 +135,17 @@ def test_adaptive_free_fmm_converges_in_p_to_the_direct_sum():
         ep.append(rel(phi, ref[0]))
         ef.append(rel(fld, ref[1]))
     assert ep[0] > 4 * ep[1] > 16 * ep[2] and ef[0] > 3 * ef[1] > 9 * ef[2] and ep[2] < 3e-4, (ep, ef)
+
+
+def test_adaptive_reaction_fmm_converges_in_p_to_the_direct_sum():
+    """The reaction part on adaptive dual trees (V by M2L with T, U/W/X by the component
+    integral) converges in p to the direct sum on the paper's bodies."""
+    w = inputs.workload("paper_irregular", n=300)
+    md = oracle.Medium(**w["medium"])
+    ref = oracle.direct(md, w["q"], w["xyz"], w["layer"], parts=2)
+    ep, ef = [], []
+    for p in (2, 4):
+        phi, fld = fmm.react_fmm_adaptive(md, w["q"], w["xyz"], w["layer"], p, 8)
+        ep.append(rel(phi, ref[0]))
+        ef.append(rel(fld, ref[1]))
+    assert ep[0] > 5 * ep[1] and ef[0] > 3 * ef[1] and ep[1] < 1e-2, (ep, ef)
