@@ -50,6 +50,28 @@ def _radial_rows(lam, R, p):
     return special.spherical_in(np.arange(p + 1)[:, None], lam * np.asarray(R)[None, :])[nrow]
 
 
+def _lists_ws(tb, sb, lev, kind, ws):
+    """Uniform-tree lists with separation ws boxes: near (kind 1) = source boxes within ws boxes
+    in every coordinate; far (kind 0) = source boxes farther than ws whose parents are within ws
+    of the target's parent.  ws = 1 is the rule of oracle.lists (one-box separation).  CSR over
+    the target boxes: (off, idx)."""
+    if ws == 1:
+        return lists(tb, sb, lev, kind)
+    sc = np.array([_decode(int(k)) for k in sb]).reshape(-1, 3)
+    off, idx = [0], []
+    for k in tb:
+        c = np.array(_decode(int(k)))
+        d = np.abs(sc - c).max(1)
+        if kind == 1:
+            sel = np.nonzero(d <= ws)[0]
+        else:
+            dp = np.abs((sc >> 1) - (c >> 1)).max(1)
+            sel = np.nonzero((d > ws) & (dp <= ws))[0]
+        idx.extend(sel.tolist())
+        off.append(len(idx))
+    return np.array(off, np.int64), np.array(idx, np.int64)
+
+
 def _me_of_points(lam, pts, q, c, p):
     """sum_j q_j 4 pi i_n(lam r_j) conj Y_n^m of the points about c (P2M)."""
     R, T, P = E.sph(pts - c)
@@ -72,9 +94,10 @@ def _le_at_points(lam, L, c, pts, p):
     return val.real, grad
 
 
-def free_fmm(md, q, xyz, layer, p, D):
+def free_fmm(md, q, xyz, layer, p, D, ws=1):
     """Free-space part of phi and field (field = -grad phi) of every charge by the FMM above, with
-    every group tree at uniform depth D >= 2.  Returns (phi[n], field[n, 3])."""
+    every group tree at uniform depth D >= 2 and separation ws boxes (1: the GPU's lists).
+    Returns (phi[n], field[n, 3])."""
     q = np.asarray(q, float)
     xyz = np.asarray(xyz, float).reshape(-1, 3)
     layer = np.asarray(layer, np.int32)
@@ -109,7 +132,7 @@ def free_fmm(md, q, xyz, layer, p, D):
         # far field
         L = {lev: np.zeros((len(boxes[lev]), (p + 1) ** 2), complex) for lev in range(2, D + 1)}
         for lev in range(2, D + 1):
-            off, idx = lists(boxes[lev], boxes[lev], lev, 0)
+            off, idx = _lists_ws(boxes[lev], boxes[lev], lev, 0, ws)
             ops = {}
             for t in range(len(boxes[lev])):
                 ct = geo[lev].centre(boxes[lev][t])
@@ -130,7 +153,7 @@ def free_fmm(md, q, xyz, layer, p, D):
                     ops[kd] = E.free_shat(lam, d, p, p).T
                 L[lev + 1][ci] += ops[kd] @ L[lev][par[ci]]
         # leaves: local expansion and near field
-        uoff, uidx = lists(boxes[D], boxes[D], D, 1)
+        uoff, uidx = _lists_ws(boxes[D], boxes[D], D, 1, ws)
         for b, mem in enumerate(members):
             pts = xyz[mem]
             v, g = _le_at_points(lam, L[D][b], geo[D].centre(boxes[D][b]), pts, p)
@@ -273,7 +296,7 @@ class ReactionM2L:
         return (np.exp(1j * self.k * ph) * self.T(rho, zt, zs)) @ M
 
 
-def react_fmm(md, q, xyz, layer, p, D):
+def react_fmm(md, q, xyz, layer, p, D, ws=1):
     """Reaction part of phi and field of every charge: Algorithm 1 for every component, on the
     uniform trees (depth D) of each target group (l, a).  Targets are the layer's charges; sources
     are the polarization images (eq. eqpolarizedsource) of every charge, one ME per source type
@@ -335,11 +358,12 @@ def react_fmm(md, q, xyz, layer, p, D):
             # far field
             L = {lev: np.zeros((len(tb[lev]), K), complex) for lev in range(2, D + 1)}
             for lev in range(2, D + 1):
-                off, idx = lists(tb[lev], ib[lev], lev, 0)
+                off, idx = _lists_ws(tb[lev], ib[lev], lev, 0, ws)
                 if len(idx) == 0:
                     continue
                 h = geo[lev].size
-                ops = {t: ReactionM2L(md, l, t // 2, a, t % 2 + 1, p, h, math.sqrt(18.0) * h) for t in types}
+                rmax = math.sqrt(2.0) * (2 * ws + 1) * h
+                ops = {t: ReactionM2L(md, l, t // 2, a, t % 2 + 1, p, h, rmax) for t in types}
                 for t_ in range(len(tb[lev])):
                     ct = geo[lev].centre(tb[lev][t_])
                     for s in idx[off[t_]:off[t_ + 1]]:
@@ -357,7 +381,7 @@ def react_fmm(md, q, xyz, layer, p, D):
                         ops[kd] = E.free_shat(lam, d, p, p).T
                     L[lev + 1][ci] += ops[kd] @ L[lev][par[ci]]
             # leaves: local expansion and near field
-            uoff, uidx = lists(tb[D], ib[D], D, 1)
+            uoff, uidx = _lists_ws(tb[D], ib[D], D, 1, ws)
             hD = geo[D].size
             rules = {}
             tz = xyz[tsrc, 2]
@@ -365,7 +389,7 @@ def react_fmm(md, q, xyz, layer, p, D):
                 lp, b = t // 2, t % 2 + 1
                 ht = _heights(md, l, a, tz).min()
                 hs = _source_heights(md, lp, b, xyz[isrc[ityp == t], 2]).min()
-                rules[t] = ComponentRule(md, l, lp, a, b, ht + hs, 2.0 * math.sqrt(2.0) * hD * 1.000001)
+                rules[t] = ComponentRule(md, l, lp, a, b, ht + hs, math.sqrt(2.0) * (ws + 1) * hD * 1.000001)
             for bt in range(len(tb[D])):
                 mem = tsrc[tleaf == bt]
                 v, g = _le_at_points(lam, L[D][bt], geo[D].centre(tb[D][bt]), xyz[mem], p)
@@ -385,10 +409,10 @@ def react_fmm(md, q, xyz, layer, p, D):
     return phi, field
 
 
-def fmm(md, q, xyz, layer, p, D):
+def fmm(md, q, xyz, layer, p, D, ws=1):
     """phi and field of every charge (free part + reaction part), the sum of free_fmm and react_fmm."""
-    a, fa = free_fmm(md, q, xyz, layer, p, D)
-    b, fb = react_fmm(md, q, xyz, layer, p, D)
+    a, fa = free_fmm(md, q, xyz, layer, p, D, ws)
+    b, fb = react_fmm(md, q, xyz, layer, p, D, ws)
     return a + b, fa + fb
 
 
