@@ -149,3 +149,12 @@ def test_adaptive_reaction_fmm_converges_in_p_to_the_direct_sum():
         ep.append(rel(phi, ref[0]))
         ef.append(rel(fld, ref[1]))
     assert ep[0] > 5 * ep[1] and ef[0] > 3 * ef[1] and ep[1] < 1e-2, (ep, ef)
+
+
+def test_two_box_separation_is_more_accurate_at_the_same_order(w600):
+    """With far pairs at least two boxes apart (near field 5^3 boxes) the truncation error at a
+    given p falls by more than an order of magnitude against the one-box rule."""
+    w, md, ref = w600
+    e1 = rel(fmm.free_fmm(md, w["q"], w["xyz"], w["layer"], 4, 4, ws=1)[0], ref[0])
+    e2 = rel(fmm.free_fmm(md, w["q"], w["xyz"], w["layer"], 4, 4, ws=2)[0], ref[0])
+    assert e2 < e1 / 10, (e1, e2)
