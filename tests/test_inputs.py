@@ -91,3 +91,28 @@ def test_benchmark_oracle_fixture_matches_the_oracle_and_the_bench_workload():
     phi, fld = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=np.array([fx["targets"][k]]))
     assert abs(phi[0] - fx["phi"][k]) <= 1e-12 * abs(phi[0])
     assert np.allclose(fld[0], fx["field"][k], rtol=1e-12, atol=1e-14)
+
+
+def test_four_layer_200k_oracle_fixture_matches_the_oracle():
+    """tests/golden/four_layer_200k_oracle.json (make_four_layer_200k_oracle.py, oracle only):
+    the stated draw of 25 charges per layer and one stored charge recomputed by the oracle."""
+    import importlib.util
+    import json
+    import os
+
+    import oracle
+
+    here = os.path.dirname(__file__)
+    spec = importlib.util.spec_from_file_location("mk200k", os.path.join(here, "golden", "make_four_layer_200k_oracle.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    fx = json.load(open(os.path.join(here, "golden", "four_layer_200k_oracle.json")))
+    w = inputs.workload("four_layer", n=fx["n"], seed=fx["seed"])
+    assert fx["targets"] == mk.sample_targets(w["layer"], fx["per_layer"], fx["seed"])
+    assert np.array_equal(np.array(fx["q"]), w["q"][fx["targets"]])
+    oracle.build()
+    md = oracle.Medium(**w["medium"])
+    k = 57
+    phi, fld = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=np.array([fx["targets"][k]]))
+    assert abs(phi[0] - fx["phi"][k]) <= 1e-12 * abs(phi[0])
+    assert np.allclose(fld[0], fx["field"][k], rtol=1e-12, atol=1e-14)
