@@ -6,6 +6,12 @@ over three unit cubes (one per layer), q ~ U[-1, 1], p = 10, mixed precision.  I
 resident in HBM; L2 is flushed (256 MB write) between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload three_layer|paper_irregular] [--n N] [--p P]
+
+--workload paper_irregular runs the same measurement on the paper's own charges (Sec. 4: three
+irregular bodies in the medium eps = (1, 8.6, 20.5), lambda = (1.2, 0.5, 2.1)) under its own
+metric name, for context beside the paper's CPU timings (potential only, p = 5, N up to
+2,861,288); the default workload is the headline.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (direct sum) on the host
 cores on a bounded sample of the same workload.  With --gpus N > 1 (launched by
