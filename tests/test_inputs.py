@@ -116,3 +116,28 @@ def test_four_layer_200k_oracle_fixture_matches_the_oracle():
     phi, fld = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=np.array([fx["targets"][k]]))
     assert abs(phi[0] - fx["phi"][k]) <= 1e-12 * abs(phi[0])
     assert np.allclose(fld[0], fx["field"][k], rtol=1e-12, atol=1e-14)
+
+
+def test_batch_systems_follow_their_recipe():
+    """The batching workload's generator: N log-uniform in [1e3, 6.4e4]; 2-4 layers with
+    eps ~ U[1, 10], lambda ~ U[0.2, 2], finite thicknesses ~ U[0.5, 2], d_0 = 0; every charge of a
+    system in one host layer, inside it by the stated margin, xy in the unit square."""
+    import oracle
+    systems = inputs.batch(nsys=40)
+    assert len(systems) == 40
+    for s in systems:
+        md = s["medium"]
+        d, eps, lam = np.asarray(md["d"]), np.asarray(md["eps"]), np.asarray(md["lam"])
+        n = len(s["q"])
+        assert 1000 <= n <= 64000 and 2 <= len(eps) <= 4 and len(d) == len(eps) - 1
+        assert d[0] == 0.0 and np.all(np.diff(d) < 0) and np.all((-np.diff(d) >= 0.5) & (-np.diff(d) <= 2.0))
+        assert np.all((eps >= 1) & (eps <= 10)) and np.all((lam >= 0.2) & (lam <= 2.0))
+        assert len(np.unique(s["layer"])) == 1
+        o = oracle.Medium(d, eps, lam)
+        host = int(s["layer"][0])
+        assert all(o.layer_of(z) == host for z in s["xyz"][:200, 2])
+        assert np.all(np.abs(s["xyz"][:, :2]) <= 0.5) and np.all(np.abs(s["q"]) <= 1.0)
+        zs = s["xyz"][:, 2]
+        top = d[host - 1] if host > 0 else np.inf
+        bot = d[host] if host < len(d) else -np.inf
+        assert np.all(zs < top - 0.04) and np.all(zs > bot + 0.04)
