@@ -9,7 +9,9 @@ does, and it shares no code with the CUDA path.
 Contents (each cites the passage it follows):
   phat, ylm            normalized associated Legendre functions and spherical harmonics
                        (Sec. 3.1), continued to arguments x > 1 with the square-root branch of
-                       Prop. 1 (eq. branch): sqrt(1 - x^2) = -i sqrt(x^2 - 1) for x > 1.
+                       Prop. 1 (eq. branch): sqrt(1 - x^2) = -i sqrt(x^2 - 1) for x > 1;
+                       phat_all, ylm_all evaluate every order at once (same definition).
+  phat_ratio_t_coeffs  phat_n^m / phat_m^m as a polynomial in t = x^2 - 1 (exact rationals).
   addition_k0          the zeroth-order addition theorem (Thm. 1, eq. sphbessel00).
   free_me, free_le     free-space ME and LE (Sec. 3.1, eqs. freespace3dmulexp,
                        freespace3dlocexp, melecoeffree).
