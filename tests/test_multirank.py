@@ -96,3 +96,17 @@ def test_paper_workload_option_names_its_own_metric_and_config():
     seed = bench.rank_seed(0)
     assert bench.load_oracle_fixture(1000000, seed) is not None
     assert bench.load_oracle_fixture(1000000, seed, "paper_irregular") is None
+
+
+def test_clock_summary_reads_median_max_and_active_reasons():
+    """The clock record of the timed region: median SM clock, maximum, and the throttle reasons
+    seen active, from nvidia-smi's CSV lines (malformed lines are skipped)."""
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2040, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage", "0, N/A, 2070, 1, 0, a, b, c, d"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2040.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] == 3
+    assert bench.ClockSampler(0).summary()["samples"] == 0
