@@ -130,6 +130,8 @@ def parse():
     ap.add_argument("--p", type=int, default=P_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the leaf-size target by timing candidates on the workload first")
     return ap.parse_args()
 
 
@@ -272,7 +274,15 @@ def run_ours(args, rank, world, local_rank):
     x = torch.tensor(w["xyz"], device=dev)
     l = torch.tensor(w["layer"], dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.MIXED, stream=stream)
+    leaf, tuned = 128, None
+    if args.autotune:
+        from paper_2002_01334_gb300 import autotune
+        measure, close = autotune.cuda_measure(m, args.p, F.MIXED, q, x, l, stream=stream)
+        leaf, table = autotune.choose(autotune.CANDIDATES, measure, repeats=2)
+        close()
+        tuned = {"parameter": "max_per_leaf", "ms_by_candidate": {str(k): v for k, v in table.items()},
+                 "chosen": leaf}
+    ctx = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.MIXED, max_per_leaf=leaf, stream=stream)
     n = args.n
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     fld = torch.empty((n, 3), dtype=torch.float64, device=dev)
@@ -413,7 +423,10 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": metric_of(args.workload), "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": workload_config(n, args.p, "mixed", args.workload), "clocks": clk.summary(),
+                "config": dict(workload_config(n, args.p, "mixed", args.workload),
+                               **({"tree": "automatic depth, <=%d mean targets per leaf (autotuned)" % leaf}
+                                  if tuned else {})),
+                "clocks": clk.summary(), "autotune": tuned,
                 "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
                         "d2h_bytes_per_step": n * (8 + 24)},
                 "gpu_launches": launches_per_step * args.steps, "roofline": roof_main, "rooflines": roofs,
