@@ -1,7 +1,9 @@
-"""CPU pins of the oracle's free-space FMM (oracle/fmm.py): with every expansion truncated at p
-and nothing else approximated, it must converge geometrically in p to the direct sum (Sec. 3.1
-expansions, one-box separation), for potential and field, at several tree depths.  It is the
-reference against which a GPU FMM of the same tree and order can be compared to rounding."""
+"""CPU pins of the oracle's FMM (oracle/fmm.py), free space and reaction components, on uniform
+and adaptive trees: with every expansion truncated at p and nothing else approximated, it must
+converge geometrically in p to the direct sum (Sec. 3.1 and 3.4 expansions), for potential and
+field.  Its pieces are checked on their own too (the near-field rule and the reaction M2L
+operators against the oracle's adaptive quadratures).  It is the reference against which a GPU
+FMM of the same trees and order can be compared to rounding."""
 import numpy as np
 import pytest
 
