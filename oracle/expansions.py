@@ -557,3 +557,39 @@ def free_m2m(lam, M, rcs, rcs_new, p):
 def free_l2l(lam, L, rct, rct_new, p):
     """LE about rct shifted to rct_new (eq. metome): L~_nm = sum Shat_{nu n}^{mu m}(rct_new - rct) L_{nu mu}."""
     return free_shat(lam, np.asarray(rct_new, float) - rct, p, p).T @ L
+
+
+# ------------------------------------------------------------------------------------------
+# Recurrences of the scaled Sommerfeld-type integrals (Sec. 3.5, eqs. recurrence1 and
+# backwardrecurrence1), on arrays S[n, m, i, j] = S^n S_{nm,ij} (as oracle.S_table returns)
+
+def _a(n):
+    return math.sqrt(n * (n + 1.0))
+
+
+def forward_recurrence(S0, rho_over_S):
+    """Fill m >= 2 from the columns m = 0, 1 of S0 by eq. recurrence1:
+    S^n S_{n,m+1} = (2m / a_{n+m}) (S/rho) S^{n-1} S_{n-1,m} - (a_{n-m} / a_{n+m}) S^n S_{n,m-1}."""
+    S = np.array(S0, float)
+    S[:, 2:] = 0.0
+    K = S.shape[0] - 1
+    for m in range(1, K):
+        for n in range(m + 1, K + 1):
+            S[n, m + 1] = (2 * m / _a(n + m)) / rho_over_S * S[n - 1, m] - (_a(n - m) / _a(n + m)) * S[n, m - 1]
+    return S
+
+
+def backward_recurrence(S0, rho_over_S):
+    """Fill the rows n < K (columns m >= 1) from the top row n = K and the column m = 0 of S0 by
+    eq. backwardrecurrence1, the forward recurrence solved for its lower-order term:
+    S^{n-1} S_{n-1,m} = (a_{n+m} / 2m) (rho/S) S^n S_{n,m+1} + (a_{n-m} / 2m) (rho/S) S^n S_{n,m-1}.
+    The column m = 0 below the top row is not produced by the recurrence (its 2m vanishes) and is
+    taken from S0, like the top row."""
+    S = np.array(S0, float)
+    K = S.shape[0] - 1
+    S[:K, 1:] = 0.0
+    for n in range(K, 1, -1):
+        for m in range(1, n):
+            S[n - 1, m] = (_a(n + m) / (2 * m)) * rho_over_S * S[n, m + 1] + \
+                (_a(n - m) / (2 * m)) * rho_over_S * S[n, m - 1]
+    return S

@@ -377,3 +377,35 @@ def test_tree_keys_and_lists_brute_force():
             ref = brute_lists(coords_of(tb), coords_of(sb), lev, kind)
             got = [list(idx[off[t]:off[t + 1]]) for t in range(len(tb))]
             assert got == ref
+
+
+def test_sommerfeld_recurrences_where_each_holds():
+    """Sec. 3.5: the forward recurrence (eq. recurrence1) from exact columns d = 0, 1 and the
+    backward recurrence (eq. backwardrecurrence1) from the exact top row and column d = 0,
+    against direct quadrature of every entry (oracle.S_table), relative to each row's largest
+    entry the operators use.  Backward holds for small rho/S, forward for large; forward at
+    rho = S loses everything by K = 21, although the paper states it stable for rho >= S."""
+    from oracle import expansions as E
+    md = oracle.Medium([0.0, -1.2], [1.0, 2.0, 5.0], [0.5, 1.0, 0.8])
+    h, K = 0.3, 21
+
+    def errs(r2, kt, ks):
+        r = np.sqrt(r2)
+        D = oracle.S_table(md, 1, 1, 1, 2, h, r * h, (kt + 0.5) * h, (ks + 0.5) * h, K)
+        F, B = E.forward_recurrence(D, r), E.backward_recurrence(D, r)
+        ef = eb = 0.0
+        for n in range(2, K + 1):
+            used = [d for d in range(n + 1) if (n - d) % 2 == 1]
+            rm = np.abs(D[n, used]).max()
+            uf, ub = [d for d in used if d >= 2], [d for d in used if d >= 1]
+            ef = max(ef, np.abs(F[n, uf] - D[n, uf]).max(initial=0) / rm)
+            eb = max(eb, np.abs(B[n, ub] - D[n, ub]).max(initial=0) / rm)
+        return ef, eb
+
+    for r2, kt, ks in [(1, 1, 1), (2, 0, 1), (0.09, 0, 0)]:
+        ef, eb = errs(r2, kt, ks)
+        assert eb < 1e-12, (r2, eb)
+    assert errs(1, 1, 1)[0] > 1e-2
+    for r2, kt, ks in [(13, 0, 0), (18, 1, 1)]:
+        ef, eb = errs(r2, kt, ks)
+        assert ef < 1e-9, (r2, ef)
