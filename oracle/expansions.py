@@ -573,6 +573,8 @@ def forward_recurrence(S0, rho_over_S):
     S = np.array(S0, float)
     S[:, 2:] = 0.0
     K = S.shape[0] - 1
+    if rho_over_S == 0:  # S_{nm}(0, z, z') = 0 for m > 0 (Sec. 3.5)
+        return S
     for m in range(1, K):
         for n in range(m + 1, K + 1):
             S[n, m + 1] = (2 * m / _a(n + m)) / rho_over_S * S[n - 1, m] - (_a(n - m) / _a(n + m)) * S[n, m - 1]
