@@ -61,7 +61,7 @@ def lib():
         L.orc_tree_keys.restype = C.c_int64
         L.orc_level_boxes.argtypes = [up, C.c_int64, C.c_int, C.c_int, up]
         L.orc_level_boxes.restype = C.c_int64
-        L.orc_lists.argtypes = [up, C.c_int64, up, C.c_int64, C.c_int, C.c_int, lp, lp]
+        L.orc_lists.argtypes = [up, C.c_int64, up, C.c_int64, C.c_int, C.c_int, C.c_int, lp, lp]
         L.orc_lists.restype = C.c_int64
         L.orc_morton.argtypes = [C.c_int, C.c_int, C.c_int]
         L.orc_morton.restype = C.c_uint64
@@ -210,15 +210,15 @@ def level_boxes(keys, D, lev):
     return out[:c]
 
 
-def lists(tboxes, sboxes, lev, kind):
-    """CSR interaction lists (kind 0 far/V, kind 1 near/U) at level lev."""
+def lists(tboxes, sboxes, lev, kind, ws=1):
+    """CSR interaction lists (kind 0 far/V, kind 1 near/U) at level lev, separation ws boxes."""
     tb = np.ascontiguousarray(tboxes, np.uint64)
     sb = np.ascontiguousarray(sboxes, np.uint64)
     off = np.zeros(len(tb) + 1, np.int64)
-    tot = lib().orc_lists(_p(tb, C.c_uint64), len(tb), _p(sb, C.c_uint64), len(sb), lev, kind,
+    tot = lib().orc_lists(_p(tb, C.c_uint64), len(tb), _p(sb, C.c_uint64), len(sb), lev, kind, int(ws),
                           _p(off, C.c_int64), None)
     idx = np.zeros(max(1, tot), np.int64)
-    lib().orc_lists(_p(tb, C.c_uint64), len(tb), _p(sb, C.c_uint64), len(sb), lev, kind,
+    lib().orc_lists(_p(tb, C.c_uint64), len(tb), _p(sb, C.c_uint64), len(sb), lev, kind, int(ws),
                     _p(off, C.c_int64), _p(idx, C.c_int64))
     return off, idx[:tot]
 

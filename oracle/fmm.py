@@ -51,25 +51,10 @@ def _radial_rows(lam, R, p):
 
 
 def _lists_ws(tb, sb, lev, kind, ws):
-    """Uniform-tree lists with separation ws boxes: near (kind 1) = source boxes within ws boxes
-    in every coordinate; far (kind 0) = source boxes farther than ws whose parents are within ws
-    of the target's parent.  ws = 1 is the rule of oracle.lists (one-box separation).  CSR over
-    the target boxes: (off, idx)."""
-    if ws == 1:
-        return lists(tb, sb, lev, kind)
-    sc = np.array([_decode(int(k)) for k in sb]).reshape(-1, 3)
-    off, idx = [0], []
-    for k in tb:
-        c = np.array(_decode(int(k)))
-        d = np.abs(sc - c).max(1)
-        if kind == 1:
-            sel = np.nonzero(d <= ws)[0]
-        else:
-            dp = np.abs((sc >> 1) - (c >> 1)).max(1)
-            sel = np.nonzero((d > ws) & (dp <= ws))[0]
-        idx.extend(sel.tolist())
-        off.append(len(idx))
-    return np.array(off, np.int64), np.array(idx, np.int64)
+    """Uniform-tree lists with separation ws boxes (oracle.lists): near (kind 1) = source boxes
+    within ws boxes in every coordinate; far (kind 0) = source boxes farther than ws whose parents
+    are within ws of the target's parent.  CSR over the target boxes: (off, idx)."""
+    return lists(tb, sb, lev, kind, ws)
 
 
 def _me_of_points(lam, pts, q, c, p):

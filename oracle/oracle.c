@@ -637,30 +637,33 @@ static int64_t find_box(const uint64_t *boxes, int64_t nb, uint64_t key) {
   return -1;
 }
 static int fdiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
-/* Interaction lists at level lev between target boxes tb[0..nt) and source boxes sb[0..ns).
- * kind 0: far list (V): |d|_inf >= 2 and parents are neighbours (|parent offset| <= 1).
- * kind 1: near list (U): |d|_inf <= 1.
- * Offsets are visited dx outermost, then dy, then dz, each from -3 to 3.
+/* Interaction lists at level lev between target boxes tb[0..nt) and source boxes sb[0..ns), for a
+ * separation of ws boxes (ws = 1: one-box, ws = 2: two-box; the traditional FMM list rule that
+ * Sec. 3.5 builds Algorithm 1 on, with the interaction list of a box made of the children of its
+ * parent's neighbours that are not its own neighbours):
+ * kind 0: far list (V): |d|_inf > ws and the parents are within ws of each other (|parent offset|_inf <= ws).
+ * kind 1: near list (U): |d|_inf <= ws.
+ * Offsets are visited dx outermost, then dy, then dz, each ascending from -(2 ws + 1) to 2 ws + 1.
  * off[nt+1] CSR offsets, idx[] source box indices.  Returns total entries. */
-int64_t orc_lists(const uint64_t *tb, int64_t nt, const uint64_t *sb, int64_t ns, int lev, int kind, int64_t *off,
-                  int64_t *idx) {
+int64_t orc_lists(const uint64_t *tb, int64_t nt, const uint64_t *sb, int64_t ns, int lev, int kind, int ws,
+                  int64_t *off, int64_t *idx) {
   int64_t c = 0;
-  const int nc = 1 << lev;
+  const int nc = 1 << lev, R = 2 * ws + 1;
   for (int64_t t = 0; t < nt; ++t) {
     off[t] = c;
     int ix, iy, iz;
     unspread(tb[t], &ix, &iy, &iz);
-    for (int dx = -3; dx <= 3; ++dx)
-      for (int dy = -3; dy <= 3; ++dy)
-        for (int dz = -3; dz <= 3; ++dz) {
+    for (int dx = -R; dx <= R; ++dx)
+      for (int dy = -R; dy <= R; ++dy)
+        for (int dz = -R; dz <= R; ++dz) {
           const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
           if (jx < 0 || jy < 0 || jz < 0 || jx >= nc || jy >= nc || jz >= nc) continue;
           const int adist = abs(dx) > abs(dy) ? (abs(dx) > abs(dz) ? abs(dx) : abs(dz)) : (abs(dy) > abs(dz) ? abs(dy) : abs(dz));
           if (kind == 1) {
-            if (adist > 1) continue;
+            if (adist > ws) continue;
           } else {
-            if (adist < 2) continue;
-            if (abs(fdiv2(jx) - fdiv2(ix)) > 1 || abs(fdiv2(jy) - fdiv2(iy)) > 1 || abs(fdiv2(jz) - fdiv2(iz)) > 1)
+            if (adist <= ws) continue;
+            if (abs(fdiv2(jx) - fdiv2(ix)) > ws || abs(fdiv2(jy) - fdiv2(iy)) > ws || abs(fdiv2(jz) - fdiv2(iz)) > ws)
               continue;
           }
           const int64_t s = find_box(sb, ns, orc_morton(jx, jy, jz));

@@ -316,22 +316,23 @@ def test_images_across_interface_from_targets():
                     assert zi > m["d"][l - 1]
 
 
-def brute_lists(tcoords, scoords, lev, kind):
+def brute_lists(tcoords, scoords, lev, kind, ws=1):
     sset = {tuple(c): i for i, c in enumerate(scoords)}
+    R = 2 * ws + 1
     out = []
     for t in tcoords:
         row = []
-        for dx in range(-3, 4):
-            for dy in range(-3, 4):
-                for dz in range(-3, 4):
+        for dx in range(-R, R + 1):
+            for dy in range(-R, R + 1):
+                for dz in range(-R, R + 1):
                     s = (t[0] + dx, t[1] + dy, t[2] + dz)
                     if s not in sset:
                         continue
                     cheb = max(abs(dx), abs(dy), abs(dz))
                     if kind == 1:
-                        ok = cheb <= 1
+                        ok = cheb <= ws
                     else:
-                        ok = cheb >= 2 and all(abs((s[k] >> 1) - (t[k] >> 1)) <= 1 for k in range(3))
+                        ok = cheb > ws and all(abs((s[k] >> 1) - (t[k] >> 1)) <= ws for k in range(3))
                     if ok:
                         row.append(sset[s])
         out.append(row)
@@ -369,14 +370,47 @@ def test_tree_keys_and_lists_brute_force():
     tz = [c[2] for c in coords_of(tk)]
     iz = [c[2] for c in coords_of(ik)]
     assert max(tz) < (1 << (D - 1)) <= min(iz)
-    for lev in (2, 3, 4):
-        tb = oracle.level_boxes(tk, D, lev)
-        sb = oracle.level_boxes(ik, D, lev)
-        for kind in (0, 1):
-            off, idx = oracle.lists(tb, sb, lev, kind)
-            ref = brute_lists(coords_of(tb), coords_of(sb), lev, kind)
-            got = [list(idx[off[t]:off[t + 1]]) for t in range(len(tb))]
-            assert got == ref
+    for ws in (1, 2):
+        for lev in (2, 3, 4):
+            tb = oracle.level_boxes(tk, D, lev)
+            sb = oracle.level_boxes(ik, D, lev)
+            for kind in (0, 1):
+                off, idx = oracle.lists(tb, sb, lev, kind, ws)
+                ref = brute_lists(coords_of(tb), coords_of(sb), lev, kind, ws)
+                got = [list(idx[off[t]:off[t + 1]]) for t in range(len(tb))]
+                assert got == ref
+
+
+@pytest.mark.parametrize("ws", [1, 2])
+def test_lists_cover_every_leaf_pair_once(ws):
+    """With separation ws, every (target leaf, source leaf) pair of a uniform tree is handled exactly
+    once: by the near list at the leaf level, or by the far list of exactly one pair of ancestors
+    (the partition property the FMM's correctness rests on).  Brute force over random boxes."""
+    rng = np.random.default_rng(11 + ws)
+    D = 4
+    n = 1 << D
+    tc = {tuple(c) for c in rng.integers(0, n, size=(150, 3)).tolist()}
+    sc = {tuple(c) for c in rng.integers(0, n, size=(150, 3)).tolist()}
+    key = lambda c, lev: int(oracle.morton(c[0] >> (D - lev), c[1] >> (D - lev), c[2] >> (D - lev)))
+    boxes = {}
+    for lev in range(2, D + 1):
+        boxes[lev] = (np.array(sorted({key(c, lev) for c in tc}), np.uint64),
+                      np.array(sorted({key(c, lev) for c in sc}), np.uint64))
+    hits = {}
+    for lev in range(2, D + 1):
+        tb, sb = boxes[lev]
+        kinds = (0, 1) if lev == D else (0,)
+        for kind in kinds:
+            off, idx = oracle.lists(tb, sb, lev, kind, ws)
+            for t in range(len(tb)):
+                for s in idx[off[t]:off[t + 1]]:
+                    hits.setdefault((lev, int(tb[t]), int(sb[s])), 0)
+                    hits[(lev, int(tb[t]), int(sb[s]))] += 1
+    assert max(hits.values()) == 1
+    for t in tc:
+        for s in sc:
+            cover = sum((lev, key(t, lev), key(s, lev)) in hits for lev in range(2, D + 1))
+            assert cover == 1, (t, s, cover)
 
 
 def test_sommerfeld_recurrences_where_each_holds():
