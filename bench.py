@@ -105,17 +105,35 @@ def load_oracle_fixture(n, seed, workload="three_layer", path=None):
     return fx if ok else None
 
 
-def oracle_fixture_errors(sampled, fx):
-    """Relative L2 errors against the oracle at the fixture's targets; sampled maps a name to
-    (phi, field) host arrays at those targets, in the fixture's order."""
+GATE = 1e-6  # relative L2 bound of the accuracy gate (potential and field)
+
+
+def oracle_fixture_errors(sampled, fx, layers=None):
+    """Errors against the oracle at the fixture's targets; sampled maps a name to (phi, field) host
+    arrays at those targets, in the fixture's order.  Relative L2 over the sample, and with the
+    targets' layers the paper's per-layer Err_max (max |a - ref| / max |ref|, field rows as vectors);
+    "pass" when both relative L2 errors are within GATE."""
     ref_phi = np.asarray(fx["phi"], float)
     ref_fld = np.asarray(fx["field"], float)
-    out = {"targets": len(fx["targets"]),
+    out = {"targets": len(fx["targets"]), "gate": GATE,
            "sample": "%d targets per layer, drawn without replacement (seed %d); oracle direct sum, FP64"
                      % (fx["per_layer"], fx["seed"])}
     for name, (ph, fl) in sampled.items():
-        out[name] = {"relL2_phi": float(np.linalg.norm(np.asarray(ph) - ref_phi) / np.linalg.norm(ref_phi)),
-                     "relL2_field": float(np.linalg.norm(np.asarray(fl) - ref_fld) / np.linalg.norm(ref_fld))}
+        ph, fl = np.asarray(ph), np.asarray(fl)
+        r = {"relL2_phi": float(np.linalg.norm(ph - ref_phi) / np.linalg.norm(ref_phi)),
+             "relL2_field": float(np.linalg.norm(fl - ref_fld) / np.linalg.norm(ref_fld))}
+        if layers is not None:
+            lay = np.asarray(layers)
+            em_p, em_f = [], []
+            for k in np.unique(lay):
+                s = lay == k
+                em_p.append(float(np.abs(ph[s] - ref_phi[s]).max() / np.abs(ref_phi[s]).max()))
+                em_f.append(float(np.linalg.norm(fl[s] - ref_fld[s], axis=1).max() /
+                                  np.linalg.norm(ref_fld[s], axis=1).max()))
+            r["errmax_phi_per_layer"] = em_p
+            r["errmax_field_per_layer"] = em_f
+        r["pass"] = bool(r["relL2_phi"] <= GATE and r["relL2_field"] <= GATE)
+        out[name] = r
     return out
 
 
@@ -143,11 +161,12 @@ def workload_config(n, p, precision, workload="three_layer"):
                 "charges": "q~U[-1,1], uniform in the bodies r(theta) = 0.5 - a + (a/8)(35 cos^4 - 30 cos^2 + 3), "
                            "a = 0.1, 0.15, 0.05, centres z = 0.6, -0.6, -1.8, counts in the ratio 912:640:1296",
                 "precision": precision, "l2": "flushed between steps (256 MB write)",
-                "tree": "automatic depth, <=128 mean targets per leaf"}
+                "tree": "automatic depth, <=128 mean targets per leaf", "separation": "two-box interaction lists"}
     return {"workload": "three-layer screened Coulomb, N=%d, p=%d" % (n, p), "n": n, "p": p, "layers": 3,
             "interfaces": [0.0, -1.2], "eps": [1.0, 2.0, 5.0], "lambda": [0.5, 1.0, 0.8],
             "charges": "q~U[-1,1], uniform in three unit cubes (one per layer)", "precision": precision,
-            "l2": "flushed between steps (256 MB write)", "tree": "automatic depth, <=128 mean targets per leaf"}
+            "l2": "flushed between steps (256 MB write)", "tree": "automatic depth, <=128 mean targets per leaf",
+            "separation": "two-box interaction lists"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -210,6 +229,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample of the same workload, scaled to targets/s over all sources)
 # ---------------------------------------------------------------------------------------------
+CPU_SOURCE_STRIDE = 10  # the oracle's bounded sample: every 10th charge as a source
+
+
 def oracle_sample(w, n_targets, source_stride):
     import oracle
     md = oracle.Medium(**w["medium"])
@@ -235,7 +257,7 @@ def run_reference(args, rank, world):
     oracle.build()
     w = inputs.workload(args.workload, n=args.n)
     cores = oracle.num_threads()
-    nt, stride = max(2, cores), 20
+    nt, stride = max(2, cores), CPU_SOURCE_STRIDE
     for _ in range(args.warmup):
         oracle_sample(w, nt, stride)
     vals, times = [], []
@@ -248,8 +270,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": metric_of(args.workload), "value": value, "unit": "targets/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args.n, args.p, "fp64 direct sum (CPU oracle)", args.workload),
-                           l2="not applicable (host cores)"), "cpu_baseline": info,
+            "config": workload_config(args.n, args.p, "mixed", args.workload), "cpu_baseline": info,
             "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -356,8 +377,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         accuracy = {"relL2_phi_mixed_vs_fp64": float(torch.linalg.norm(phi - p64) / torch.linalg.norm(p64)),
                     "relL2_field_mixed_vs_fp64": float(torch.linalg.norm(fld - f64) / torch.linalg.norm(f64)),
-                    "gate": 1e-6,
+                    "gate": GATE,
                     "per_layer_phi": per_layer_errors(phi, p64, l, len(m["eps"]))}
+        accuracy["pass"] = bool(accuracy["relL2_phi_mixed_vs_fp64"] <= GATE and
+                                accuracy["relL2_field_mixed_vs_fp64"] <= GATE)
         ctx64.close()
 
     # both FMMs against the oracle's stored values at sampled targets (no oracle run here)
@@ -370,7 +393,7 @@ def run_ours(args, rank, world, local_rank):
                 sampled = {"mixed": (phi[idx].cpu().numpy(), fld[idx].cpu().numpy())}
                 if accuracy is not None:
                     sampled["fp64"] = (p64[idx].cpu().numpy(), f64[idx].cpu().numpy())
-                vs_oracle = oracle_fixture_errors(sampled, fx)
+                vs_oracle = oracle_fixture_errors(sampled, fx, w["layer"][np.asarray(fx["targets"])])
         except Exception as e:  # a report only: never lose the measurement line over it
             vs_oracle = {"error": repr(e)}
 
@@ -384,9 +407,18 @@ def run_ours(args, rank, world, local_rank):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock (TFLOP/s)
+    # FP32 / FP64: FMA chains timed on this device now (lpbfmm_measure_peak); TF32 tensor: the
+    # measured bf16 burst x the nominal TF32 / BF16 ratio 1.1 / 2.25; HBM: the measured copy
+    fp32_peak = F.measure_peak(F.PEAK_FP32_FMA)
+    fp64_peak = F.measure_peak(F.PEAK_FP64_FMA)
     bf16 = peaks.get("bf16_tflops")
-    tf32_peak = (bf16 if bf16 else 1900.0) * 1.1 / 2.25  # measured bf16 burst x nominal TF32/BF16 ratio
+    tf32_peak = (bf16 if bf16 else 1900.0) * 1.1 / 2.25
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    peak_info = {"fp32_fma_tflops": fp32_peak, "fp64_fma_tflops": fp64_peak, "tf32_tflops": tf32_peak,
+                 "hbm_gbs": hbm_peak, "sms": torch.cuda.get_device_properties(dev).multi_processor_count,
+                 "how": "fp32/fp64: measured FMA chains (lpbfmm_measure_peak); tf32: measured bf16 burst "
+                        "(MEASURED_PEAKS.json) x 1.1/2.25; hbm: measured copy (MEASURED_PEAKS.json)" +
+                        ("" if peaks.get("hbm_gbs") else " [fallback 6800 GB/s: file absent]")}
     per = lambda nm: phase_ms.get(nm, float("nan")) / args.steps
 
     traffic_of = profiled_traffic
@@ -409,13 +441,23 @@ def run_ours(args, rank, world, local_rank):
     if "m2l_simt" in phase_ms:
         roofs.append(roof("k_m2l_f32 (M2L, FP32 SIMT)", "alu", 4.0 * K * K * counts["m2l_react"], per("m2l_simt"),
                           fp32_peak, "4 K^2 per translation"))
+    if "tree" in phase_ms:
+        # the tree build streams the inputs once and writes every group's sorted point records:
+        # 36 B per charge read, 44 B per target or image point written (key 8, index 4, x y z q 32)
+        tb = 36.0 * n + 44.0 * (counts["targets"] + counts["images"])
+        t = per("tree")
+        a = tb / (t / 1e3) / 1e9
+        roofs.append({"kernel": "tree build (validation, keys, radix sorts, boxes, lists)", "bound": "hbm",
+                      "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak, "traffic": None,
+                      "ms_per_eval": t, "algorithmic_bytes": tb,
+                      "bytes_per_unit": "36 per charge read + 44 per sorted target or image point written"})
     roof_main = max(roofs, key=lambda r: r["ms_per_eval"]) if roofs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        v, dt, info = oracle_sample(w, max(2, oracle.num_threads()), 10)
+        v, dt, info = oracle_sample(w, max(2, oracle.num_threads()), CPU_SOURCE_STRIDE)
         info["value"] = v
         cpu = info
 
@@ -433,7 +475,7 @@ def run_ours(args, rank, world, local_rank):
                 "phases_ms_per_eval": {k: v / args.steps for k, v in phase_ms.items()}, "device_status": device_status,
                 "cpu_baseline": cpu,
                 "fp64_fmm_value": fp64_value, "accuracy": accuracy, "accuracy_vs_oracle": vs_oracle,
-                "counts": counts}
+                "counts": counts, "peaks": peak_info}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -60,16 +60,24 @@ extern "C" {
 
 typedef struct lpbfmm_ctx *lpbfmm_t;
 
+/* Separation of the interaction lists, in boxes (Sec. 3.5 builds Algorithm 1 on the traditional
+ * FMM lists: a box's multipole-to-local list holds the children of its parent's near boxes that
+ * are not near it, its near list the boxes within the separation).  1 = one-box: near boxes touch;
+ * 2 = two-box: one box lies between a box and the nearest box of its far list, so every
+ * expansion converges at a faster geometric rate at the same p (more M2L and near-field work). */
+#define LPBFMM_SEPARATION_DEFAULT 2
+
 typedef struct {
   int precision;     /* LPBFMM_FP64 or LPBFMM_MIXED                                        */
   int max_per_leaf;  /* automatic depth: smallest depth >= 2 whose mean target occupancy of
                         the non-empty leaves is <= max_per_leaf (default 128)               */
   int uniform_depth; /* > 0: use this tree depth for every target group; 0: automatic      */
-  int reserved;      /* must be 0                                                            */
+  int separation;    /* 1 or 2 boxes; 0 = LPBFMM_SEPARATION_DEFAULT                        */
   void *stream;      /* cudaStream_t for all work; NULL = the legacy default stream          */
 } lpbfmm_opts;
 
-/* Fill *opts with the defaults (FP64, max_per_leaf 128, automatic depth, default stream). */
+/* Fill *opts with the defaults (FP64, max_per_leaf 128, automatic depth, default separation,
+ * default stream). */
 void lpbfmm_default_opts(lpbfmm_opts *opts);
 
 /*
@@ -146,8 +154,8 @@ int lpbfmm_debug_tree(lpbfmm_t h, int l, int a, double *root, int64_t *n_targets
  * kind 0 = far (multipole-to-local) list, kind 1 = near list at the leaf level; src 0 = the
  * group's free-space sources (its own targets), src 1 = its images.  Host outputs in CSR form
  * over the level's target boxes (sorted by key): off[nbox+1], idx[off[nbox]] source box
- * indices, each row in the order dx, dy, dz from -3 to 3 (dx outermost).  With off == NULL
- * only *nbox and *nent are returned.
+ * indices, each row in ascending order of the offset (dx, dy, dz) with dx outermost.  With
+ * off == NULL only *nbox and *nent are returned.
  */
 int lpbfmm_debug_lists(lpbfmm_t h, int l, int a, int lev, int kind, int src, int64_t *nbox, int64_t *nent,
                        int64_t *off, int64_t *idx);
@@ -159,9 +167,11 @@ int lpbfmm_debug_lists(lpbfmm_t h, int l, int a, int lev, int kind, int src, int
  *          (lambda_l/lz_l)^i (lambda_l'/lz_l')^j d lr,         K = 0..Kmax, d = 0..K,
  * computed on the device the way the FMM computes them: quadrature for d = 0, 1 and the
  * forward recurrence in d (eq. recurrence1) for d >= 2.  Only the entries with K - d odd are
- * computed (the multipole-to-local operators use no others); the rest are 0.  zt, zs > 0 are the distances of the
- * target and source centres to the component's interface, rho = ratio * h with ratio^2 in
- * {0,1,2,4,5,8,9,10,13,18}.  out is a host array.
+ * computed (the multipole-to-local operators use no others); the rest are 0.  zt, zs > 0 are the
+ * distances of the target and source centres to the component's interface, zt = (k_t + 1/2) h and
+ * zs = (k_s + 1/2) h with integers k_t, k_s >= 0, k_t + k_s <= 4; rho = ratio * h with ratio^2 in
+ * {0,1,2,4,5,8,9,10,13,16,17,18,20,25,26,29,32,34,41,50}.  Other geometries return
+ * LPBFMM_ERR_ARG.  out is a host array.
  */
 int lpbfmm_debug_stable(lpbfmm_t h, int l, int a, int lp, int b, double hbox, double rho, double zt,
                         double zs, int Kmax, double *out);
@@ -175,10 +185,11 @@ int lpbfmm_debug_stable(lpbfmm_t h, int l, int a, int lp, int b, double hbox, do
  *         on the context's stream (the call does not synchronize), owned by the caller.
  *   Kmax  at most LPBFMM_NOALLOC_KMAX; the class's quadrature may use at most
  *         LPBFMM_NOALLOC_NQ nodes.  Larger requests return LPBFMM_ERR_UNSUPPORTED.
- * Temporaries live in one fixed device array of about 2.1 MB per device, whose address is
+ * Temporaries live in one fixed device array of about 1.8 MB per device, whose address is
  * looked up on the first call on each device: make that first call before any stream capture.
  * Calls that overlap in time on one device (other streams, other contexts) share that array
- * and race; serialize them.  Other errors as lpbfmm_debug_stable.
+ * and race; serialize them.  The context's device must be current (LPBFMM_ERR_ARG otherwise).
+ * Other errors as lpbfmm_debug_stable.
  */
 #define LPBFMM_NOALLOC_KMAX 23   /* = 2p + 3 at p = 10 */
 #define LPBFMM_NOALLOC_NQ 4096
@@ -236,11 +247,11 @@ int lpbfmm_last_profile(lpbfmm_t h, int cap, const char **names, float *ms, int 
  *                          x^{-i} sum_k c_k t^k with t = x^2 - 1, i = (n - m) mod 2.  These are the
  *                          Legendre-product expansions behind the reaction M2L operators of
  *                          Sec. 3.5 (eqs. metoletableform and the product formula before it).
- *   LPBFMM_TABLE_PHAT_DIR  P[dir][h(q,k)], q <= 2p: phat_q^k(cos theta) of the 72 translation
- *                          directions: dir = 7 ri + dz + 3 (ri indexes rho^2 in {0, 1, 2, 4, 5, 8,
- *                          9, 10, 13, 18}, dz in -3..3) with cos theta = -dz / sqrt(rho^2 + dz^2)
- *                          (1 when both vanish), and dir 70, 71 with cos theta = -1/sqrt(3),
- *                          +1/sqrt(3) (child-to-parent shifts).
+ *   LPBFMM_TABLE_PHAT_DIR  P[dir][h(q,k)], q <= 2p: phat_q^k(cos theta) of the 222 translation
+ *                          directions: dir = 11 ri + dz + 5 (ri indexes rho^2 in {0, 1, 2, 4, 5, 8,
+ *                          9, 10, 13, 16, 17, 18, 20, 25, 26, 29, 32, 34, 41, 50}, dz in -5..5) with
+ *                          cos theta = -dz / sqrt(rho^2 + dz^2) (1 when both vanish), and dir 220,
+ *                          221 with cos theta = -1/sqrt(3), +1/sqrt(3) (child-to-parent shifts).
  *   LPBFMM_TABLE_SFAC      s[K][d], K, d < 36 (row stride 36): sqrt((K+d)! (K-d)!) for d <= K, else
  *                          0; the normalization of the Sommerfeld-type integrals (Sec. 3.5, eq.
  *                          M2Ltable).  Independent of p.
@@ -249,6 +260,18 @@ int lpbfmm_last_profile(lpbfmm_t h, int cap, const char **names, float *ms, int 
  * short buffer, LPBFMM_ERR_P for p outside [LPBFMM_P_MIN, LPBFMM_P_MAX], LPBFMM_ERR_OOM if host
  * memory runs out.
  */
+/*
+ * Measured arithmetic peak of the current device for the rooflines of the library's SIMT kernels
+ * (not part of the method): chains of fused multiply-adds, 8 independent chains per thread and 64
+ * resident warps per SM, timed with CUDA events on a stream of its own after a warm-up.
+ * which = LPBFMM_PEAK_FP32_FMA or LPBFMM_PEAK_FP64_FMA; *tflops receives 2 x FMAs per second / 1e12.
+ * Runs for some tens of milliseconds; allocates 8 bytes of device memory.  LPBFMM_ERR_ARG for a
+ * null pointer or an unknown which.
+ */
+#define LPBFMM_PEAK_FP32_FMA 0
+#define LPBFMM_PEAK_FP64_FMA 1
+int lpbfmm_measure_peak(int which, double *tflops);
+
 #define LPBFMM_TABLE_GAUNT 0
 #define LPBFMM_TABLE_TPOLY 1
 #define LPBFMM_TABLE_PHAT_DIR 2

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblpbfmm.so")
-SOURCES = ["api.cu", "tree.cu", "ops.cu", "fmm.cu"]
+SOURCES = ["api.cu", "tree.cu", "ops.cu", "fmm.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -81,23 +81,22 @@ static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w
 // G[a][c][q] = int Y_a^alpha Y_q^{gamma-alpha} conj(Y_c^gamma) dOmega (all real), full indices a, c
 // sqrt((K+d)! (K-d)!) for 0 <= d <= K <= KMAX_TAB, the normalisation of the scaled
 // Sommerfeld tables (long double products, then rounded once)
-// Phat_q^k(cos theta), q <= 2p, of the 72 translation directions: the free-space M2L classes
-// (rho^2 index ri, dz) at index ri * 7 + dz + 3, b = (rho, 0, -dz), and the child-parent
-// directions b = (1, 1, -1) / (1, 1, 1) (index 70, 71).  Orthonormal, Condon-Shortley phase,
-// by the standard three-term recurrences in long double.
+// Phat_q^k(cos theta), q <= 2p, of the NDIR translation directions: the free-space M2L classes
+// (rho^2 index ri, dz) at index ri * NDZ + dz + OFF_R, b = (rho, 0, -dz), and the child-parent
+// directions b = (1, 1, -1) / (1, 1, 1) (index NFREE_CLS, NFREE_CLS + 1).  Orthonormal,
+// Condon-Shortley phase, by the standard three-term recurrences in long double.
 static std::vector<double> phat_dir_table(int p) {
   const int qmax = 2 * p, npl = (qmax + 1) * (qmax + 2) / 2;
-  const long double rho2[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
-  std::vector<double> out((size_t)72 * npl, 0.0);
+  std::vector<double> out((size_t)NDIR * npl, 0.0);
   auto idx = [](int q, int k) { return q * (q + 1) / 2 + k; };
-  for (int dir = 0; dir < 72; ++dir) {
+  for (int dir = 0; dir < NDIR; ++dir) {
     long double x;
-    if (dir < 70) {
-      const int ri = dir / 7, dz = dir % 7 - 3;
-      const long double bz = -dz, bn = sqrtl(rho2[ri] + (long double)dz * dz);
+    if (dir < NFREE_CLS) {
+      const int ri = dir / NDZ, dz = dir % NDZ - OFF_R;
+      const long double bz = -dz, bn = sqrtl((long double)rho2_of(ri) + (long double)dz * dz);
       x = bn > 0 ? bz / bn : 1.0L;
     } else {
-      x = (dir == 70 ? -1.0L : 1.0L) / sqrtl(3.0L);
+      x = (dir == NFREE_CLS ? -1.0L : 1.0L) / sqrtl(3.0L);
     }
     std::vector<long double> P(npl, 0.0L);
     const long double s = sqrtl(fmaxl(0.0L, 1.0L - x * x));
@@ -331,6 +330,7 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     }
   }
   for (auto &g : c.groups) build_group_lists(c, g, parts);
+  prof_mark(c, "tree");
   {
     double lmin = 1e300, hmin = 1e300;
     for (int k = 0; k <= L; ++k) lmin = std::min(lmin, c.md.lam[k]);
@@ -352,10 +352,10 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
           zs = std::min(zs, std::fabs(image_z(md, g.l, g.a, lp, b, zhi[lp]) - g.dI));
         }
       }
-      build_near_nodes(c, g, std::max(zt + zs, 1e-12), 2.0 * std::sqrt(2.0) * g.h(g.D));
+      build_near_nodes(c, g, std::max(zt + zs, 1e-12), (c.ws + 1) * std::sqrt(2.0) * g.h(g.D));
     }
   }
-  prof_mark(c, "tree+ops");
+  prof_mark(c, "tables+ops");
   run_fmm_all(c, c.groups, parts, phi, field);
   prof_mark(c, "end");
 }
@@ -379,7 +379,7 @@ void lpbfmm_default_opts(lpbfmm_opts *o) {
   o->precision = LPBFMM_FP64;
   o->max_per_leaf = 128;
   o->uniform_depth = 0;
-  o->reserved = 0;
+  o->separation = 0;
   o->stream = nullptr;
 }
 
@@ -401,7 +401,7 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
   lpbfmm_default_opts(&o);
   if (opts) o = *opts;
   if ((o.precision != LPBFMM_FP64 && o.precision != LPBFMM_MIXED) || o.max_per_leaf < 0 || o.uniform_depth < 0 ||
-      o.uniform_depth > DMAX || o.reserved != 0)
+      o.uniform_depth > DMAX || o.separation < 0 || o.separation > WS_MAX)
     return LPBFMM_ERR_ARG;
   lpbfmm_ctx *c = new (std::nothrow) lpbfmm_ctx();
   if (!c) return LPBFMM_ERR_OOM;
@@ -412,6 +412,7 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     for (int k = 0; k <= n_iface; ++k) { c->md.eps[k] = eps[k]; c->md.lam[k] = lambda[k]; }
     c->p = p;
     c->K = (p + 1) * (p + 2) / 2;
+    c->ws = o.separation ? o.separation : LPBFMM_SEPARATION_DEFAULT;
     c->tol = tol;
     c->opts = o;
     c->stream = (cudaStream_t)o.stream;
@@ -676,8 +677,8 @@ int lpbfmm_debug_array(lpbfmm_t h, int l, int a, const char *name, int lev, void
   else if (nm == "vreact") { src = g->vreact[lev]; nb = ntb * NOFF * 4; }
   else if (nm == "ikeys") { src = g->I.lev[lev].key; nb = nib * 8; }
   else if (nm == "tkeys") { src = g->T.lev[lev].key; nb = ntb * 8; }
-  else if (nm == "rows") { src = g->rows[lev]; nb = 3 * ntb * 4; }
-  else if (nm == "nrows") { src = g->nrows[lev]; nb = 12; }
+  else if (nm == "rows") { src = g->rows[lev]; nb = (size_t)NKT * ntb * 4; }
+  else if (nm == "nrows") { src = g->nrows[lev]; nb = NKT * 4; }
   else return LPBFMM_ERR_ARG;
   *bytes = (int64_t)nb;
   if (!dst || !src) return src ? LPBFMM_OK : LPBFMM_ERR_ARG;
@@ -697,9 +698,9 @@ __global__ void k_count_near(const int32_t *u, int64_t nb, const uint32_t *tcnt,
                              unsigned long long *out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long v = 0;
-  if (i < nb * 27) {
+  if (i < nb * NNEAR) {
     const int32_t s = u[i];
-    if (s >= 0) v = (unsigned long long)tcnt[i / 27] * scnt[s];
+    if (s >= 0) v = (unsigned long long)tcnt[i / NNEAR] * scnt[s];
   }
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
@@ -722,10 +723,10 @@ int lpbfmm_last_counts(lpbfmm_t h, int64_t *out) {
       }
       const int64_t nb = g.T.lev[g.D].n;
       if (g.ufree)
-        k_count_near<<<(unsigned)((nb * 27 + 255) / 256), 256, 0, h->stream>>>(g.ufree, nb, g.T.lev[g.D].count,
+        k_count_near<<<(unsigned)((nb * NNEAR + 255) / 256), 256, 0, h->stream>>>(g.ufree, nb, g.T.lev[g.D].count,
                                                                               g.T.lev[g.D].count, d + 2);
       if (g.ureact)
-        k_count_near<<<(unsigned)((nb * 27 + 255) / 256), 256, 0, h->stream>>>(g.ureact, nb, g.T.lev[g.D].count,
+        k_count_near<<<(unsigned)((nb * NNEAR + 255) / 256), 256, 0, h->stream>>>(g.ureact, nb, g.T.lev[g.D].count,
                                                                               g.I.lev[g.D].count, d + 3);
     }
     LPB_CUDA(cudaGetLastError());

@@ -304,7 +304,7 @@ __global__ void k_l2l(const uint32_t *d_nc, const uint32_t *cparent, const uint6
 
 // ---------------------------------------------------------------------------------------
 // M2L: one launch for every (group, level, free / reaction row) job.  A work item is
-// (job, tile of target boxes, slice dx of the 343 offsets).  For every offset of its slice
+// (job, tile of target boxes, slice dx of the NOFF offsets).  For every offset of its slice
 // the class operator (P, Q) and the phase-rotated multipoles of the tile's sources are staged
 // in shared memory in K-chunks and multiplied as a small GEMM (rows = output coefficients,
 // columns = target boxes); each target's partial local expansion of the slice is written to
@@ -312,7 +312,7 @@ __global__ void k_l2l(const uint32_t *d_nc, const uint32_t *cparent, const uint6
 // result does not depend on scheduling.  (FP64 mode and p > 10; the mixed mode uses k_m2l_tc.)
 // ---------------------------------------------------------------------------------------
 constexpr int M2L_KC = 32;
-constexpr int M2L_NSLICE = 7;  // offsets with dx = -3..3, 49 each
+constexpr int M2L_NSLICE = NSLICE;  // offsets with dx = -OFF_R..OFF_R, SLICE_OFFS each
 
 struct XJob {
   const int32_t *tlist;   // target box indices (nullptr: 0..ntb-1)
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const 
   const size_t KK = (size_t)K * K;
   bool any = false;
   __syncthreads();
-  for (int o = slice * 49; o < slice * 49 + 49; ++o) {
+  for (int o = slice * SLICE_OFFS; o < slice * SLICE_OFFS + SLICE_OFFS; ++o) {
     const int cls = J.cls_of[o];
     if (cls < 0) continue;
     int has = 0;
@@ -487,7 +487,8 @@ __global__ void __launch_bounds__(256) k_m2l(const XJob *jobs, int njobs, const 
 // the multipoles are rotated by e^{i mu phi} in place; the product is rotated by e^{-i m phi}
 // into the register accumulators, which are written to the slice's partial slots at the end.
 constexpr int F32_TPT = 6, F32_TT = 16 * F32_TPT, F32_NR = 5, F32_KR = 16 * F32_NR;
-constexpr int F32_MAXSTEP = 49 * 2 * MAXLAYER;
+constexpr int F32_MAXSTEP = SLICE_OFFS * 2 * (MAXLAYER - 1);  // offsets x source types (2L, L <= 8)
+constexpr int HASW = (SLICE_OFFS + 31) / 32;  // words of a per-slice offset mask
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(256, 1) k_m2l_f32(const XJob *jobs, int njobs,
   int *mofs = srcs + 2 * F32_TT;              // [KR] m of each half-representation index
   float *rotc = (float *)(mofs + F32_KR);     // [2][PMAX+1][2]
   __shared__ int nsteps;
-  __shared__ unsigned hasmask[2];
+  __shared__ unsigned hasmask[HASW];
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(256, 1) k_m2l_f32(const XJob *jobs, int njobs,
   const size_t KK = (size_t)K * K;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   if (threadIdx.x < F32_TT) tid_[threadIdx.x] = m2l_target(J, ti, threadIdx.x, F32_TT, ntl);
-  if (threadIdx.x < 2) hasmask[threadIdx.x] = 0u;
+  if (threadIdx.x < HASW) hasmask[threadIdx.x] = 0u;
   if (threadIdx.x < F32_KR) mofs[threadIdx.x] = threadIdx.x < K ? cK.mof[threadIdx.x] : 0;
   // zero the operator padding rows K..KR-1 of both stages once
   for (int s2 = 0; s2 < 2; ++s2)
@@ -554,17 +555,17 @@ __global__ void __launch_bounds__(256, 1) k_m2l_f32(const XJob *jobs, int njobs,
   if (threadIdx.x < F32_TT) {
     const int t = tid_[threadIdx.x];
     if (t >= 0)
-      for (int k = 0; k < 49; ++k) {
-        const int o = slice * 49 + k;
+      for (int k = 0; k < SLICE_OFFS; ++k) {
+        const int o = slice * SLICE_OFFS + k;
         if (J.cls_of[o] >= 0 && J.vlist[(size_t)t * NOFF + o] >= 0) atomicOr(&hasmask[k >> 5], 1u << (k & 31));
       }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int n = 0;
-    for (int k = 0; k < 49; ++k)
+    for (int k = 0; k < SLICE_OFFS; ++k)
       if (hasmask[k >> 5] & (1u << (k & 31)))
-        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * 49 + k) << 4) | tau;
+        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * SLICE_OFFS + k) << 4) | tau;
     nsteps = n;
   }
   __syncthreads();
@@ -1025,10 +1026,23 @@ __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, con
 }
 
 // One warp per (target leaf, half) and no block-wide barriers: warp h of a leaf takes the
-// targets 128 i + 64 h + lane + 32 t (t = 0, 1) and streams the sources of the 27 neighbours
-// through its own double-buffered chunks of P2P_WSRC records.  Two warps per leaf and an
-// 80-register budget keep 24 warps resident per SM.
+// targets 128 i + 64 h + lane + 32 t (t = 0, 1) and streams the sources of the leaf's near boxes
+// through its own double-buffered chunks of P2P_WSRC records.  The near boxes are compacted to the
+// non-empty ones first; a chunk is (near box k, offset within it), walked by a cursor.  Two warps
+// per leaf and an 80-register budget keep 24 warps resident per SM.
 constexpr int P2P_WARPS = 4, P2P_WSRC = 64;
+
+struct P2PCursor {
+  int k;
+  uint32_t off;
+};
+__device__ __forceinline__ void p2p_next(P2PCursor &c, const uint32_t *nb_cnt) {
+  c.off += P2P_WSRC;
+  if (c.off >= nb_cnt[c.k]) {
+    ++c.k;
+    c.off = 0;
+  }
+}
 
 template <int NT>
 __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tcnt, uint32_t tst,
@@ -1036,8 +1050,7 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
                                               const uint32_t *src, float hh, float hl, float lam, double scale,
                                               double *phi, double *field, float4 (*sh)[P2P_WSRC],
                                               float4 (*sl)[P2P_WSRC], const uint32_t *nb_start,
-                                              const uint32_t *nb_cnt, const uint32_t *ch_pre, const int (*nb_d)[3],
-                                              int nch) {
+                                              const uint32_t *nb_cnt, const int *nb_o, int nch) {
   float th[2][3], tl[2][3];
   uint32_t tk[2];
   bool tv[2];
@@ -1050,17 +1063,9 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
     th[t][0] = a.x; th[t][1] = a.y; th[t][2] = a.z;
     tl[t][0] = b.x; tl[t][1] = b.y; tl[t][2] = b.z;
   }
-  auto chunk = [&](int c, int &o, uint32_t &first, int &nn) {
-    o = 0;
-    while ((int)ch_pre[o + 1] <= c) ++o;
-    const uint32_t off = (uint32_t)(c - (int)ch_pre[o]) * P2P_WSRC;
-    first = nb_start[o] + off;
-    nn = (int)min((uint32_t)P2P_WSRC, nb_cnt[o] - off);
-  };
-  auto issue = [&](int c, int buf) {
-    int o, nn;
-    uint32_t first;
-    chunk(c, o, first, nn);
+  auto issue = [&](const P2PCursor &cc, int buf) {
+    const uint32_t first = nb_start[cc.k] + cc.off;
+    const int nn = (int)min((uint32_t)P2P_WSRC, nb_cnt[cc.k] - cc.off);
     for (int e = lane; e < 2 * P2P_WSRC; e += 32) {
       const int j = e >> 1;
       if (j < nn) {
@@ -1072,21 +1077,27 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
   };
   float sp[2] = {0, 0}, cp[2] = {0, 0}, sx[2] = {0, 0}, cx[2] = {0, 0};
   float sy[2] = {0, 0}, cy[2] = {0, 0}, sz[2] = {0, 0}, cz[2] = {0, 0};
-  if (nch > 0) issue(0, 0);
+  P2PCursor ci{0, 0u}, cc{0, 0u};  // next chunk to issue, chunk being summed
+  if (nch > 0) {
+    issue(ci, 0);
+    p2p_next(ci, nb_cnt);
+  }
   for (int c = 0; c < nch; ++c) {
     const int buf = c & 1;
     if (c + 1 < nch) {
-      issue(c + 1, buf ^ 1);
+      issue(ci, buf ^ 1);
+      p2p_next(ci, nb_cnt);
       cp_wait1();
     } else {
       cp_wait0();
     }
     __syncwarp();
-    int o, nn;
-    uint32_t first;
-    chunk(c, o, first, nn);
+    const int nn = (int)min((uint32_t)P2P_WSRC, nb_cnt[cc.k] - cc.off);
+    int ddx, ddy, ddz;
+    near_decode(nb_o[cc.k], ddx, ddy, ddz);
+    p2p_next(cc, nb_cnt);
     float px[4], py[4], pz[4], qx[4], qy[4], qz[4];
-    const float dxh = -(float)nb_d[o][0], dyh = -(float)nb_d[o][1], dzh = -(float)nb_d[o][2];
+    const float dxh = -(float)ddx, dyh = -(float)ddy, dzh = -(float)ddz;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       two_sum_shift(th[t][0], tl[t][0], dxh * hh, dxh * hl, px[t], qx[t]);
@@ -1124,49 +1135,43 @@ __global__ void __launch_bounds__(32 * P2P_WARPS, 6) k_p2p_free_f32(const uint32
                                                                     float hl, float lam, double scale, double *phi,
                                                                     double *field) {
   __shared__ __align__(16) float4 sh_[P2P_WARPS][2][P2P_WSRC], sl_[P2P_WARPS][2][P2P_WSRC];
-  __shared__ uint32_t nb_start_[P2P_WARPS][NNEAR], nb_cnt_[P2P_WARPS][NNEAR], ch_pre_[P2P_WARPS][NNEAR + 1];
-  __shared__ int nb_d_[P2P_WARPS][NNEAR][3];
+  __shared__ uint32_t nb_start_[P2P_WARPS][NNEAR], nb_cnt_[P2P_WARPS][NNEAR];
+  __shared__ int nb_o_[P2P_WARPS][NNEAR];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t gw = blockIdx.x * P2P_WARPS + w;
   const uint32_t box = gw >> 1, half = gw & 1;
   if (box >= *d_nb) return;
   const uint32_t tst = bstart[box], tcnt = bcount[box];
   if (64 * half >= tcnt) return;
-  uint32_t *nb_start = nb_start_[w], *nb_cnt = nb_cnt_[w], *ch_pre = ch_pre_[w];
-  int(*nb_d)[3] = nb_d_[w];
-  if (lane < NNEAR) {
-    const int o = lane;
-    const int sb = ulist[(size_t)box * NNEAR + o];
-    const uint64_t kt = bkey[box];
-    nb_start[o] = sb < 0 ? 0u : bstart[sb];
-    nb_cnt[o] = sb < 0 ? 0u : bcount[sb];
-    if (sb >= 0) {
-      const uint64_t ks = bkey[sb];
-      nb_d[o][0] = (int)compact3_(ks >> 2) - (int)compact3_(kt >> 2);
-      nb_d[o][1] = (int)compact3_(ks >> 1) - (int)compact3_(kt >> 1);
-      nb_d[o][2] = (int)compact3_(ks) - (int)compact3_(kt);
-    } else {
-      nb_d[o][0] = nb_d[o][1] = nb_d[o][2] = 0;
+  uint32_t *nb_start = nb_start_[w], *nb_cnt = nb_cnt_[w];
+  int *nb_o = nb_o_[w];
+  // compact the non-empty near boxes (slot order kept) and count their chunks
+  int nnb = 0, nch = 0;
+  for (int o0 = 0; o0 < NNEAR; o0 += 32) {
+    const int o = o0 + lane;
+    const int sb = o < NNEAR ? ulist[(size_t)box * NNEAR + o] : -1;
+    const uint32_t cnt = sb >= 0 ? bcount[sb] : 0u;
+    const unsigned m = __ballot_sync(0xffffffffu, cnt > 0);
+    if (cnt > 0) {
+      const int k = nnb + __popc(m & ((1u << lane) - 1u));
+      nb_start[k] = bstart[sb];
+      nb_cnt[k] = cnt;
+      nb_o[k] = o;
     }
+    nnb += __popc(m);
+    int ch = (int)((cnt + P2P_WSRC - 1) / P2P_WSRC);
+#pragma unroll
+    for (int s2 = 16; s2; s2 >>= 1) ch += __shfl_xor_sync(0xffffffffu, ch, s2);
+    nch += ch;
   }
   __syncwarp();
-  if (lane == 0) {
-    uint32_t acc = 0;
-    for (int o = 0; o < NNEAR; ++o) {
-      ch_pre[o] = acc;
-      acc += (nb_cnt[o] + P2P_WSRC - 1) / P2P_WSRC;
-    }
-    ch_pre[NNEAR] = acc;
-  }
-  __syncwarp();
-  const int nch = (int)ch_pre[NNEAR];
   for (uint32_t t0 = 64 * half; t0 < tcnt; t0 += 128) {
     if (tcnt - t0 > 32)
       p2p_warp_pass<2>(lane, t0, tcnt, tst, h4, l4, src, hh, hl, lam, scale, phi, field, sh_[w], sl_[w], nb_start,
-                       nb_cnt, ch_pre, nb_d, nch);
+                       nb_cnt, nb_o, nch);
     else
       p2p_warp_pass<1>(lane, t0, tcnt, tst, h4, l4, src, hh, hl, lam, scale, phi, field, sh_[w], sl_[w], nb_start,
-                       nb_cnt, ch_pre, nb_d, nch);
+                       nb_cnt, nb_o, nch);
   }
 }
 
@@ -1261,7 +1266,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_react(
 // driver for one group
 // ---------------------------------------------------------------------------------------
 struct Tables {
-  int32_t *cls_free, *cls_react;  // [343], [2][3][343]
+  int32_t *cls_free, *cls_react;  // [NOFF], [2][NKT][NOFF]
   void *rot, *rot4;               // per precision
 };
 Tables g_tab_d[LPB_MAX_DEVICES], g_tab_f[LPB_MAX_DEVICES];  // per device
@@ -1269,24 +1274,21 @@ static std::atomic<uint64_t> g_tab_ready{0};
 
 static void make_tables(Ctx &c) {
   if (!not_done_on_device(g_tab_ready)) return;
-  std::vector<int32_t> cf(NOFF, -1), cr(2 * 3 * NOFF, -1);
-  const int r2v[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
-  auto rho_idx = [&](int dx, int dy) {
-    for (int k = 0; k < NRHO; ++k)
-      if (r2v[k] == dx * dx + dy * dy) return k;
-    return -1;
-  };
-  const int kkt[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
+  // operator class of every offset that can appear in a far list (|d|_inf >= 2); which offsets
+  // do appear is decided by the list builder for the context's separation
+  std::vector<int32_t> cf(NOFF, -1), cr(2 * NKT * NOFF, -1);
   std::vector<double> rot(NOFF * (PMAX + 1) * 2), rot4(4 * (PMAX + 1) * 2);
   for (int o = 0; o < NOFF; ++o) {
-    const int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
-    const int cheb = std::max(abs(dx), std::max(abs(dy), abs(dz)));
-    if (cheb >= 2) cf[o] = rho_idx(dx, dy) * 7 + dz + 3;
+    int dx, dy, dz;
+    off_decode(o, dx, dy, dz);
+    const int cheb = cheb3(dx, dy, dz);
+    if (cheb >= 2) cf[o] = rho_index(dx, dy) * NDZ + dz + OFF_R;
     for (int a = 1; a <= 2; ++a)
-      for (int kt = 0; kt < 3; ++kt) {
+      for (int kt = 0; kt < NKT; ++kt) {
         const int ks = (a == 1) ? -dz - 1 - kt : dz - 1 - kt;
-        if (cheb < 2 || ks < 0 || kt + ks > 2) continue;
-        cr[((a - 1) * 3 + kt) * NOFF + o] = rho_idx(dx, dy) * NKK + kkt[kt][ks];
+        const int kk = kk_index(kt, ks);
+        if (cheb < 2 || kk < 0) continue;
+        cr[((a - 1) * NKT + kt) * NOFF + o] = rho_index(dx, dy) * NKK + kk;
       }
     const double ph = (dx == 0 && dy == 0) ? 0.0 : atan2(-(double)dy, -(double)dx);
     for (int m = 0; m <= PMAX; ++m) {
@@ -1304,9 +1306,9 @@ static void make_tables(Ctx &c) {
   }
   int32_t *dcf, *dcr;
   LPB_CUDA(cudaMalloc(&dcf, sizeof(int32_t) * NOFF));
-  LPB_CUDA(cudaMalloc(&dcr, sizeof(int32_t) * 6 * NOFF));
+  LPB_CUDA(cudaMalloc(&dcr, sizeof(int32_t) * 2 * NKT * NOFF));
   LPB_CUDA(cudaMemcpy(dcf, cf.data(), sizeof(int32_t) * NOFF, cudaMemcpyHostToDevice));
-  LPB_CUDA(cudaMemcpy(dcr, cr.data(), sizeof(int32_t) * 6 * NOFF, cudaMemcpyHostToDevice));
+  LPB_CUDA(cudaMemcpy(dcr, cr.data(), sizeof(int32_t) * 2 * NKT * NOFF, cudaMemcpyHostToDevice));
   std::vector<float> rotf(rot.begin(), rot.end()), rot4f(rot4.begin(), rot4.end());
   void *rd, *r4d, *rf, *r4f;
   LPB_CUDA(cudaMalloc(&rd, sizeof(double) * rot.size()));
@@ -1438,7 +1440,7 @@ struct TJob {
   const uint64_t *ckey;
   int64_t npar;
 };
-constexpr int TC_MAXSTEP = 49 * 2 * MAXLAYER;
+constexpr int TC_MAXSTEP = SLICE_OFFS * 2 * (MAXLAYER - 1);
 
 constexpr int TC_ROWS = 128, TC_WORKERS = 256, TC_THREADS = TC_WORKERS + 32;
 constexpr int TC_WAIT = 1 << 22;  // mbarrier polls before the kernel reports a timeout
@@ -1459,7 +1461,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   __shared__ int steps[TC_MAXSTEP];  // (offset << 4) | source type
   __shared__ int remap_s[N], mcol[N];  // coordinate -> half index code; m of that coefficient
   __shared__ int nsteps;
-  __shared__ unsigned hasmask[2];
+  __shared__ unsigned hasmask[HASW];
   // full[b]: the workers have staged buffer b (TC_WORKERS arrivals); empty[b]: its MMAs are done;
   // accbar[a]: a step's MMAs into accumulator a are done; foldbar[a]: the workers have read it
   __shared__ uint64_t full[NST], empty[NST], accbar[2], foldbar[2];
@@ -1478,7 +1480,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   // worker thread (tid < TC_WORKERS) = (row, half): row = target slot and TMEM lane, half = which
   // 4 of a chunk's 8 units and which half of the accumulator columns it handles; the last warp
   // issues the MMAs (lane 0)
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, row = tid & (TC_ROWS - 1), hf = (tid >> 7) & 1;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (TC_ROWS - 1), hf = (tid >> 7) & 1;
   const bool worker = tid < TC_WORKERS;
   const int ntypes = J.ntypes;
   for (int c = tid; c < N; c += TC_THREADS) {
@@ -1505,22 +1507,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     }
     tid_[tid] = t;
   }
-  if (tid < 2) hasmask[tid] = 0u;
+  if (tid < HASW) hasmask[tid] = 0u;
   __syncthreads();
   if (tid < TC_ROWS) {
     const int t = tid_[tid];
     if (t >= 0)
-      for (int k = 0; k < 49; ++k) {
-        const int o = slice * 49 + k;
+      for (int k = 0; k < SLICE_OFFS; ++k) {
+        const int o = slice * SLICE_OFFS + k;
         if (J.cls_of[o] >= 0 && J.vlist[(size_t)t * NOFF + o] >= 0) atomicOr(&hasmask[k >> 5], 1u << (k & 31));
       }
   }
   __syncthreads();
   if (tid == 0) {
     int n = 0;
-    for (int k = 0; k < 49; ++k)
+    for (int k = 0; k < SLICE_OFFS; ++k)
       if (hasmask[k >> 5] & (1u << (k & 31)))
-        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * 49 + k) << 4) | tau;
+        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * SLICE_OFFS + k) << 4) | tau;
     nsteps = n;
   }
   __syncthreads();
@@ -1892,10 +1894,10 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
             (const float2 *)g.Mimg[l], nir, c.K, c.p, N, raw);
         LPB_LAUNCH();
         c.launches++;
-        for (int kt = 0; kt < 3; ++kt) {
+        for (int kt = 0; kt < 2 * c.ws + 1; ++kt) {
           TJob j;
           j.raw = raw; j.whi = whi; j.wlo = wlo; j.rot = (const float *)tb.rot;
-          j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF;
+          j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * NKT + kt) * NOFF;
           j.tlist = g.rows[l] + (size_t)kt * ntb; j.d_ntl = g.nrows[l] + kt;
           j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = M2L_NSLICE; j.ntypes = g.ntypes;
           j.pstart = nullptr; j.pcount = nullptr; j.ckey = nullptr; j.npar = 0;
@@ -1903,9 +1905,9 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
           tjobs.push_back(j);
         }
       } else if (react_far && g.vreact[l]) {
-        for (int kt = 0; kt < 3; ++kt)
+        for (int kt = 0; kt < 2 * c.ws + 1; ++kt)
           add(g.rows[l] + (size_t)kt * ntb, g.nrows[l] + kt, ntb, g.vreact[l],
-              tb.cls_react + ((g.a - 1) * 3 + kt) * NOFF, g.Mimg[l], g.op_react[l], part, g.ntypes, M2L_NSLICE,
+              tb.cls_react + ((g.a - 1) * NKT + kt) * NOFF, g.Mimg[l], g.op_react[l], part, g.ntypes, M2L_NSLICE,
               nullptr, nullptr);
       }
     }

@@ -14,13 +14,72 @@
 namespace lpb {
 
 constexpr int DMAX = 10;      // Morton keys are built at this depth (30 bits)
-constexpr int NOFF = 343;     // offsets (dx,dy,dz) in [-3,3]^3, index ((dx+3)*7+(dy+3))*7+(dz+3)
-constexpr int NNEAR = 27;     // offsets in [-1,1]^3
-constexpr int NHDIR = 49;     // horizontal directions (dx,dy) in [-3,3]^2
-constexpr int NRHO = 10;      // distinct dx^2+dy^2 values {0,1,2,4,5,8,9,10,13,18}
-constexpr int NFREE_CLS = NRHO * 7;       // free-space M2L classes (rho^2, dz)
-constexpr int NKK = 6;                    // (k_t, k_s) with k_t + k_s <= 2
-constexpr int NREACT_CLS = NRHO * NKK;    // reaction M2L classes (rho^2, k_t, k_s)
+
+// Interaction lists of a uniform tree with a separation of ws boxes (1 <= ws <= WS_MAX): the near
+// list holds the source boxes within ws boxes in every coordinate, the far (multipole-to-local)
+// list the children of the parent's near boxes that are not near themselves, at offsets
+// (dx, dy, dz) in [-(2 ws + 1), 2 ws + 1]^3.  Slots are laid out for WS_MAX whatever ws is.
+constexpr int WS_MAX = 2;
+constexpr int OFF_R = 2 * WS_MAX + 1;       // far offsets lie in [-OFF_R, OFF_R]^3
+constexpr int OFF_D = 2 * OFF_R + 1;
+constexpr int NOFF = OFF_D * OFF_D * OFF_D;  // far slots, index ((dx+R) D + (dy+R)) D + (dz+R)
+constexpr int NSLICE = OFF_D;               // M2L work is split by dx
+constexpr int SLICE_OFFS = OFF_D * OFF_D;   // offsets of one dx-slice
+constexpr int NEAR_D = 2 * WS_MAX + 1;
+constexpr int NNEAR = NEAR_D * NEAR_D * NEAR_D;  // near slots, index ((dx+W) E + (dy+W)) E + (dz+W)
+constexpr int NRHO = 20;                    // distinct dx^2 + dy^2 for |dx|, |dy| <= OFF_R
+constexpr int NDZ = OFF_D;
+constexpr int NFREE_CLS = NRHO * NDZ;       // free-space M2L classes (rho^2, dz)
+constexpr int NDIR = NFREE_CLS + 2;         // operator directions: the classes, then child -> parent
+constexpr int NKT = 2 * WS_MAX + 1;         // reaction rows k_t (box distance to the interface)
+constexpr int NKK = NKT * (NKT + 1) / 2;    // (k_t, k_s) with k_t + k_s < NKT
+constexpr int NREACT_CLS = NRHO * NKK;      // reaction M2L classes (rho^2, k_t, k_s)
+
+LPB_HD int rho2_of(int ri) {
+  constexpr int t[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 16, 17, 18, 20, 25, 26, 29, 32, 34, 41, 50};
+  return t[ri];
+}
+LPB_HD int rho_index(int dx, int dy) {
+  const int r2 = dx * dx + dy * dy;
+  for (int k = 0; k < NRHO; ++k)
+    if (rho2_of(k) == r2) return k;
+  return -1;
+}
+// (k_t, k_s) ordered by k_t + k_s, then k_t
+LPB_HD int kk_index(int kt, int ks) {
+  const int s = kt + ks;
+  if (kt < 0 || ks < 0 || s >= NKT) return -1;
+  return s * (s + 1) / 2 + kt;
+}
+LPB_HD void kk_decode(int kk, int &kt, int &ks) {
+  int s = 0;
+  while ((s + 1) * (s + 2) / 2 <= kk) ++s;
+  kt = kk - s * (s + 1) / 2;
+  ks = s - kt;
+}
+LPB_HD int off_index(int dx, int dy, int dz) { return ((dx + OFF_R) * OFF_D + (dy + OFF_R)) * OFF_D + dz + OFF_R; }
+LPB_HD void off_decode(int o, int &dx, int &dy, int &dz) {
+  dx = o / (OFF_D * OFF_D) - OFF_R;
+  dy = (o / OFF_D) % OFF_D - OFF_R;
+  dz = o % OFF_D - OFF_R;
+}
+LPB_HD void near_decode(int o, int &dx, int &dy, int &dz) {
+  dx = o / (NEAR_D * NEAR_D) - WS_MAX;
+  dy = (o / NEAR_D) % NEAR_D - WS_MAX;
+  dz = o % NEAR_D - WS_MAX;
+}
+LPB_HD int cheb3(int dx, int dy, int dz) {
+  const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+  return ax > ay ? (ax > az ? ax : az) : (ay > az ? ay : az);
+}
+// does some offset (dx, dy, dz) of the free-space class (rho^2 index ri, dz) lie in a far list of
+// separation ws?
+LPB_HD bool free_class_is_far(int ri, int dz, int ws) {
+  for (int dx = -OFF_R; dx <= OFF_R; ++dx)
+    for (int dy = -OFF_R; dy <= OFF_R; ++dy)
+      if (dx * dx + dy * dy == rho2_of(ri) && cheb3(dx, dy, dz) > ws) return true;
+  return false;
+}
 
 struct CudaError {
   cudaError_t e;
@@ -110,8 +169,8 @@ struct Group {
   int32_t *vfree[DMAX + 1] = {};
   int32_t *vreact[DMAX + 1] = {};
   int32_t *ufree = nullptr, *ureact = nullptr;
-  int32_t *rows[DMAX + 1] = {};  // reaction target boxes with k_t in {0,1,2}: 3 * ntb slots
-  uint32_t *nrows[DMAX + 1] = {};
+  int32_t *rows[DMAX + 1] = {};  // reaction target boxes with k_t in [0, 2 ws]: NKT * ntb slots
+  uint32_t *nrows[DMAX + 1] = {};  // [NKT]
   uint8_t *used[DMAX + 1] = {};  // reaction classes in use, NREACT_CLS per level
   int32_t *ktrow[DMAX + 1] = {};
   // expansions
@@ -132,6 +191,7 @@ struct Group {
 struct Ctx {
   Medium md;
   int p = 10, K = 66;
+  int ws = 2;  // separation of the interaction lists (boxes)
   double tol = 1e-14;
   lpbfmm_opts opts;
   cudaStream_t stream = nullptr;

@@ -23,7 +23,7 @@ struct OpDesc {
   int kind;     // 0 = M2L free, 1 = M2M, 2 = L2L
   int out_inv;  // 0: out scale x^n/(2n+1)!!, 1: (2n+1)!!/x^n
   int in_inv;
-  int dir;      // direction of b: free M2L class 0..69, 70 + cz for M2M / L2L (Ctx::phat_dir)
+  int dir;      // direction of b: free M2L class (< NFREE_CLS), NFREE_CLS + cz for M2M / L2L (Ctx::phat_dir)
   double lam, bnorm, cosb, xout, xin, pref;
   int64_t dst;  // element offset of P (Q follows after K*K)
 };
@@ -118,6 +118,7 @@ __global__ void k_build_ops(const OpDesc *descs, const double *prep, const doubl
 // ---------------------------------------------------------------------------------------
 struct RDesc {
   int l, a, lp, b, tau, ntypes, st, pad;
+  int cls0, pad2;        // the table array holds classes cls0, cls0 + 1, ... (0: every class)
   double h, Lam, Lamp;
   const uint8_t *used;   // [NREACT_CLS]
   double *stab;          // [NREACT_CLS][ntypes][TS]
@@ -125,9 +126,6 @@ struct RDesc {
   int64_t dst;           // element offset of class 0, type tau in the op array
 };
 
-__constant__ double c_rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
-__constant__ int c_kk_t[NKK] = {0, 0, 1, 0, 1, 2};
-__constant__ int c_kk_s[NKK] = {0, 1, 0, 2, 1, 0};
 
 constexpr int MAXPANEL = 1024;
 
@@ -180,9 +178,10 @@ __device__ __forceinline__ void gl16(double *x, double *w) {
 // Quadrature of S^K S_{K d, ij} for d = 0, 1, K = 0..KT on one composite Gauss-Legendre node
 // set per (component, level) in u = lambda_rho h: panel width min(2/zeta_min, pi/rho_max),
 // graded near u = 0 to resolve the branch points at u = +-i Lambda.  Node data (first kernel):
-//   nd[q] = {u, w sigma / u_z, Lam / u_z, Lamp / u'_z, e^{-u_z (k+1/2)} (k=0..2),
-//            e^{-u'_z (k+1/2)} (k=0..2), J0(u rho_r), J1(u rho_r) (r = 0..9)}
-constexpr int NDF = 10 + 2 * NRHO;
+//   nd[q] = {u, w sigma / u_z, Lam / u_z, Lamp / u'_z, e^{-u_z (k+1/2)} (k < NKT),
+//            e^{-u'_z (k+1/2)} (k < NKT), J0(u rho_r), J1(u rho_r) (r < NRHO)}
+constexpr int ND_ET = 4, ND_ES = ND_ET + NKT, ND_J0 = ND_ES + NKT, ND_J1 = ND_J0 + NRHO;
+constexpr int NDF = ND_J1 + NRHO;
 
 // host: the u beyond which u^KT e^{-zeta u} has fallen by tol (and e^-3 more) below its peak
 // at u = KT/zeta
@@ -196,7 +195,7 @@ static double node_umax(int KT, double zeta, double tol) {
 
 struct NDesc {
   double umax, wmax, lmin;
-  double ucut[3];  // truncation point for zeta = 1, 2, 3 (zeta = k_t + k_s + 1)
+  double ucut[NKT];  // truncation point for zeta = k_t + k_s + 1 = 1 .. NKT
   int npan, nq;
   double *nodes;        // [nq][NDF]
   const double *bes;    // shared J0, J1 columns of this node set [nq][2 NRHO], or null (computed here)
@@ -217,7 +216,7 @@ __global__ void k_stab_bessel(NDesc N, double *bes) {
     const int pi_ = j >> 4, gi = 15 - (j & 15);  // ascending abscissae
     const double u = pu[pi_] + 0.5 * pw[pi_] * (c_glx[gi] + 1.0);
     for (int r = 0; r < NRHO; ++r) {
-      const double x = u * sqrt(c_rho2[r]);
+      const double x = u * sqrt((double)rho2_of(r));
       o[r] = j0(x);
       o[NRHO + r] = j1(x);
     }
@@ -246,18 +245,18 @@ __global__ void k_stab_nodes(const RDesc *descs, const NDesc *nds, Medium md) {
     o[1] = w * sg / uz;
     o[2] = D.Lam / uz;
     o[3] = D.Lamp / uzp;
-    for (int k = 0; k < 3; ++k) {
-      o[4 + k] = exp(-uz * (k + 0.5));
-      o[7 + k] = exp(-uzp * (k + 0.5));
+    for (int k = 0; k < NKT; ++k) {
+      o[ND_ET + k] = exp(-uz * (k + 0.5));
+      o[ND_ES + k] = exp(-uzp * (k + 0.5));
     }
     if (N.bes) {
       const double *b = N.bes + (size_t)j * 2 * NRHO;
-      for (int r = 0; r < 2 * NRHO; ++r) o[10 + r] = b[r];
+      for (int r = 0; r < 2 * NRHO; ++r) o[ND_J0 + r] = b[r];
     } else {
       for (int r = 0; r < NRHO; ++r) {
-        const double x = u * sqrt(c_rho2[r]);
-        o[10 + r] = j0(x);
-        o[10 + NRHO + r] = j1(x);
+        const double x = u * sqrt((double)rho2_of(r));
+        o[ND_J0 + r] = j0(x);
+        o[ND_J1 + r] = j1(x);
       }
     }
   }
@@ -278,7 +277,8 @@ __global__ void k_stab_quad(const RDesc *descs, const NDesc *nds, int KT, const 
   double *Pw = sqsm;                          // [KT+1][SQ_LD] powers
   double *V = sqsm + (size_t)(KT + 1) * SQ_LD;  // [8][SQ_LD] node values
   const int ri = cls / NKK, kk = cls % NKK;
-  const int kt = c_kk_t[kk], ks = c_kk_s[kk];
+  int kt, ks;
+  kk_decode(kk, kt, ks);
   const double ucut = N.ucut[kt + ks];
   // output of this thread: d, ij, K with K - d odd
   const int n0 = (KT + 1) / 2, n1 = KT / 2;  // K odd (d = 0): 1,3,..; K even >= 2 (d = 1): 2,4,..
@@ -297,8 +297,8 @@ __global__ void k_stab_quad(const RDesc *descs, const NDesc *nds, int KT, const 
     if (q < N.nq) {
       const double *o = N.nodes + (size_t)q * NDF;
       u = o[0];
-      const double base = o[1] * o[4 + kt] * o[7 + ks];
-      const double j0v = o[10 + ri], j1v = o[10 + NRHO + ri], fi = o[2], fj = o[3];
+      const double base = o[1] * o[ND_ET + kt] * o[ND_ES + ks];
+      const double j0v = o[ND_J0 + ri], j1v = o[ND_J1 + ri], fi = o[2], fj = o[3];
       const bool in = u <= ucut && u > 0.0;
       const double b0 = in ? base * j0v : 0.0, b1 = in ? base * j1v : 0.0;
       V[0 * SQ_LD + threadIdx.x] = b0;
@@ -326,7 +326,7 @@ __global__ void k_stab_quad(const RDesc *descs, const NDesc *nds, int KT, const 
     __syncthreads();
     if (c0 + SQ_CHUNK < N.nq && N.nodes[(size_t)(c0 + SQ_CHUNK) * NDF] > ucut) break;
   }
-  double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  double *S = D.stab + ((size_t)(cls - D.cls0) * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   if (oK >= 0) {
     const double nrm = 1.0 / sfac[oK * (KMAX_TAB + 1) + od];
     S[stab_index(KT, oK, od, oij)] = acc * nrm;
@@ -339,7 +339,7 @@ __global__ void k_stab_quad(const RDesc *descs, const NDesc *nds, int KT, const 
 }
 static size_t stab_quad_smem(int KT) { return sizeof(double) * (size_t)(KT + 1 + 8) * SQ_LD; }
 
-// host: node set of one (component, level) covering every class (zeta >= 1, rho <= sqrt(18) h)
+// host: node set of one (component, level) covering every class (zeta >= 1, rho <= sqrt(50) h)
 // number of panels of the graded rule (host mirror of make_panels)
 static int count_panels(double umax, double wmax, double lmin) {
   int n = 0;
@@ -353,15 +353,15 @@ static int count_panels(double umax, double wmax, double lmin) {
   return n;
 }
 
-// Panel width 2 in u = lambda_rho h: with rho <= sqrt(18) the Bessel factor J_d(u rho) has
+// Panel width 2 in u = lambda_rho h: with rho <= sqrt(50) the Bessel factor J_d(u rho) has
 // derivatives bounded by rho^n, and the 16-point Gauss rule's error term on a width-2 panel,
-// rho^32 2^33 (16!)^4 / (33 (32!)^3), is ~1e-25 of the integrand's scale; the factors
-// e^{-zeta u} (zeta <= 3) are smoother still.  The panels are graded towards u = 0, where the
+// rho^32 2^33 (16!)^4 / (33 (32!)^3), is ~1e-18 of the integrand's scale (~1e-25 for
+// rho <= sqrt(18)); the factors e^{-zeta u} (zeta <= NKT) are smoother still.  The panels are graded towards u = 0, where the
 // branch points u = +-i Lambda of u_z sit.
 static NDesc node_desc(int KT, double tol, double Lam, double Lamp) {
   NDesc N;
   N.umax = node_umax(KT, 1.0, tol);
-  for (int z = 0; z < 3; ++z) N.ucut[z] = node_umax(KT, z + 1.0, tol);
+  for (int z = 0; z < NKT; ++z) N.ucut[z] = node_umax(KT, z + 1.0, tol);
   N.wmax = 2.0;
   N.lmin = fmin(Lam, Lamp);
   N.npan = count_panels(N.umax, N.wmax, N.lmin);
@@ -394,9 +394,9 @@ __global__ void k_stab_recur(const RDesc *descs, int KT) {
   const int cls = blockIdx.x;
   if (D.used && !D.used[cls]) return;
   const int ri = cls / NKK;
-  const double rh = sqrt(c_rho2[ri]);
+  const double rh = sqrt((double)rho2_of(ri));
   const double irh = rh > 0.0 ? 1.0 / rh : 0.0;
-  double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  double *S = D.stab + ((size_t)(cls - D.cls0) * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   const int lane = threadIdx.x;
   for (int d = 1; d < KT; ++d) {
     for (int e = lane; e < (KT + 1) * 4; e += 32) {
@@ -482,7 +482,7 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
   __shared__ double smm[PMAX + 1], rdf[PMAX + 1];
   __shared__ double fa[KHALF_MAX], fb[KHALF_MAX];  // prefactor A(o, i) = fa[o] fb[i]
   __shared__ float faf[KHALF_MAX], fbf[KHALF_MAX];  // the same in FP32 (FP32 operators, p <= 12)
-  const double *S = D.stab + ((size_t)cls * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
+  const double *S = D.stab + ((size_t)(cls - D.cls0) * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
   for (int e = threadIdx.x; e < (KT + 1) * (KT + 1) * 4; e += blockDim.x) {
     const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
     Sf[e] = df_split((d <= Kk) ? sfac[Kk * (KMAX_TAB + 1) + d] * S[e] : 0.0);
@@ -610,8 +610,8 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       if (g.is_free && (parts & 1)) {
         b.m2m_t = total;
         for (int cz = 0; cz < 2; ++cz)
-          add(1, 1, 0, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hp, lam_t * hc, 1.0, 70 + cz,
-              (size_t)cz * 2 * KK);
+          add(1, 1, 0, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hp, lam_t * hc, 1.0,
+              NFREE_CLS + cz, (size_t)cz * 2 * KK);
         total += 4 * KK;
       }
       if (parts & 2) {
@@ -621,7 +621,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
           type_decode(t, lp, bb);
           const double la = c.md.lam[lp];
           for (int cz = 0; cz < 2; ++cz)
-            add(1, 1, 0, la, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, la * hp, la * hc, 1.0, 70 + cz,
+            add(1, 1, 0, la, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, la * hp, la * hc, 1.0, NFREE_CLS + cz,
                 ((size_t)t * 2 + cz) * 2 * KK);
         }
         total += (size_t)g.ntypes * 4 * KK;
@@ -629,21 +629,19 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       // L2L: parent (l-1) -> child at l
       b.l2l = total;
       for (int cz = 0; cz < 2; ++cz)
-        add(2, 0, 1, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hc, lam_t * hp, 1.0, 70 + cz,
-            (size_t)cz * 2 * KK);
+        add(2, 0, 1, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hc, lam_t * hp, 1.0,
+            NFREE_CLS + cz, (size_t)cz * 2 * KK);
       total += 4 * KK;
     }
     if (g.is_free && (parts & 1)) {
       b.fm2l = total;
-      const double rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
       const double pref = lam_t / (2.0 * PI * PI * c.md.eps[g.l]);
       for (int ri = 0; ri < NRHO; ++ri)
-        for (int dz = -3; dz <= 3; ++dz) {
-          const int cls = ri * 7 + dz + 3;
-          const bool adjacent = rho2[ri] <= 2.0 && abs(dz) <= 1;
-          if (adjacent) continue;
+        for (int dz = -OFF_R; dz <= OFF_R; ++dz) {
+          const int cls = ri * NDZ + dz + OFF_R;
+          if (!free_class_is_far(ri, dz, c.ws)) continue;
           // b = c_t - c_s = -(offset) h; azimuth factored out: b = (rho h, 0, -dz h)
-          add(0, 0, 0, lam_t, sqrt(rho2[ri]) * h, 0.0, -dz * h, lam_t * h, lam_t * h, pref, cls,
+          add(0, 0, 0, lam_t, sqrt((double)rho2_of(ri)) * h, 0.0, -dz * h, lam_t * h, lam_t * h, pref, cls,
               (size_t)cls * 2 * KK);
         }
       total += (size_t)NFREE_CLS * 2 * KK;
@@ -685,6 +683,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       type_decode(t, lp, bb);
       RDesc d;
       d.l = g.l; d.a = g.a; d.lp = lp; d.b = bb; d.tau = t; d.ntypes = g.ntypes; d.st = st; d.pad = l;
+      d.cls0 = 0; d.pad2 = 0;
       d.h = h; d.Lam = c.md.lam[g.l] * h; d.Lamp = c.md.lam[lp] * h;
       d.used = g.used[l];
       d.stab = g.stab[l];
@@ -770,36 +769,49 @@ void build_near_nodes(Ctx &c, Group &g, double zeta_min, double rho_max) {
   c.launches++;
 }
 
-void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
-                  double *out) {
-  // single class with the requested geometry: reuse the quadrature + recurrence kernels through a
-  // one-class descriptor (class index chosen from rho/h, zt/h - 1/2, zs/h - 1/2)
+// reaction class of a single-class table request: rho / h, zt / h - 1/2 and zs / h - 1/2 must be a
+// class of the tables (rho^2 / h^2 one of the NRHO values, k_t + k_s < NKT)
+static int class_of_request(double h, double rho, double zt, double zs) {
   const double r2 = (rho / h) * (rho / h);
-  const double rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
   int ri = -1;
   for (int k = 0; k < NRHO; ++k)
-    if (fabs(r2 - rho2[k]) < 1e-9) ri = k;
+    if (fabs(r2 - rho2_of(k)) < 1e-9) ri = k;
   const int kt = (int)llround(zt / h - 0.5), ks = (int)llround(zs / h - 0.5);
-  const int kkt[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
-  if (ri < 0 || kt < 0 || ks < 0 || kt + ks > 2 || fabs(zt / h - 0.5 - kt) > 1e-9 || fabs(zs / h - 0.5 - ks) > 1e-9)
+  const int kk = kk_index(kt, ks);
+  if (ri < 0 || kk < 0 || fabs(zt / h - 0.5 - kt) > 1e-9 || fabs(zs / h - 0.5 - ks) > 1e-9)
     throw StatusError{LPBFMM_ERR_ARG};
-  const int cls = ri * NKK + kkt[kt][ks];
+  return ri * NKK + kk;
+}
+
+static RDesc one_class_desc(Ctx &c, int l, int a, int lp, int b, double h, int cls) {
+  RDesc d;
+  d.l = l; d.a = a; d.lp = lp; d.b = b; d.tau = 0; d.ntypes = 1; d.st = a == 1 ? -1 : 1; d.pad = 0;
+  d.cls0 = cls; d.pad2 = 0;
+  d.h = h; d.Lam = c.md.lam[l] * h; d.Lamp = c.md.lam[lp] * h;
+  d.used = nullptr; d.stab = nullptr; d.coef = nullptr; d.dst = 0;
+  return d;
+}
+
+void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
+                  double *out) {
+  // single class with the requested geometry: the quadrature + recurrence kernels of the FMM run
+  // on a one-class descriptor whose table array holds that class alone
+  const int cls = class_of_request(h, rho, zt, zs);
   const int KT = Kmax;
   const size_t TS = (size_t)(KT + 1) * (KT + 1) * 4;
   double *stab = nullptr;
   uint8_t *used = nullptr;
   RDesc *dr = nullptr;
-  LPB_CUDA(cudaMalloc(&stab, sizeof(double) * NREACT_CLS * TS));
+  LPB_CUDA(cudaMalloc(&stab, sizeof(double) * TS));
   LPB_CUDA(cudaMalloc(&used, NREACT_CLS));
   LPB_CUDA(cudaMalloc(&dr, sizeof(RDesc)));
-  LPB_CUDA(cudaMemsetAsync(stab, 0, sizeof(double) * NREACT_CLS * TS, c.stream));
+  LPB_CUDA(cudaMemsetAsync(stab, 0, sizeof(double) * TS, c.stream));
   std::vector<uint8_t> hu(NREACT_CLS, 0);
   hu[cls] = 1;
   LPB_CUDA(cudaMemcpyAsync(used, hu.data(), NREACT_CLS, cudaMemcpyHostToDevice, c.stream));
-  RDesc d;
-  d.l = l; d.a = a; d.lp = lp; d.b = b; d.tau = 0; d.ntypes = 1; d.st = a == 1 ? -1 : 1; d.pad = 0;
-  d.h = h; d.Lam = c.md.lam[l] * h; d.Lamp = c.md.lam[lp] * h;
-  d.used = used; d.stab = stab; d.coef = nullptr; d.dst = 0;
+  RDesc d = one_class_desc(c, l, a, lp, b, h, cls);
+  d.used = used;
+  d.stab = stab;
   LPB_CUDA(cudaMemcpyAsync(dr, &d, sizeof(RDesc), cudaMemcpyHostToDevice, c.stream));
   const double tol = fmax(c.tol, 1e-16);
   NDesc N = node_desc(KT, tol, d.Lam, d.Lamp);
@@ -811,16 +823,14 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
   LPB_LAUNCH();
   {
     const size_t sm = stab_quad_smem(KT);
-    LPB_CUDA(cudaFuncSetAttribute(k_stab_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)stab_quad_smem(KMAX_TAB)));
+    LPB_ATTR_ONCE(k_stab_quad, stab_quad_smem(KMAX_TAB));
     k_stab_quad<<<dim3(NREACT_CLS, 1), SQ_CHUNK, sm, c.stream>>>(dr, dn, KT, c.sfac);
     LPB_LAUNCH();
   }
   k_stab_recur<<<dim3(NREACT_CLS, 1), 32, 0, c.stream>>>(dr, KT);
   LPB_LAUNCH();
   std::vector<double> h_out(TS);
-  LPB_CUDA(cudaMemcpyAsync(h_out.data(), stab + (size_t)cls * TS, sizeof(double) * TS, cudaMemcpyDeviceToHost,
-                           c.stream));
+  LPB_CUDA(cudaMemcpyAsync(h_out.data(), stab, sizeof(double) * TS, cudaMemcpyDeviceToHost, c.stream));
   LPB_CUDA(cudaStreamSynchronize(c.stream));
   cudaFree(stab);
   cudaFree(used);
@@ -839,27 +849,27 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
 // synchronize the whole device).  Every temporary lives in one fixed device array; its
 // address is resolved per device with cudaGetSymbolAddress on the first call on that device.
 // ---------------------------------------------------------------------------------------
-constexpr size_t NA_TS = (size_t)(LPBFMM_NOALLOC_KMAX + 1) * (LPBFMM_NOALLOC_KMAX + 1) * 4;
-constexpr size_t NA_STAB = (size_t)NREACT_CLS * NA_TS;             // doubles, all classes
+constexpr size_t NA_TS = (size_t)(LPBFMM_NOALLOC_KMAX + 1) * (LPBFMM_NOALLOC_KMAX + 1) * 4;  // one class
 constexpr size_t NA_NODES = (size_t)LPBFMM_NOALLOC_NQ * NDF;        // doubles
 constexpr size_t NA_DESC = (sizeof(RDesc) + sizeof(NDesc) + NREACT_CLS + 7) / 8 + 8;
-constexpr size_t NA_DOUBLES = NA_STAB + NA_NODES + NA_DESC;        // ~2.1 MB in all
+constexpr size_t NA_DOUBLES = NA_TS + NA_NODES + NA_DESC;           // ~1.8 MB in all
 static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
 static std::mutex g_noalloc_mu;
-static double *g_noalloc_addr[64] = {};
+static double *g_noalloc_addr[LPB_MAX_DEVICES] = {};
 
-static double *noalloc_scratch() {
-  int dev = 0;
+// the scratch array's device address on the context's device (which must be current)
+static double *noalloc_scratch(const Ctx &c) {
+  int dev = -1;
   LPB_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+  if (dev != c.device) throw StatusError{LPBFMM_ERR_ARG};
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  if (!g_noalloc_addr[c.device]) {
     void *p = nullptr;
     LPB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_addr[dev] = (double *)p;
+    g_noalloc_addr[c.device] = (double *)p;
   }
-  return g_noalloc_addr[dev];
+  return g_noalloc_addr[c.device];
 }
 
 // descriptors, class mask and the class's table are (re)initialised by one launch: the table
@@ -878,43 +888,30 @@ __global__ void k_noalloc_init(RDesc d, NDesc n, RDesc *rd, NDesc *nd, uint8_t *
 void stable_noalloc(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
                     double *out) {
   if (Kmax > LPBFMM_NOALLOC_KMAX) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
-  const double rho2[NRHO] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
-  const double r2 = (rho / h) * (rho / h);
-  int ri = -1;
-  for (int k = 0; k < NRHO; ++k)
-    if (fabs(r2 - rho2[k]) < 1e-9) ri = k;
-  const int kt = (int)llround(zt / h - 0.5), ks = (int)llround(zs / h - 0.5);
-  const int kkt[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
-  if (ri < 0 || kt < 0 || ks < 0 || kt + ks > 2 || fabs(zt / h - 0.5 - kt) > 1e-9 || fabs(zs / h - 0.5 - ks) > 1e-9)
-    throw StatusError{LPBFMM_ERR_ARG};
-  const int cls = ri * NKK + kkt[kt][ks];
+  const int cls = class_of_request(h, rho, zt, zs);
   const int KT = Kmax;
   const size_t TS = (size_t)(KT + 1) * (KT + 1) * 4;
-  RDesc d;
-  d.l = l; d.a = a; d.lp = lp; d.b = b; d.tau = 0; d.ntypes = 1; d.st = a == 1 ? -1 : 1; d.pad = 0;
-  d.h = h; d.Lam = c.md.lam[l] * h; d.Lamp = c.md.lam[lp] * h;
-  d.coef = nullptr; d.dst = 0;
+  RDesc d = one_class_desc(c, l, a, lp, b, h, cls);
   NDesc N = node_desc(KT, fmax(c.tol, 1e-16), d.Lam, d.Lamp);
   if (N.nq > LPBFMM_NOALLOC_NQ) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
-  double *base = noalloc_scratch();
-  double *stab = base, *nodes = base + NA_STAB;
+  double *base = noalloc_scratch(c);
+  double *stab = base, *nodes = base + NA_TS;
   RDesc *dr = (RDesc *)(nodes + NA_NODES);
   NDesc *dn = (NDesc *)((char *)dr + ((sizeof(RDesc) + 15) / 16) * 16);
   uint8_t *used = (uint8_t *)((char *)dn + ((sizeof(NDesc) + 15) / 16) * 16);
   d.used = used;
   d.stab = stab;
   N.nodes = nodes;
-  k_noalloc_init<<<8, 256, 0, c.stream>>>(d, N, dr, dn, used, cls, stab + (size_t)cls * TS, (int)TS);
+  k_noalloc_init<<<8, 256, 0, c.stream>>>(d, N, dr, dn, used, cls, stab, (int)TS);
   LPB_LAUNCH();
   k_stab_nodes<<<dim3((unsigned)((N.nq + 255) / 256), 1), 256, 0, c.stream>>>(dr, dn, c.md);
   LPB_LAUNCH();
-  LPB_CUDA(cudaFuncSetAttribute(k_stab_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stab_quad_smem(KMAX_TAB)));
+  LPB_ATTR_ONCE(k_stab_quad, stab_quad_smem(KMAX_TAB));
   k_stab_quad<<<dim3(NREACT_CLS, 1), SQ_CHUNK, stab_quad_smem(KT), c.stream>>>(dr, dn, KT, c.sfac);
   LPB_LAUNCH();
   k_stab_recur<<<dim3(NREACT_CLS, 1), 32, 0, c.stream>>>(dr, KT);
   LPB_LAUNCH();
-  LPB_CUDA(cudaMemcpyAsync(out, stab + (size_t)cls * TS, sizeof(double) * TS, cudaMemcpyDeviceToDevice, c.stream));
+  LPB_CUDA(cudaMemcpyAsync(out, stab, sizeof(double) * TS, cudaMemcpyDeviceToDevice, c.stream));
 }
 
 }  // namespace lpb

@@ -1,5 +1,5 @@
 // Input validation, per-group octrees (Morton keys + radix sort) and interaction lists.
-// Tree rule (Sec. 3.5): the root cube of target group (l, a) is bisected by its interface
+// Tree rule (Sec. 3.5, before Algorithm 1): the root cube of target group (l, a) is bisected by its interface
 // (d_l for a = 1, d_{l-1} for a = 2), so every box of level >= 1 has its centre on the
 // side of the points it holds; all trees here have uniform depth D.
 #include "internal.h"
@@ -495,23 +495,11 @@ void build_group_boxes(Ctx &c, Group &g) {
 }
 
 // ---------------------------------------------------------------------------------------
-// interaction lists.  Far list (multipole-to-local, V): source boxes at offset d with
-// |d|_inf >= 2 whose parent neighbours the target's parent.  Near list (U): |d|_inf <= 1.
-// Dense layout: [target box][offset slot] -> source box index or -1.
+// interaction lists with separation ws.  Far list (multipole-to-local, V): source boxes at
+// offset d with |d|_inf > ws whose parent lies within ws of the target's parent.  Near list
+// (U): |d|_inf <= ws.  Dense layout: [target box][offset slot] -> source box index or -1, with
+// the slots of WS_MAX (offsets of a smaller ws leave the outer slots at -1).
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int rho_index(int dx, int dy) {
-  const int r2 = dx * dx + dy * dy;
-  switch (r2) {
-    case 0: return 0; case 1: return 1; case 2: return 2; case 4: return 3; case 5: return 4;
-    case 8: return 5; case 9: return 6; case 10: return 7; case 13: return 8; case 18: return 9;
-  }
-  return -1;
-}
-__device__ __forceinline__ int kk_index(int kt, int ks) {
-  if (kt < 0 || ks < 0 || kt + ks > 2) return -1;
-  const int tab[3][3] = {{0, 1, 3}, {2, 4, -1}, {5, -1, -1}};
-  return tab[kt][ks];
-}
 __device__ __forceinline__ int64_t find_key(const uint64_t *keys, int64_t n, uint64_t k) {
   int64_t lo = 0, hi = n - 1;
   while (lo <= hi) {
@@ -523,10 +511,10 @@ __device__ __forceinline__ int64_t find_key(const uint64_t *keys, int64_t n, uin
   return -1;
 }
 
-// far = 1: V list over 343 slots; far = 0: near list over 27 slots
-// react: reaction list (targets vs images): also records used classes and the target row k_t
+// far = 1: V list over NOFF slots; far = 0: near list over NNEAR slots
+// react: reaction list (targets vs images): also records the classes in use
 __global__ void k_lists(const uint64_t *tkey, const uint32_t *d_nt, const uint64_t *skey, const uint32_t *d_ns,
-                        int lev, int far, int react, int a, int32_t *out, uint8_t *used) {
+                        int lev, int far, int react, int a, int ws, int32_t *out, uint8_t *used) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nslot = far ? NOFF : NNEAR;
   const int64_t t = gid / nslot;
@@ -534,17 +522,19 @@ __global__ void k_lists(const uint64_t *tkey, const uint32_t *d_nt, const uint64
   const int64_t nt = *d_nt;
   if (t >= nt) return;
   int dx, dy, dz;
-  if (far) { dx = o / 49 - 3; dy = (o / 7) % 7 - 3; dz = o % 7 - 3; }
-  else { dx = o / 9 - 1; dy = (o / 3) % 3 - 1; dz = o % 3 - 1; }
+  if (far) off_decode(o, dx, dy, dz);
+  else near_decode(o, dx, dy, dz);
   const uint64_t k = tkey[t];
   const int ix = compact3(k >> 2), iy = compact3(k >> 1), iz = compact3(k);
   const int jx = ix + dx, jy = iy + dy, jz = iz + dz, nc = 1 << lev;
   int32_t res = -1;
-  const int cheb = max(abs(dx), max(abs(dy), abs(dz)));
+  const int cheb = cheb3(dx, dy, dz);
   bool ok = jx >= 0 && jy >= 0 && jz >= 0 && jx < nc && jy < nc && jz < nc;
   if (far) {
-    ok = ok && cheb >= 2 && abs((jx >> 1) - (ix >> 1)) <= 1 && abs((jy >> 1) - (iy >> 1)) <= 1 &&
-         abs((jz >> 1) - (iz >> 1)) <= 1;
+    ok = ok && cheb > ws && abs((jx >> 1) - (ix >> 1)) <= ws && abs((jy >> 1) - (iy >> 1)) <= ws &&
+         abs((jz >> 1) - (iz >> 1)) <= ws;
+  } else {
+    ok = ok && cheb <= ws;
   }
   const int64_t ns = *d_ns;
   if (ok && ns > 0) {
@@ -564,21 +554,23 @@ __global__ void k_lists(const uint64_t *tkey, const uint32_t *d_nt, const uint64
   out[t * nslot + o] = res;
 }
 
-__global__ void k_rows(const uint64_t *tkey, const uint32_t *d_nt, int lev, int a, int32_t *rows, uint32_t *nrows,
-                       int32_t *ktrow, int64_t cap) {
+// reaction target rows: boxes at k_t = 0 .. 2 ws box layers from the interface, per row
+__global__ void k_rows(const uint64_t *tkey, const uint32_t *d_nt, int lev, int a, int nkt, int32_t *rows,
+                       uint32_t *nrows, int32_t *ktrow, int64_t cap) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= *d_nt) return;
   const int iz = compact3(tkey[t]);
   const int half = 1 << (lev - 1);
   const int kt = (a == 1) ? iz - half : half - 1 - iz;
   ktrow[t] = kt;
-  if (kt >= 0 && kt <= 2) {
+  if (kt >= 0 && kt < nkt) {
     const uint32_t pos = atomicAdd(&nrows[kt], 1u);
     rows[kt * cap + pos] = (int32_t)t;
   }
 }
 
 void build_group_lists(Ctx &c, Group &g, int parts) {
+  const int ws = c.ws, nkt = 2 * c.ws + 1;
   for (int l = 2; l <= g.D; ++l) {
     const Level &T = g.T.lev[l];
     const Level &I = g.I.lev[l];
@@ -587,7 +579,7 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
     const unsigned fb = (unsigned)((nt * NOFF + 255) / 256);
     if (g.is_free && (parts & 1)) {
       g.vfree[l] = c.arena.get<int32_t>(nt * NOFF);
-      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, T.key, T.d_n, l, 1, 0, g.a, g.vfree[l], nullptr);
+      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, T.key, T.d_n, l, 1, 0, g.a, ws, g.vfree[l], nullptr);
       LPB_LAUNCH();
       c.launches++;
     }
@@ -595,13 +587,13 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
       g.vreact[l] = c.arena.get<int32_t>(nt * NOFF);
       g.used[l] = c.arena.get<uint8_t>(NREACT_CLS);
       LPB_CUDA(cudaMemsetAsync(g.used[l], 0, NREACT_CLS, c.stream));
-      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, I.key, I.d_n, l, 1, 1, g.a, g.vreact[l], g.used[l]);
+      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, I.key, I.d_n, l, 1, 1, g.a, ws, g.vreact[l], g.used[l]);
       LPB_LAUNCH();
-      g.rows[l] = c.arena.get<int32_t>(3 * nt);
-      g.nrows[l] = c.arena.get<uint32_t>(3);
+      g.rows[l] = c.arena.get<int32_t>((size_t)NKT * nt);
+      g.nrows[l] = c.arena.get<uint32_t>(NKT);
       g.ktrow[l] = c.arena.get<int32_t>(nt);
-      LPB_CUDA(cudaMemsetAsync(g.nrows[l], 0, 3 * sizeof(uint32_t), c.stream));
-      k_rows<<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(T.key, T.d_n, l, g.a, g.rows[l], g.nrows[l],
+      LPB_CUDA(cudaMemsetAsync(g.nrows[l], 0, NKT * sizeof(uint32_t), c.stream));
+      k_rows<<<(unsigned)((nt + 255) / 256), 256, 0, c.stream>>>(T.key, T.d_n, l, g.a, nkt, g.rows[l], g.nrows[l],
                                                                  g.ktrow[l], nt);
       LPB_LAUNCH();
       c.launches += 2;
@@ -614,14 +606,14 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
   if (g.is_free && (parts & 1)) {
     g.ufree = c.arena.get<int32_t>(nt * NNEAR);
     k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].d_n, D, 0, 0,
-                                      g.a, g.ufree, nullptr);
+                                      g.a, ws, g.ufree, nullptr);
     LPB_LAUNCH();
     c.launches++;
   }
   if ((parts & 2) && g.I.lev[D].n) {
     g.ureact = c.arena.get<int32_t>(nt * NNEAR);
     k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.I.lev[D].key, g.I.lev[D].d_n, D, 0, 1,
-                                      g.a, g.ureact, nullptr);
+                                      g.a, ws, g.ureact, nullptr);
     LPB_LAUNCH();
     c.launches++;
   }

@@ -30,7 +30,7 @@ class LpbfmmError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_per_leaf", C.c_int), ("uniform_depth", C.c_int),
-                ("reserved", C.c_int), ("stream", C.c_void_p)]
+                ("separation", C.c_int), ("stream", C.c_void_p)]
 
 
 def lib():
@@ -65,6 +65,7 @@ def lib():
         L.lpbfmm_last_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_float),
                                           C.POINTER(C.c_int)]
         L.lpbfmm_host_table.argtypes = [C.c_int, C.c_int, dp, i64, C.POINTER(i64)]
+        L.lpbfmm_measure_peak.argtypes = [C.c_int, dp]
         _lib = L
     return _lib
 
@@ -86,16 +87,18 @@ def _darr(vals):
 
 
 class Context:
-    """One medium (interfaces d, eps, lambda per layer) and truncation order p (lpbfmm_create)."""
+    """One medium (interfaces d, eps, lambda per layer) and truncation order p (lpbfmm_create);
+    separation = 1 (one-box) or 2 (two-box) interaction lists, 0 = the library default (2)."""
 
     def __init__(self, d, eps, lam, p, tol=1e-14, precision=FP64, max_per_leaf=128, uniform_depth=0,
-                 stream=None):
+                 stream=None, separation=0):
         L = lib()
         o = Opts()
         L.lpbfmm_default_opts(C.byref(o))
         o.precision = int(precision)
         o.max_per_leaf = int(max_per_leaf)
         o.uniform_depth = int(uniform_depth or 0)
+        o.separation = int(separation or 0)
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()
         o.stream = C.c_void_p(stream.cuda_stream if stream is not None else 0)
@@ -216,6 +219,14 @@ class Context:
 
 
 TABLE_GAUNT, TABLE_TPOLY, TABLE_PHAT_DIR, TABLE_SFAC = 0, 1, 2, 3
+PEAK_FP32_FMA, PEAK_FP64_FMA = 0, 1
+
+
+def measure_peak(which):
+    """lpbfmm_measure_peak: the current device's measured FMA peak (TFLOP/s) in FP32 or FP64."""
+    v = C.c_double()
+    _check(lib().lpbfmm_measure_peak(int(which), C.byref(v)), "lpbfmm_measure_peak")
+    return v.value
 
 
 def host_table(which, p):

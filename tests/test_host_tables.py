@@ -98,15 +98,18 @@ def test_phat_dir_table_equals_scipy_harmonics(p):
     if not hasattr(special, "sph_harm_y"):
         pytest.skip("scipy without sph_harm_y")
     qmax = 2 * p
-    P = F.host_table(F.TABLE_PHAT_DIR, p).reshape(72, -1)
-    rho2 = [0, 1, 2, 4, 5, 8, 9, 10, 13, 18]
-    for d in range(72):
-        if d < 70:
-            ri, dz = d // 7, d % 7 - 3
+    # every distinct dx^2 + dy^2 for |dx|, |dy| <= 5 (the far offsets of two-box separation)
+    rho2 = sorted({dx * dx + dy * dy for dx in range(6) for dy in range(6)})
+    assert len(rho2) == 20
+    nd = 11 * len(rho2) + 2
+    P = F.host_table(F.TABLE_PHAT_DIR, p).reshape(nd, -1)
+    for d in range(nd):
+        if d < nd - 2:
+            ri, dz = d // 11, d % 11 - 5
             bn = math.sqrt(rho2[ri] + dz * dz)
             x = -dz / bn if bn > 0 else 1.0
         else:
-            x = (-1.0 if d == 70 else 1.0) / math.sqrt(3.0)
+            x = (-1.0 if d == nd - 2 else 1.0) / math.sqrt(3.0)
         th = math.acos(x)
         for q in range(qmax + 1):
             for k in range(q + 1):

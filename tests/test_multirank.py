@@ -80,10 +80,16 @@ def test_per_layer_errors_match_their_definition():
 
 def test_oracle_fixture_errors_match_their_definition():
     fx = {"targets": [3, 9], "per_layer": 1, "seed": 5, "phi": [1.0, -2.0], "field": [[1, 0, 0], [0, 2, 0]]}
-    got = bench.oracle_fixture_errors({"x": (np.array([1.1, -2.0]), np.array([[1, 0, 0], [0, 2, 0.2]]))}, fx)
+    got = bench.oracle_fixture_errors({"x": (np.array([1.1, -2.0]), np.array([[1, 0, 0], [0, 2, 0.2]]))}, fx,
+                                      layers=[0, 1])
     assert got["targets"] == 2
     assert abs(got["x"]["relL2_phi"] - 0.1 / np.sqrt(5.0)) < 1e-15
     assert abs(got["x"]["relL2_field"] - 0.2 / np.sqrt(5.0)) < 1e-15
+    assert got["x"]["errmax_phi_per_layer"] == pytest.approx([0.1, 0.0])
+    assert got["x"]["errmax_field_per_layer"] == pytest.approx([0.0, 0.1])
+    assert got["x"]["pass"] is False
+    ok = bench.oracle_fixture_errors({"y": (np.array([1.0, -2.0]), np.array([[1, 0, 0], [0, 2, 1e-7]]))}, fx)
+    assert ok["y"]["pass"] is True and "errmax_phi_per_layer" not in ok["y"]
 
 
 def test_paper_workload_option_names_its_own_metric_and_config():
