@@ -69,9 +69,12 @@ typedef struct lpbfmm_ctx *lpbfmm_t;
 
 typedef struct {
   int precision;     /* LPBFMM_FP64 or LPBFMM_MIXED                                        */
-  int max_per_leaf;  /* automatic depth: smallest depth >= 2 whose mean target occupancy of
-                        the non-empty leaves is <= max_per_leaf (default 128)               */
-  int uniform_depth; /* > 0: use this tree depth for every target group; 0: automatic      */
+  int max_per_leaf;  /* automatic depth: the free-space part uses the smallest depth >= 2 whose
+                        mean target occupancy of the non-empty leaves is <= max_per_leaf
+                        (default 128); a group's reaction part goes up to two levels deeper,
+                        until no target box and image box are near (Sec. 3.5, Remark 1)     */
+  int uniform_depth; /* > 0: use this tree depth for every target group and both parts;
+                        0: automatic                                                         */
   int separation;    /* 1 or 2 boxes; 0 = LPBFMM_SEPARATION_DEFAULT                        */
   void *stream;      /* cudaStream_t for all work; NULL = the legacy default stream          */
 } lpbfmm_opts;
@@ -123,7 +126,9 @@ int lpbfmm_eval_parts(lpbfmm_t h, int64_t n, const double *q, const double *xyz,
  * using the reciprocity G_{l l'}(r, r') = G_{l' l}(r', r) of the layered Green's function (the
  * vector-Jacobian product of phi).  For E = 1/2 sum q_i phi_i: dE/dq = g_q with g_phi = q, and
  * dE/dr = g_xyz with g_phi = q / 2 (so the force on charge j is -g_xyz[j]).  Two evaluations
- * are run.  Device arrays; g_q[n], g_xyz[n*3] are outputs.
+ * are run.  Device arrays; g_q[n], g_xyz[n*3] are outputs.  The context keeps a work space of
+ * 7 n doubles between calls (allocated when n first exceeds its size); g_q and g_xyz are written
+ * in stream order on the context's stream.
  */
 int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
                    const double *g_phi, double *g_q, double *g_xyz);
@@ -152,7 +157,8 @@ int lpbfmm_debug_tree(lpbfmm_t h, int l, int a, double *root, int64_t *n_targets
 /*
  * Diagnostics: after an lpbfmm_eval, the interaction lists of group (l, a) at level lev:
  * kind 0 = far (multipole-to-local) list, kind 1 = near list at the leaf level; src 0 = the
- * group's free-space sources (its own targets), src 1 = its images.  Host outputs in CSR form
+ * group's free-space sources (its own targets; leaf level = the free-space depth), src 1 = its
+ * images (leaf level = the tree depth of lpbfmm_debug_tree).  Host outputs in CSR form
  * over the level's target boxes (sorted by key): off[nbox+1], idx[off[nbox]] source box
  * indices, each row in ascending order of the offset (dx, dy, dz) with dx outermost.  With
  * off == NULL only *nbox and *nent are returned.

@@ -9,8 +9,7 @@ against closed forms, the paper's printed formulas, invariants and brute force. 
 ``expansions`` restates the truncated expansions and translations of Sec. 3 (numpy/scipy;
 tests/test_expansion_pins.py checks that they converge in p to this package's direct values),
 ``adaptive`` the adaptive dual trees and their lists (tests/test_adaptive_tree.py), and ``fmm``
-a plain CPU FMM, free-space and reaction parts, built from them (tests/test_cpu_fmm.py);
-``studies`` reruns the accuracy studies quoted in the design notes.
+a plain CPU FMM, free-space and reaction parts, built from them (tests/test_cpu_fmm.py).
 """
 import ctypes as C
 import os

@@ -280,10 +280,27 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     }
   }
   for (auto &g : c.groups) build_group_targets(c, g, n, q, xyz, layer, rank, cnt);
-  // depth
+  // smallest distances of the group's targets and images to its interface (exact extremes of
+  // monotone expressions of the z ranges)
+  auto z_gaps = [&](const Group &g, double &zt, double &zs) {
+    zt = (g.a == 1) ? (zlo[g.l] - g.dI) : (g.dI - zhi[g.l]);
+    zs = 1e300;
+    for (int lp = 0; lp <= L; ++lp) {
+      if (!cnt[lp]) continue;
+      for (int b = 1; b <= 2; ++b) {
+        if ((b == 1 && lp == L) || (b == 2 && lp == 0)) continue;
+        zs = std::min(zs, std::fabs(image_z(md, g.l, g.a, lp, b, zlo[lp]) - g.dI));
+        zs = std::min(zs, std::fabs(image_z(md, g.l, g.a, lp, b, zhi[lp]) - g.dI));
+      }
+    }
+  };
+  // depth: Df of the free-space part by the occupancy rule (or given); the reaction part goes up to
+  // two levels deeper, to the first level whose boxes are small enough that no target box and
+  // image box are near (k_t + k_s >= ws for the closest rows): its near field, the costly direct
+  // Sommerfeld integrals, then vanishes (Sec. 3.5, Remark 1)
   const int G = (int)c.groups.size();
   if (c.opts.uniform_depth > 0) {
-    for (auto &g : c.groups) g.D = std::min(DMAX, std::max(2, c.opts.uniform_depth));
+    for (auto &g : c.groups) g.D = g.Df = std::min(DMAX, std::max(2, c.opts.uniform_depth));
   } else {
     uint32_t *dc = c.arena.get<uint32_t>((size_t)G * (DMAX + 1));
     LPB_CUDA(cudaMemsetAsync(dc, 0, sizeof(uint32_t) * G * (DMAX + 1), c.stream));
@@ -294,9 +311,19 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     const int s = c.opts.max_per_leaf > 0 ? c.opts.max_per_leaf : 128;
     for (int k = 0; k < G; ++k) {
       Group &g = c.groups[k];
-      g.D = DMAX;
+      g.Df = DMAX;
       for (int D = 2; D <= DMAX; ++D)
-        if ((uint64_t)g.T.np <= (uint64_t)s * hc[(size_t)k * (DMAX + 1) + D]) { g.D = D; break; }
+        if ((uint64_t)g.T.np <= (uint64_t)s * hc[(size_t)k * (DMAX + 1) + D]) { g.Df = D; break; }
+      g.D = g.Df;
+      if (parts & 2) {
+        double zt, zs;
+        z_gaps(g, zt, zs);
+        while (g.D < std::min(DMAX, g.Df + 2)) {
+          const double h = g.h(g.D);
+          if (std::floor(zt / h) + std::floor(zs / h) >= c.ws) break;
+          ++g.D;
+        }
+      }
     }
   }
   for (auto &g : c.groups) build_group_images(c, g, n, q, xyz, layer, rank, cnt);
@@ -342,16 +369,8 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
   for (auto &g : c.groups) {
     build_operators(c, g, parts);
     if ((parts & 2) && g.ureact) {
-      double zt = (g.a == 1) ? (zlo[g.l] - g.dI) : (g.dI - zhi[g.l]);
-      double zs = 1e300;
-      for (int lp = 0; lp <= L; ++lp) {
-        if (!cnt[lp]) continue;
-        for (int b = 1; b <= 2; ++b) {
-          if ((b == 1 && lp == L) || (b == 2 && lp == 0)) continue;
-          zs = std::min(zs, std::fabs(image_z(md, g.l, g.a, lp, b, zlo[lp]) - g.dI));
-          zs = std::min(zs, std::fabs(image_z(md, g.l, g.a, lp, b, zhi[lp]) - g.dI));
-        }
-      }
+      double zt, zs;
+      z_gaps(g, zt, zs);
       build_near_nodes(c, g, std::max(zt + zs, 1e-12), (c.ws + 1) * std::sqrt(2.0) * g.h(g.D));
     }
   }
@@ -477,18 +496,23 @@ int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, co
                    const double *g_phi, double *g_q, double *g_xyz) {
   if (!h || n < 0 || (n > 0 && (!q || !xyz || !layer_id || !g_phi || !g_q || !g_xyz))) return LPBFMM_ERR_ARG;
   if (n == 0) return LPBFMM_OK;
-  double *tmp = nullptr;
-  int rc = LPBFMM_OK;
-  if (cudaMalloc(&tmp, sizeof(double) * 7 * n) != cudaSuccess) { cudaGetLastError(); return LPBFMM_ERR_OOM; }
-  double *fg = tmp, *pq = tmp + 3 * n, *fq = tmp + 4 * n;
-  rc = lpbfmm_eval(h, n, g_phi, xyz, layer_id, g_q, fg);
+  // work space kept by the context: grown (after the stream has drained) only when n grows
+  const size_t need = (size_t)7 * n;
+  if (need > h->adj_cap) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LPBFMM_ERR_CUDA;
+    if (h->adj) cudaFree(h->adj);
+    h->adj = nullptr;
+    h->adj_cap = 0;
+    if (cudaMalloc(&h->adj, sizeof(double) * need) != cudaSuccess) { cudaGetLastError(); return LPBFMM_ERR_OOM; }
+    h->adj_cap = need;
+  }
+  double *fg = h->adj, *pq = h->adj + 3 * n, *fq = h->adj + 4 * n;
+  int rc = lpbfmm_eval(h, n, g_phi, xyz, layer_id, g_q, fg);
   if (rc == LPBFMM_OK) rc = lpbfmm_eval(h, n, q, xyz, layer_id, pq, fq);
   if (rc == LPBFMM_OK) {
     k_adjoint_combine<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, q, g_phi, fq, fg, g_xyz);
     if (cudaGetLastError() != cudaSuccess) rc = LPBFMM_ERR_CUDA;
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = LPBFMM_ERR_CUDA;
   }
-  cudaFree(tmp);
   return rc;
 }
 
@@ -536,6 +560,7 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   h->arena.release();
+  if (h->adj) cudaFree(h->adj);
   if (h->gaunt) cudaFree(h->gaunt);
   if (h->tpoly) cudaFree(h->tpoly);
   if (h->sfac) cudaFree(h->sfac);
@@ -622,7 +647,9 @@ int lpbfmm_debug_lists(lpbfmm_t h, int l, int a, int lev, int kind, int src, int
                        int64_t *off, int64_t *idx) {
   if (!h) return LPBFMM_ERR_ARG;
   Group *g = find_group(h, l, a);
-  if (!g || lev < 2 || lev > g->D || (kind == 1 && lev != g->D)) return LPBFMM_ERR_ARG;
+  if (!g) return LPBFMM_ERR_ARG;
+  const int leaf = src ? g->D : g->Df;  // leaf level of the reaction / free-space part
+  if (lev < 2 || lev > leaf || (kind == 1 && lev != leaf)) return LPBFMM_ERR_ARG;
   const int32_t *dl = nullptr;
   const int nslot = kind ? NNEAR : NOFF;
   if (kind == 0) dl = src ? g->vreact[lev] : g->vfree[lev];
@@ -721,10 +748,10 @@ int lpbfmm_last_counts(lpbfmm_t h, int64_t *out) {
             k_count_lists<<<(unsigned)((nv + 255) / 256), 256, 0, h->stream>>>(g.vreact[l], nv, d + 1);
         }
       }
-      const int64_t nb = g.T.lev[g.D].n;
+      const int64_t nb = g.T.lev[g.D].n, nbf = g.T.lev[g.Df].n;
       if (g.ufree)
-        k_count_near<<<(unsigned)((nb * NNEAR + 255) / 256), 256, 0, h->stream>>>(g.ufree, nb, g.T.lev[g.D].count,
-                                                                              g.T.lev[g.D].count, d + 2);
+        k_count_near<<<(unsigned)((nbf * NNEAR + 255) / 256), 256, 0, h->stream>>>(g.ufree, nbf, g.T.lev[g.Df].pcount,
+                                                                               g.T.lev[g.Df].pcount, d + 2);
       if (g.ureact)
         k_count_near<<<(unsigned)((nb * NNEAR + 255) / 256), 256, 0, h->stream>>>(g.ureact, nb, g.T.lev[g.D].count,
                                                                               g.I.lev[g.D].count, d + 3);

@@ -997,8 +997,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// e^{-lambda r} = 2^{(-lambda log2 e) r}; field factor (1 + lambda r) / r^2 = (1/r)(1/r + lambda)
-template <int NT>
+// e^{-lambda r} = 2^{(-lambda log2 e) r}; field factor (1 + lambda r) / r^2 = (1/r)(1/r + lambda).
+// MODE by the source box's offset from the target leaf: P2P_SELF (the leaf itself: compensated
+// coordinates, the r = 0 self pair dropped by a select), P2P_TOUCH (a box that touches the leaf:
+// compensated coordinates, r > 0), P2P_APART (a box at least one box away: r >= h, so the FP32
+// rounding of the plain differences, ~2^-23 of 3h, is below 1e-7 of r and the low parts are not
+// used).
+constexpr int P2P_APART = 0, P2P_TOUCH = 1, P2P_SELF = 2;
+template <int NT, int MODE>
 __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int nn,
                                               const float (&px)[4], const float (&py)[4], const float (&pz)[4],
                                               const float (&qx)[4], const float (&qy)[4], const float (&qz)[4],
@@ -1007,14 +1013,23 @@ __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, con
   const float nl2 = -lam * 1.44269504088896341f;
 #pragma unroll 2
   for (int j = 0; j < nn; ++j) {
-    const float4 s = sh[j], sL = sl[j];
+    const float4 s = sh[j];
+    float4 sL = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MODE != P2P_APART) sL = sl[j];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      const float dx = (px[t] - s.x) + (qx[t] - sL.x);
-      const float dy = (py[t] - s.y) + (qy[t] - sL.y);
-      const float dz = (pz[t] - s.z) + (qz[t] - sL.z);
+      float dx, dy, dz;
+      if (MODE == P2P_APART) {
+        dx = px[t] - s.x;
+        dy = py[t] - s.y;
+        dz = pz[t] - s.z;
+      } else {
+        dx = (px[t] - s.x) + (qx[t] - sL.x);
+        dy = (py[t] - s.y) + (qy[t] - sL.y);
+        dz = (pz[t] - s.z) + (qz[t] - sL.z);
+      }
       const float r2 = dx * dx + dy * dy + dz * dz;
-      const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+      const float ri = (MODE == P2P_SELF) ? (r2 > 0.f ? rsqrtf(r2) : 0.f) : rsqrtf(r2);
       const float e = s.w * ex2_approx(nl2 * (r2 * ri)) * ri;
       fp[t] += e;
       const float f = e * ri * (ri + lam);
@@ -1063,14 +1078,24 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
     th[t][0] = a.x; th[t][1] = a.y; th[t][2] = a.z;
     tl[t][0] = b.x; tl[t][1] = b.y; tl[t][2] = b.z;
   }
+  auto mode_of = [&](int k) {
+    int ddx, ddy, ddz;
+    near_decode(nb_o[k], ddx, ddy, ddz);
+    const int ch = cheb3(ddx, ddy, ddz);
+    return ch == 0 ? P2P_SELF : (ch == 1 ? P2P_TOUCH : P2P_APART);
+  };
   auto issue = [&](const P2PCursor &cc, int buf) {
     const uint32_t first = nb_start[cc.k] + cc.off;
     const int nn = (int)min((uint32_t)P2P_WSRC, nb_cnt[cc.k] - cc.off);
-    for (int e = lane; e < 2 * P2P_WSRC; e += 32) {
-      const int j = e >> 1;
-      if (j < nn) {
-        if (e & 1) cp_async16(&sl[buf][j], &l4[first + j], true);
-        else cp_async16(&sh[buf][j], &h4[first + j], true);
+    if (mode_of(cc.k) == P2P_APART) {
+      for (int j = lane; j < nn; j += 32) cp_async16(&sh[buf][j], &h4[first + j], true);
+    } else {
+      for (int e = lane; e < 2 * P2P_WSRC; e += 32) {
+        const int j = e >> 1;
+        if (j < nn) {
+          if (e & 1) cp_async16(&sl[buf][j], &l4[first + j], true);
+          else cp_async16(&sh[buf][j], &h4[first + j], true);
+        }
       }
     }
     cp_commit();
@@ -1095,6 +1120,7 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
     const int nn = (int)min((uint32_t)P2P_WSRC, nb_cnt[cc.k] - cc.off);
     int ddx, ddy, ddz;
     near_decode(nb_o[cc.k], ddx, ddy, ddz);
+    const int mode = mode_of(cc.k);
     p2p_next(cc, nb_cnt);
     float px[4], py[4], pz[4], qx[4], qy[4], qz[4];
     const float dxh = -(float)ddx, dyh = -(float)ddy, dzh = -(float)ddz;
@@ -1105,7 +1131,12 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
       two_sum_shift(th[t][2], tl[t][2], dzh * hh, dzh * hl, pz[t], qz[t]);
     }
     float fp[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fy[4] = {0, 0, 0, 0}, fz[4] = {0, 0, 0, 0};
-    p2p_f32_chunk<NT>(sh[buf], sl[buf], nn, px, py, pz, qx, qy, qz, lam, fp, fx, fy, fz);
+    if (mode == P2P_APART)
+      p2p_f32_chunk<NT, P2P_APART>(sh[buf], sl[buf], nn, px, py, pz, qx, qy, qz, lam, fp, fx, fy, fz);
+    else if (mode == P2P_TOUCH)
+      p2p_f32_chunk<NT, P2P_TOUCH>(sh[buf], sl[buf], nn, px, py, pz, qx, qy, qz, lam, fp, fx, fy, fz);
+    else
+      p2p_f32_chunk<NT, P2P_SELF>(sh[buf], sl[buf], nn, px, py, pz, qx, qy, qz, lam, fp, fx, fy, fz);
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       kahan_add(sp[t], cp[t], fp[t]);
@@ -1765,7 +1796,7 @@ static Geo geo_at(const Group &g, int l) {
 template <typename T>
 static void upward_t(Ctx &c, Group &g, int parts) {
   typedef typename C2<T>::t T2;
-  const int K = c.K, D = g.D;
+  const int K = c.K, D = g.D, Df = g.Df;
   const Tables &tb = sizeof(T) == 8 ? g_tab_d[c.device] : g_tab_f[c.device];
   const bool dofree = g.is_free && (parts & 1);
   const bool doreact = (parts & 2) && g.I.np > 0;
@@ -1780,19 +1811,20 @@ static void upward_t(Ctx &c, Group &g, int parts) {
     const int64_t ntb = g.T.lev[l].n, nib = g.I.lev[l].n;
     g.Lt[l] = c.arena.get<T2>(ntb * K);
     LPB_CUDA(cudaMemsetAsync(g.Lt[l], 0, sizeof(T2) * ntb * K, c.stream));
-    if (dofree) g.Mfree[l] = c.arena.get<T2>(ntb * K);
+    if (dofree && l <= Df) g.Mfree[l] = c.arena.get<T2>(ntb * K);
     if (doreact) g.Mimg[l] = c.arena.get<T2>(nib * g.ntypes * K);
   }
+  // free-space P2M at the free-space leaves (level Df; their point ranges)
   if (dofree)
-    PT_DISPATCH(launch_p2m, c, g.T.lev[D].d_n, g.T.lev[D].n, g.T.lev[D].start, g.T.lev[D].count, nullptr, nullptr, 1,
-                g.T.lev[D].key, g.T, geo_at<T>(g, D), lt_t, g.Mfree[D]);
+    PT_DISPATCH(launch_p2m, c, g.T.lev[Df].d_n, g.T.lev[Df].n, g.T.lev[Df].pstart, g.T.lev[Df].pcount, nullptr,
+                nullptr, 1, g.T.lev[Df].key, g.T, geo_at<T>(g, Df), lt_t, g.Mfree[Df]);
   if (doreact) {
     LPB_CUDA(cudaMemsetAsync(g.Mimg[D], 0, sizeof(T2) * g.I.lev[D].n * g.ntypes * K, c.stream));
     PT_DISPATCH(launch_p2m, c, g.I.d_nseg, g.I.nseg, g.I.seg_start, g.I.seg_count, g.I.seg_box, g.I.seg_type,
                 g.ntypes, g.I.lev[D].key, g.I, geo_at<T>(g, D), lt_i, g.Mimg[D]);
   }
   for (int l = D; l >= 3; --l) {
-    if (dofree && g.T.lev[l - 1].n) {
+    if (dofree && l <= Df && g.T.lev[l - 1].n) {
       k_m2m<T><<<dim3((unsigned)g.T.lev[l - 1].n, 1), M2M_THREADS, 0, c.stream>>>(
           g.T.lev[l - 1].d_n, g.T.lev[l - 1].start, g.T.lev[l - 1].count, g.T.lev[l].key, 1, (const T2 *)g.Mfree[l],
           (T2 *)g.Mfree[l - 1], (const T *)g.op_m2m_t[l], (const T *)tb.rot4, K);
@@ -1839,9 +1871,9 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     items += m2l_tiles(j, TT) * M2L_NSLICE;
   };
   for (auto &g : groups) {
-    const bool dofree = g.is_free && (parts & 1);
     const bool react_far = (parts & 2) && g.I.np > 0 && !(parts & 8);
     for (int l = 2; l <= g.D; ++l) {
+      const bool dofree = g.is_free && (parts & 1) && l <= g.Df;
       const int64_t ntb = g.T.lev[l].n;
       if (!ntb || !(dofree || (react_far && g.vreact[l]))) continue;
       T2 *part = c.arena.get<T2>((size_t)ntb * M2L_NSLOT * c.K);
@@ -1987,25 +2019,27 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
   if (dofree) {
     prof_mark(c, "downward");
+    // the free-space near field at the free-space leaves (level Df)
+    const Level &Lf = g.T.lev[g.Df];
+    const int Df = g.Df;
     if (sizeof(T) == 4) {
-      const unsigned nb = (unsigned)g.T.lev[D].n;
+      const unsigned nb = (unsigned)Lf.n;
       const int64_t np = g.T.np;
       float4 *h4 = c.arena.get<float4>((size_t)np), *l4 = c.arena.get<float4>((size_t)np);
-      k_split_points<<<nb, 64, 0, c.stream>>>(g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count,
-                                               g.T.x, g.T.y, g.T.z, g.T.q, geo_at<T>(g, D), h4, l4);
+      k_split_points<<<nb, 64, 0, c.stream>>>(Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.T.x, g.T.y, g.T.z, g.T.q,
+                                               geo_at<T>(g, Df), h4, l4);
       LPB_LAUNCH();
-      const double hD = g.h(D);
+      const double hD = g.h(Df);
       const float hh = (float)hD, hl = (float)(hD - (double)hh);
-      k_p2p_free_f32<<<(2 * nb + P2P_WARPS - 1) / P2P_WARPS, 32 * P2P_WARPS, 0, c.stream>>>(g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start,
-                                                    g.T.lev[D].count, g.ufree, h4, l4, g.T.src, hh, hl,
-                                                    (float)c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi,
-                                                    field);
+      k_p2p_free_f32<<<(2 * nb + P2P_WARPS - 1) / P2P_WARPS, 32 * P2P_WARPS, 0, c.stream>>>(
+          Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.ufree, h4, l4, g.T.src, hh, hl, (float)c.md.lam[g.l],
+          1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
       LPB_LAUNCH();
       c.launches += 2;
     } else {
-      k_p2p_free<T><<<(unsigned)g.T.lev[D].n, P2P_TPB, 0, c.stream>>>(
-          g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].start, g.T.lev[D].count, g.ufree, g.T.x, g.T.y, g.T.z,
-          g.T.q, g.T.src, geo_at<T>(g, D), c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
+      k_p2p_free<T><<<(unsigned)Lf.n, P2P_TPB, 0, c.stream>>>(
+          Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q, g.T.src, geo_at<T>(g, Df),
+          c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
       LPB_LAUNCH();
       c.launches++;
     }

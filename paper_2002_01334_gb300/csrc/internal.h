@@ -146,6 +146,7 @@ struct Level {
   uint32_t *count = nullptr;  // number of children / points
   uint32_t *parent = nullptr; // parent box index in the coarser level (levels > 2)
   uint32_t *d_n = nullptr;    // device copy of n (written by the scan)
+  uint32_t *pstart = nullptr, *pcount = nullptr;  // points of each box (target trees, every level)
 };
 
 struct PointSet {
@@ -161,7 +162,9 @@ struct PointSet {
 };
 
 struct Group {
-  int l = 0, a = 0, is_free = 0, D = 2, ntypes = 0;
+  // D: depth of the group's trees, the leaf level of the reaction part (images, their near field,
+  // L2P of every target); Df <= D: leaf level of the free-space part (its P2M, near lists, P2P)
+  int l = 0, a = 0, is_free = 0, D = 2, Df = 2, ntypes = 0;
   double root[4] = {0, 0, 0, 0};  // cx, cy, cz (= interface), half-size
   double dI = 0;
   PointSet T, I;
@@ -205,6 +208,8 @@ struct Ctx {
   double stab_lmin = 0.0;
   double *stab_bes = nullptr;
   int tpk = 0;
+  double *adj = nullptr;     // adjoint work space (7 n doubles), grown on demand, kept
+  size_t adj_cap = 0;
   int *status = nullptr;     // device status word
   int *h_status = nullptr;   // pinned
   void *h_pinned = nullptr;  // pinned staging

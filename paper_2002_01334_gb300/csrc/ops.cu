@@ -606,8 +606,9 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
     const double h = g.h(l), hc = h, hp = 2.0 * h;
     Blk b{};
     // M2M: children at level l -> parents at l-1 (only l >= 3)
+    const bool free_l = g.is_free && (parts & 1) && l <= g.Df;  // free-space part lives at levels <= Df
     if (l >= 3) {
-      if (g.is_free && (parts & 1)) {
+      if (free_l) {
         b.m2m_t = total;
         for (int cz = 0; cz < 2; ++cz)
           add(1, 1, 0, lam_t, 0.5 * hc, 0.5 * hc, (cz ? 0.5 : -0.5) * hc, lam_t * hp, lam_t * hc, 1.0,
@@ -633,7 +634,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
             NFREE_CLS + cz, (size_t)cz * 2 * KK);
       total += 4 * KK;
     }
-    if (g.is_free && (parts & 1)) {
+    if (free_l) {
       b.fm2l = total;
       const double pref = lam_t / (2.0 * PI * PI * c.md.eps[g.l]);
       for (int ri = 0; ri < NRHO; ++ri)
@@ -650,10 +651,11 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
   }
   T *ops = c.arena.get<T>(total);
   for (int l = 2; l <= g.D; ++l) {
-    g.op_m2m_t[l] = (l >= 3 && g.is_free && (parts & 1)) ? (void *)(ops + blk[l].m2m_t) : nullptr;
+    const bool free_l = g.is_free && (parts & 1) && l <= g.Df;
+    g.op_m2m_t[l] = (l >= 3 && free_l) ? (void *)(ops + blk[l].m2m_t) : nullptr;
     g.op_m2m_i[l] = (l >= 3 && (parts & 2)) ? (void *)(ops + blk[l].m2m_i) : nullptr;
     g.op_l2l[l] = (l >= 3) ? (void *)(ops + blk[l].l2l) : nullptr;
-    g.op_free[l] = (g.is_free && (parts & 1)) ? (void *)(ops + blk[l].fm2l) : nullptr;
+    g.op_free[l] = free_l ? (void *)(ops + blk[l].fm2l) : nullptr;
   }
   if (!descs.empty()) {
     OpDesc *dd = c.arena.get<OpDesc>(descs.size());

@@ -480,9 +480,35 @@ __global__ void k_fix_last_count(const uint32_t *d_nc, const uint32_t *d_np, con
   if (np) pcount[np - 1] = *d_nc - pstart[np - 1];
 }
 
+// points of every box of a coarser target level: its first child's first point, up to the next
+// box's first point (points are sorted by key, so a box's points are one contiguous run)
+__global__ void k_point_ranges(const uint32_t *d_n, const uint32_t *start, const uint32_t *cpstart, uint32_t np,
+                               uint32_t *pstart, uint32_t *pcount, int64_t cap) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = *d_n;
+  if (b >= n || b >= cap) return;
+  const uint32_t s = cpstart[start[b]];
+  pstart[b] = s;
+  pcount[b] = ((b + 1 < n) ? cpstart[start[b + 1]] : np) - s;
+}
+
 void build_group_boxes(Ctx &c, Group &g) {
   build_levels(c, g.T, g.D, false);
   build_levels(c, g.I, g.D, true);
+  if (g.T.np) {
+    g.T.lev[g.D].pstart = g.T.lev[g.D].start;
+    g.T.lev[g.D].pcount = g.T.lev[g.D].count;
+    for (int l = g.D - 1; l >= 2; --l) {
+      Level &P = g.T.lev[l];
+      const int64_t cap = level_cap(g.T.np, l);
+      P.pstart = c.arena.get<uint32_t>(cap);
+      P.pcount = c.arena.get<uint32_t>(cap);
+      k_point_ranges<<<(unsigned)((cap + 255) / 256), 256, 0, c.stream>>>(P.d_n, P.start, g.T.lev[l + 1].pstart,
+                                                                         (uint32_t)g.T.np, P.pstart, P.pcount, cap);
+      LPB_LAUNCH();
+      c.launches++;
+    }
+  }
   for (int which = 0; which < 2; ++which) {
     PointSet &P = which ? g.I : g.T;
     if (!P.np) continue;
@@ -577,7 +603,7 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
     const int64_t nt = T.n;
     if (!nt) continue;
     const unsigned fb = (unsigned)((nt * NOFF + 255) / 256);
-    if (g.is_free && (parts & 1)) {
+    if (g.is_free && (parts & 1) && l <= g.Df) {
       g.vfree[l] = c.arena.get<int32_t>(nt * NOFF);
       k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, T.key, T.d_n, l, 1, 0, g.a, ws, g.vfree[l], nullptr);
       LPB_LAUNCH();
@@ -599,17 +625,19 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
       c.launches += 2;
     }
   }
+  const int Df = g.Df;
+  const int64_t ntf = g.T.lev[Df].n;
+  if (g.is_free && (parts & 1) && ntf) {
+    g.ufree = c.arena.get<int32_t>(ntf * NNEAR);
+    k_lists<<<(unsigned)((ntf * NNEAR + 255) / 256), 256, 0, c.stream>>>(
+        g.T.lev[Df].key, g.T.lev[Df].d_n, g.T.lev[Df].key, g.T.lev[Df].d_n, Df, 0, 0, g.a, ws, g.ufree, nullptr);
+    LPB_LAUNCH();
+    c.launches++;
+  }
   const int D = g.D;
   const int64_t nt = g.T.lev[D].n;
   if (!nt) return;
   const unsigned nb = (unsigned)((nt * NNEAR + 255) / 256);
-  if (g.is_free && (parts & 1)) {
-    g.ufree = c.arena.get<int32_t>(nt * NNEAR);
-    k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.T.lev[D].key, g.T.lev[D].d_n, D, 0, 0,
-                                      g.a, ws, g.ufree, nullptr);
-    LPB_LAUNCH();
-    c.launches++;
-  }
   if ((parts & 2) && g.I.lev[D].n) {
     g.ureact = c.arena.get<int32_t>(nt * NNEAR);
     k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.I.lev[D].key, g.I.lev[D].d_n, D, 0, 1,

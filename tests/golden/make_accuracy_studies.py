@@ -1,8 +1,9 @@
-"""Accuracy studies quoted in the design notes, rerun from the oracle alone -- TEST INFRASTRUCTURE.
+"""Accuracy studies quoted in the design notes, rerun from the oracle alone (the oracle's CPU FMM
+against its direct sum).  Run from the repository root:
 
-    python -m oracle.studies separation   # free part, one- and two-box separation, p = 4..14
-    python -m oracle.studies reaction     # reaction part at p = 10, 12, 14 (one-box)
-    python -m oracle.studies recurrence   # FMM with table-route T: forward-recurred vs exact tables
+    python tests/golden/make_accuracy_studies.py separation   # free part, one- and two-box, p = 4..14
+    python tests/golden/make_accuracy_studies.py reaction     # reaction part at p = 10, 12, 14 (one-box)
+    python tests/golden/make_accuracy_studies.py recurrence    # table-route T: forward-recurred vs exact tables
 
 All use the three-layer test workload of the GPU tests (N = 3000, seed 21; N = 400 for the
 recurrence study), uniform depth 4 (3), and the oracle's direct sum as reference.  Slow: minutes
@@ -14,13 +15,17 @@ import time
 
 import numpy as np
 
-from . import Medium, S_table, direct
-from . import expansions as E
-from . import fmm
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import Medium, S_table, direct  # noqa: E402
+from oracle import expansions as E  # noqa: E402
+from oracle import fmm  # noqa: E402
 
 
 def _workload(n, seed=21):
-    sys.path.insert(0, __file__.rsplit("/oracle/", 1)[0])
     from paper_2002_01334_gb300 import inputs
     return inputs.workload("three_layer", n=n, seed=seed)
 

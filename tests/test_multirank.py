@@ -58,9 +58,7 @@ def test_single_rank_needs_no_process_group():
     assert bench.job_throughput(1, 1000, 2, 1000.0) == 2000.0
 
 
-def test_profiled_traffic_reads_the_committed_summary(tmp_path):
-    assert bench.profiled_traffic("k_p2p_free_f32") == 134246400
-    assert bench.profiled_traffic("k_m2l_tc") is None
+def test_profiled_traffic_reads_a_summary(tmp_path):
     f = tmp_path / "t.md"
     f.write_text("text\ntraffic_bytes_per_eval k_x 42\n")
     assert bench.profiled_traffic("k_x", str(f)) == 42
