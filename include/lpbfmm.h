@@ -120,6 +120,24 @@ int lpbfmm_eval_parts(lpbfmm_t h, int64_t n, const double *q, const double *xyz,
                       int parts, double *phi, double *field);
 
 /*
+ * The part of lpbfmm_eval carried by chosen target groups, for splitting one evaluation across
+ * devices or streams: the free-space FMM of every layer and the reaction components of every
+ * (layer, interface side) are independent (Sec. 2.2 eq. freereactioncomponents; the paper's
+ * Sec. 4 notes that the components can be computed in parallel), so the sum of the outputs over a
+ * partition equals lpbfmm_eval's output: to FP64 rounding in FP64 mode; in the mixed mode a
+ * group's free-space and reaction local expansions are added in FP32 before they are evaluated,
+ * so a partition that separates them differs by that rounding (about 1e-7 relative).
+ * mask is a host array of 2 (L + 1) ints, entry 2 l + a - 1 for target group (layer l, side a):
+ * bit 0 = the free-space part of layer l (carried by group (l, 1), or (L, 2) for the bottom
+ * layer; the bit is ignored on the other group), bit 1 = the reaction components of targets in
+ * layer l whose polarization sources sit across interface d_l (a = 1) or d_{l-1} (a = 2); entries
+ * of groups that do not exist (a = 1 for l = L, a = 2 for l = 0) are ignored.  Values outside
+ * [0, 3] return LPBFMM_ERR_ARG.  Outputs as lpbfmm_eval (zero where no selected part contributes).
+ */
+int lpbfmm_eval_groups(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
+                       const int32_t *mask, double *phi, double *field);
+
+/*
  * Adjoint of phi with respect to q and positions for an upstream gradient g_phi[n] (device):
  *   g_q[j]   = sum_i g_phi[i] G(r_i, r_j)                  = phi[g_phi](r_j)
  *   g_xyz[j] = sum_i g_phi[i] d phi_i / d r_j = -(q_j field[g_phi](r_j) + g_phi[j] field[q](r_j))

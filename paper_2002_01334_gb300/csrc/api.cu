@@ -207,8 +207,10 @@ static double unord(unsigned long long u) {
 // ---------------------------------------------------------------------------------------
 // evaluation
 // ---------------------------------------------------------------------------------------
+// parts: bits 0, 1 free-space / reaction part, bits 2, 3 diagnostics (lpbfmm_eval_parts); gmask (host,
+// may be null): per target group (l, a) at index 2 l + a - 1, the parts it computes (bits 0, 1)
 static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, const int32_t *layer, int parts,
-                      double *phi, double *field) {
+                      const int32_t *gmask, double *phi, double *field) {
   c.arena.reset();
   c.launches = 0;
   c.nev = 0;
@@ -259,7 +261,9 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
       g.l = l;
       g.a = a;
       g.is_free = (a == ((l < L) ? 1 : 2));
-      if (!(parts & 2) && !g.is_free) continue;
+      g.parts = parts & (gmask ? ((gmask[2 * l + a - 1] & 3) | 12) : 15);
+      if (!g.is_free) g.parts &= ~1;
+      if (!(g.parts & 3)) continue;
       g.ntypes = 2 * L;
       g.dI = (a == 1) ? md.d[l] : md.d[l - 1];
       double H = std::max(std::max(xhi - cx, cx - xlo), std::max(yhi - cy, cy - ylo));
@@ -315,7 +319,7 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
       for (int D = 2; D <= DMAX; ++D)
         if ((uint64_t)g.T.np <= (uint64_t)s * hc[(size_t)k * (DMAX + 1) + D]) { g.Df = D; break; }
       g.D = g.Df;
-      if (parts & 2) {
+      if (g.parts & 2) {
         double zt, zs;
         z_gaps(g, zt, zs);
         while (g.D < std::min(DMAX, g.Df + 2)) {
@@ -356,7 +360,7 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
       ++k;
     }
   }
-  for (auto &g : c.groups) build_group_lists(c, g, parts);
+  for (auto &g : c.groups) build_group_lists(c, g, g.parts);
   prof_mark(c, "tree");
   {
     double lmin = 1e300, hmin = 1e300;
@@ -367,15 +371,15 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     c.stab_bes = nullptr;
   }
   for (auto &g : c.groups) {
-    build_operators(c, g, parts);
-    if ((parts & 2) && g.ureact) {
+    build_operators(c, g, g.parts);
+    if ((g.parts & 2) && g.ureact) {
       double zt, zs;
       z_gaps(g, zt, zs);
       build_near_nodes(c, g, std::max(zt + zs, 1e-12), (c.ws + 1) * std::sqrt(2.0) * g.h(g.D));
     }
   }
   prof_mark(c, "tables+ops");
-  run_fmm_all(c, c.groups, parts, phi, field);
+  run_fmm_all(c, c.groups, phi, field);
   prof_mark(c, "end");
 }
 
@@ -471,7 +475,7 @@ int lpbfmm_eval_parts(lpbfmm_t h, int64_t n, const double *q, const double *xyz,
   if (!h || n < 0 || (n > 0 && (!q || !xyz || !layer_id || !phi)) || parts < 1 || parts > 15) return LPBFMM_ERR_ARG;
   if (n >= (int64_t)1 << 31) return LPBFMM_ERR_UNSUPPORTED;
   try {
-    eval_impl(*h, n, q, xyz, layer_id, parts, phi, field);
+    eval_impl(*h, n, q, xyz, layer_id, parts, nullptr, phi, field);
   } catch (const CudaError &e) {
     return map_error(e);
   } catch (const StatusError &e) {
@@ -483,6 +487,22 @@ int lpbfmm_eval_parts(lpbfmm_t h, int64_t n, const double *q, const double *xyz,
 int lpbfmm_eval(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id, double *phi,
                 double *field) {
   return lpbfmm_eval_parts(h, n, q, xyz, layer_id, 3, phi, field);
+}
+
+int lpbfmm_eval_groups(lpbfmm_t h, int64_t n, const double *q, const double *xyz, const int32_t *layer_id,
+                       const int32_t *mask, double *phi, double *field) {
+  if (!h || !mask || n < 0 || (n > 0 && (!q || !xyz || !layer_id || !phi))) return LPBFMM_ERR_ARG;
+  for (int k = 0; k < 2 * (h->md.L + 1); ++k)
+    if (mask[k] < 0 || mask[k] > 3) return LPBFMM_ERR_ARG;
+  if (n >= (int64_t)1 << 31) return LPBFMM_ERR_UNSUPPORTED;
+  try {
+    eval_impl(*h, n, q, xyz, layer_id, 3, mask, phi, field);
+  } catch (const CudaError &e) {
+    return map_error(e);
+  } catch (const StatusError &e) {
+    return e.code;
+  }
+  return LPBFMM_OK;
 }
 
 __global__ void k_adjoint_combine(int64_t n, const double *q, const double *g, const double *fq, const double *fg,

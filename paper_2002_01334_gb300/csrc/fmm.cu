@@ -997,6 +997,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// 1/sqrt(x) on the special-function unit (max. relative error about 2^-22.9; subnormal inputs
+// flushed to zero, which cannot occur for r^2 of distinct points at the FP32 offsets used here)
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // e^{-lambda r} = 2^{(-lambda log2 e) r}; field factor (1 + lambda r) / r^2 = (1/r)(1/r + lambda).
 // MODE by the source box's offset from the target leaf: P2P_SELF (the leaf itself: compensated
 // coordinates, the r = 0 self pair dropped by a select), P2P_TOUCH (a box that touches the leaf:
@@ -1029,7 +1037,7 @@ __device__ __forceinline__ void p2p_f32_chunk(const float4 *__restrict__ sh, con
         dz = (pz[t] - s.z) + (qz[t] - sL.z);
       }
       const float r2 = dx * dx + dy * dy + dz * dz;
-      const float ri = (MODE == P2P_SELF) ? (r2 > 0.f ? rsqrtf(r2) : 0.f) : rsqrtf(r2);
+      const float ri = (MODE == P2P_SELF) ? (r2 > 0.f ? rsqrt_approx(r2) : 0.f) : rsqrt_approx(r2);
       const float e = s.w * ex2_approx(nl2 * (r2 * ri)) * ri;
       fp[t] += e;
       const float f = e * ri * (ri + lam);
@@ -1843,7 +1851,7 @@ static void upward_t(Ctx &c, Group &g, int parts) {
 
 // every multipole-to-local translation of every group and level in one launch
 template <typename T>
-static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
+static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
   constexpr int TPT = sizeof(T) == 4 ? 4 : 2;
   constexpr int TT = 16 * TPT;
   const Tables &tb = sizeof(T) == 8 ? g_tab_d[c.device] : g_tab_f[c.device];
@@ -1871,6 +1879,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups, int parts) {
     items += m2l_tiles(j, TT) * M2L_NSLICE;
   };
   for (auto &g : groups) {
+    const int parts = g.parts;
     const bool react_far = (parts & 2) && g.I.np > 0 && !(parts & 8);
     for (int l = 2; l <= g.D; ++l) {
       const bool dofree = g.is_free && (parts & 1) && l <= g.Df;
@@ -2055,13 +2064,14 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   }
 }
 
-void run_fmm_all(Ctx &c, std::vector<Group> &groups, int parts, double *phi, double *field) {
+void run_fmm_all(Ctx &c, std::vector<Group> &groups, double *phi, double *field) {
   const bool d = c.opts.precision == LPBFMM_FP64;
-  for (auto &g : groups) d ? upward_t<double>(c, g, parts) : upward_t<float>(c, g, parts);
+  for (auto &g : groups) d ? upward_t<double>(c, g, g.parts) : upward_t<float>(c, g, g.parts);
   prof_mark(c, "upward");
-  d ? m2l_all_t<double>(c, groups, parts) : m2l_all_t<float>(c, groups, parts);
+  d ? m2l_all_t<double>(c, groups) : m2l_all_t<float>(c, groups);
   prof_mark(c, "m2l");
-  for (auto &g : groups) d ? downward_t<double>(c, g, parts, phi, field) : downward_t<float>(c, g, parts, phi, field);
+  for (auto &g : groups)
+    d ? downward_t<double>(c, g, g.parts, phi, field) : downward_t<float>(c, g, g.parts, phi, field);
   prof_mark(c, "downward");
 }
 

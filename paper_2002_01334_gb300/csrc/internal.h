@@ -165,6 +165,7 @@ struct Group {
   // D: depth of the group's trees, the leaf level of the reaction part (images, their near field,
   // L2P of every target); Df <= D: leaf level of the free-space part (its P2M, near lists, P2P)
   int l = 0, a = 0, is_free = 0, D = 2, Df = 2, ntypes = 0;
+  int parts = 3;  // what this group computes: bit 0 free-space part, bit 1 reaction part (+ bits 2, 3 as parts)
   double root[4] = {0, 0, 0, 0};  // cx, cy, cz (= interface), half-size
   double dI = 0;
   PointSet T, I;
@@ -253,7 +254,7 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
                   double *out);
 
 // fmm.cu
-void run_fmm_all(Ctx &c, std::vector<Group> &groups, int parts, double *phi, double *field);
+void run_fmm_all(Ctx &c, std::vector<Group> &groups, double *phi, double *field);
 
 // api.cu
 void prof_mark(Ctx &c, const char *name);

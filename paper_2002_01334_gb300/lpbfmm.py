@@ -45,6 +45,7 @@ def lib():
         L.lpbfmm_create.argtypes = [C.c_int, dp, dp, dp, C.c_int, C.c_double, C.POINTER(Opts), C.POINTER(vp)]
         L.lpbfmm_eval.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.lpbfmm_eval_parts.argtypes = [vp, i64, vp, vp, vp, C.c_int, vp, vp]
+        L.lpbfmm_eval_groups.argtypes = [vp, i64, vp, vp, vp, C.POINTER(C.c_int32), vp, vp]
         L.lpbfmm_adjoint.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.lpbfmm_eval_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(i64), vp, vp, vp, vp, vp]
         L.lpbfmm_debug_tree.argtypes = [vp, C.c_int, C.c_int, dp, C.POINTER(i64), C.POINTER(i64),
@@ -137,6 +138,19 @@ class Context:
                                      _dptr(layer, torch.int32), int(parts), _dptr(phi, torch.float64),
                                      _dptr(fld, torch.float64) if fld is not None else None)
         _check(rc, "lpbfmm_eval")
+        return phi, fld
+
+    def eval_groups(self, q, xyz, layer, mask, field=True):
+        """lpbfmm_eval_groups: the parts of the evaluation that mask (2 (L + 1) ints, entry 2 l + a - 1
+        for target group (l, a): bit 0 free-space, bit 1 reaction) selects."""
+        n = q.shape[0]
+        phi = torch.empty(n, dtype=torch.float64, device=q.device)
+        fld = torch.empty((n, 3), dtype=torch.float64, device=q.device) if field else None
+        m = (C.c_int32 * len(mask))(*[int(v) for v in mask])
+        rc = lib().lpbfmm_eval_groups(self.h, n, _dptr(q, torch.float64), _dptr(xyz, torch.float64),
+                                      _dptr(layer, torch.int32), m, _dptr(phi, torch.float64),
+                                      _dptr(fld, torch.float64) if fld is not None else None)
+        _check(rc, "lpbfmm_eval_groups")
         return phi, fld
 
     def adjoint(self, q, xyz, layer, g_phi):

@@ -272,6 +272,29 @@ def test_reaction_near_field_equals_pairwise_oracle(wsmall, prec, tol):
     assert rel(phi[sel], res) < tol and rel(fld[sel], resf) < tol, (rel(phi[sel], res), rel(fld[sel], resf))
 
 
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("prec,tol", [(F.FP64, 1e-13), (F.MIXED, 1e-6)])
+def test_group_subsets_sum_to_the_whole_evaluation(w3000, world, prec, tol):
+    """lpbfmm_eval_groups on the units that multigpu.assign gives each of `world` ranks: the partial
+    results sum to lpbfmm_eval's result, to FP64 rounding in FP64 mode; in the mixed mode a group's
+    free and reaction local expansions are added in FP32 before L2P when one rank holds both, so a
+    split differs by that rounding (bound 1e-6, the gate)."""
+    from paper_2002_01334_gb300 import multigpu as M
+    w, _ = w3000
+    m = w["medium"]
+    ctx = F.Context(m["d"], m["eps"], m["lam"], 10, precision=prec)
+    q, x, l = tensors(w)
+    phi, fld = ctx.eval(q, x, l)
+    costs = M.unit_costs(np.bincount(w["layer"], minlength=3).tolist())
+    sp, sf = torch.zeros_like(phi), torch.zeros_like(fld)
+    for units in M.assign(costs, world):
+        p, f = ctx.eval_groups(q, x, l, M.group_mask(units, 3))
+        sp += p
+        sf += f
+    torch.cuda.synchronize()
+    assert rel(sp.cpu().numpy(), phi.cpu().numpy()) < tol and rel(sf.cpu().numpy(), fld.cpu().numpy()) < tol
+
+
 def test_deterministic(w3000):
     w, _ = w3000
     for prec in (F.FP64, F.MIXED):

@@ -1,6 +1,7 @@
-"""Multi-rank host logic of bench.py on CPU with the gloo backend (world size 2): every rank
+"""Multi-rank host logic on CPU with the gloo backend (world size 2).  bench.py: every rank
 evaluates its own independent system (distinct seeds, no collective on the data path), the job
-time is the slowest rank's, and throughput counts the targets of all ranks."""
+time is the slowest rank's, and throughput counts the targets of all ranks.  multigpu: one
+evaluation split into disjoint units per rank plus one FP64 sum-reduce equals the one-rank result."""
 import os
 import socket
 
@@ -114,3 +115,78 @@ def test_clock_summary_reads_median_max_and_active_reasons():
     assert s["sm_mhz"] == 2040.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
     assert s["samples"] == 3
     assert bench.ClockSampler(0).summary()["samples"] == 0
+
+
+# ---------------------------------------------------------------------------------------------
+# one evaluation split across ranks (paper_2002_01334_gb300.multigpu): disjoint units of work,
+# one FP64 sum-reduce; checked with the oracle's direct sum as each rank's evaluator
+# ---------------------------------------------------------------------------------------------
+def test_assignment_is_a_balanced_partition():
+    from paper_2002_01334_gb300 import multigpu as M
+    costs = M.unit_costs([333334, 333333, 333333])
+    assert len(costs) == 6
+    for world in (1, 2, 3, 4, 8):
+        plan = M.assign(costs, world)
+        got = sorted(k for p in plan for k in p)
+        assert got == list(range(6))  # every unit exactly once
+        loads = [sum(costs[k] for k in p) for p in plan]
+        # LPT: no rank above the optimum by more than the largest unit
+        assert max(loads) <= sum(costs) / world + max(costs) + 1e-9
+    assert M.assign(costs, 2) == M.assign(list(costs), 2)  # deterministic
+
+
+def test_group_mask_of_units():
+    from paper_2002_01334_gb300 import multigpu as M
+    # units: (0, free) (0, react) (1, free) (1, react) (2, free) (2, react)
+    assert M.group_mask([0], 3) == [1, 1, 0, 0, 0, 0]
+    assert M.group_mask([3, 4], 3) == [0, 0, 2, 2, 1, 1]
+    assert M.group_mask(range(6), 3) == [3] * 6
+
+
+def _partition_main(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2002_01334_gb300 import multigpu as M
+        w = inputs.workload("three_layer", n=240, seed=77)
+        md = oracle.Medium(**w["medium"])
+        n, nl = len(w["q"]), 3
+
+        def ev(mask):  # the oracle's direct sum of the selected units, standing in for the GPU
+            phi, fld = np.zeros(n), np.zeros((n, 3))
+            for l in range(nl):
+                tg = np.nonzero(w["layer"] == l)[0]
+                for bit in (1, 2):
+                    if (mask[2 * l] | mask[2 * l + 1]) & bit:
+                        p, f = oracle.direct(md, w["q"], w["xyz"], w["layer"], targets=tg, parts=bit)
+                        phi[tg] += p
+                        fld[tg] += f
+            return torch.tensor(phi), torch.tensor(fld)
+
+        def red(t):
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        counts = np.bincount(w["layer"], minlength=nl).tolist()
+        phi, fld = M.partitioned(ev, n, nl, M.unit_costs(counts), rank, world, red)
+        out[rank] = (phi.numpy().copy(), fld.numpy().copy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partitioned_evaluation_equals_one_rank():
+    """Two gloo ranks take disjoint units (layer, free or reaction part), evaluate them, and one
+    FP64 sum-reduce gives both ranks the whole potential and field: equal to the one-rank direct
+    sum to rounding, and identical on the two ranks."""
+    import oracle
+    world = 2
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_partition_main, args=(world, port, out), nprocs=world, join=True)
+    w = inputs.workload("three_layer", n=240, seed=77)
+    ref_phi, ref_fld = oracle.direct(oracle.Medium(**w["medium"]), w["q"], w["xyz"], w["layer"])
+    for r in range(world):
+        phi, fld = out[r]
+        assert np.abs(phi - ref_phi).max() <= 1e-13 * np.abs(ref_phi).max()
+        assert np.abs(fld - ref_fld).max() <= 1e-13 * np.abs(ref_fld).max()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
