@@ -84,7 +84,7 @@ def test_benchmark_oracle_fixture_matches_the_oracle_and_the_bench_workload():
     assert fx is not None and fx["seed"] == mk.SEED and bench.load_oracle_fixture(999, mk.SEED) is None
     w = inputs.workload("three_layer", n=1000000, seed=bench.rank_seed(0))
     assert fx["targets"] == mk.sample_targets(w["layer"], fx["per_layer"], fx["seed"])
-    assert len(fx["targets"]) == 24 and len(set(fx["targets"])) == 24
+    assert len(fx["targets"]) == 1002 and len(set(fx["targets"])) == 1002
     oracle.build()
     md = oracle.Medium(**w["medium"])
     k = 9  # one stored target, recomputed (about 40 s of one core)
