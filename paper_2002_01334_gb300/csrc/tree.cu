@@ -537,10 +537,30 @@ __device__ __forceinline__ int64_t find_key(const uint64_t *keys, int64_t n, uin
   return -1;
 }
 
+// dense box index of a level: grid[Morton key] = box index or -1 (levels up to GRID_LEV_MAX)
+constexpr int GRID_LEV_MAX = 8;
+__global__ void k_grid_fill(const uint64_t *key, const uint32_t *d_n, int32_t *grid, int64_t cap) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < *d_n && b < cap) grid[key[b]] = (int32_t)b;
+}
+static const int32_t *level_grid(Ctx &c, const Level &L, int lev, int64_t np) {
+  if (lev > GRID_LEV_MAX || !L.n) return nullptr;
+  const size_t cells = (size_t)1 << (3 * lev);
+  int32_t *grid = c.arena.get<int32_t>(cells);
+  LPB_CUDA(cudaMemsetAsync(grid, 0xff, sizeof(int32_t) * cells, c.stream));
+  const int64_t cap = level_cap(np, lev);
+  k_grid_fill<<<(unsigned)((cap + 255) / 256), 256, 0, c.stream>>>(L.key, L.d_n, grid, cap);
+  LPB_LAUNCH();
+  c.launches++;
+  return grid;
+}
+
 // far = 1: V list over NOFF slots; far = 0: near list over NNEAR slots
 // react: reaction list (targets vs images): also records the classes in use
+// sgrid: dense box index of the source level (nullptr: binary search in skey)
 __global__ void k_lists(const uint64_t *tkey, const uint32_t *d_nt, const uint64_t *skey, const uint32_t *d_ns,
-                        int lev, int far, int react, int a, int ws, int32_t *out, uint8_t *used) {
+                        const int32_t *sgrid, int lev, int far, int react, int a, int ws, int32_t *out,
+                        uint8_t *used) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nslot = far ? NOFF : NNEAR;
   const int64_t t = gid / nslot;
@@ -565,7 +585,7 @@ __global__ void k_lists(const uint64_t *tkey, const uint32_t *d_nt, const uint64
   const int64_t ns = *d_ns;
   if (ok && ns > 0) {
     const uint64_t sk = (spread3(jx) << 2) | (spread3(jy) << 1) | spread3(jz);
-    const int64_t s = find_key(skey, ns, sk);
+    const int64_t s = sgrid ? (int64_t)sgrid[sk] : find_key(skey, ns, sk);
     if (s >= 0) {
       res = (int32_t)s;
       if (react && far && used) {
@@ -605,7 +625,8 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
     const unsigned fb = (unsigned)((nt * NOFF + 255) / 256);
     if (g.is_free && (parts & 1) && l <= g.Df) {
       g.vfree[l] = c.arena.get<int32_t>(nt * NOFF);
-      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, T.key, T.d_n, l, 1, 0, g.a, ws, g.vfree[l], nullptr);
+      const int32_t *tg = level_grid(c, T, l, g.T.np);
+      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, T.key, T.d_n, tg, l, 1, 0, g.a, ws, g.vfree[l], nullptr);
       LPB_LAUNCH();
       c.launches++;
     }
@@ -613,7 +634,8 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
       g.vreact[l] = c.arena.get<int32_t>(nt * NOFF);
       g.used[l] = c.arena.get<uint8_t>(NREACT_CLS);
       LPB_CUDA(cudaMemsetAsync(g.used[l], 0, NREACT_CLS, c.stream));
-      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, I.key, I.d_n, l, 1, 1, g.a, ws, g.vreact[l], g.used[l]);
+      const int32_t *ig = level_grid(c, I, l, g.I.np);
+      k_lists<<<fb, 256, 0, c.stream>>>(T.key, T.d_n, I.key, I.d_n, ig, l, 1, 1, g.a, ws, g.vreact[l], g.used[l]);
       LPB_LAUNCH();
       g.rows[l] = c.arena.get<int32_t>((size_t)NKT * nt);
       g.nrows[l] = c.arena.get<uint32_t>(NKT);
@@ -630,7 +652,8 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
   if (g.is_free && (parts & 1) && ntf) {
     g.ufree = c.arena.get<int32_t>(ntf * NNEAR);
     k_lists<<<(unsigned)((ntf * NNEAR + 255) / 256), 256, 0, c.stream>>>(
-        g.T.lev[Df].key, g.T.lev[Df].d_n, g.T.lev[Df].key, g.T.lev[Df].d_n, Df, 0, 0, g.a, ws, g.ufree, nullptr);
+        g.T.lev[Df].key, g.T.lev[Df].d_n, g.T.lev[Df].key, g.T.lev[Df].d_n, nullptr, Df, 0, 0, g.a, ws, g.ufree,
+        nullptr);
     LPB_LAUNCH();
     c.launches++;
   }
@@ -640,8 +663,8 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
   const unsigned nb = (unsigned)((nt * NNEAR + 255) / 256);
   if ((parts & 2) && g.I.lev[D].n) {
     g.ureact = c.arena.get<int32_t>(nt * NNEAR);
-    k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.I.lev[D].key, g.I.lev[D].d_n, D, 0, 1,
-                                      g.a, ws, g.ureact, nullptr);
+    k_lists<<<nb, 256, 0, c.stream>>>(g.T.lev[D].key, g.T.lev[D].d_n, g.I.lev[D].key, g.I.lev[D].d_n, nullptr, D, 0,
+                                      1, g.a, ws, g.ureact, nullptr);
     LPB_LAUNCH();
     c.launches++;
   }
