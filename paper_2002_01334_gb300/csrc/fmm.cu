@@ -1429,10 +1429,12 @@ __host__ __device__ __forceinline__ int tc_remap(int c, int K, int p) {
   return n <= p ? n * (n + 1) / 2 : -1;
 }
 
-// W_c for every class and source type: [ncls * ntypes][ldr rows (outputs)][ldr cols], hi and lo;
-// classes that used[] marks absent at this level are skipped
+// W_c of every class and source type as the shared-memory image the MMA reads: per (class, type)
+// a block of NC K-chunks, each [hi: ldr rows x 128 bytes][lo: ldr rows x 128 bytes] in the
+// 128-byte swizzled K-major layout (tc::swz), so that one bulk copy moves a class's operator into
+// shared memory.  Classes that used[] marks absent at this level are skipped.
 __global__ void k_tc_pack_w(const float *ops, int ncls_types, int ntypes, const uint8_t *used, int K, int p, int ldr,
-                            float *whi, float *wlo) {
+                            float *wimg) {
   __shared__ int code[256];
   const int ct = blockIdx.x;
   if (ct >= ncls_types || (used && !used[ct / ntypes])) return;
@@ -1441,6 +1443,8 @@ __global__ void k_tc_pack_w(const float *ops, int ncls_types, int ntypes, const 
   const size_t KK = (size_t)K * K;
   const float *P = ops + (size_t)ct * 2 * KK, *Q = P + KK;
   const int total = ldr * ldr;
+  unsigned char *blk = (unsigned char *)(wimg + (size_t)ct * 2 * ldr * ldr);
+  const size_t tile = (size_t)ldr * 128;  // bytes of one hi (or lo) chunk tile
   for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < total; e += gridDim.y * blockDim.x) {
     const int r = e / ldr, k = e % ldr;
     const int ro = code[r], ko = code[k];
@@ -1448,9 +1452,9 @@ __global__ void k_tc_pack_w(const float *ops, int ncls_types, int ntypes, const 
     if (ro >= 0 && ko >= 0) w = P[(size_t)ro * K + ko];
     else if (ro <= -2 && ko <= -2) w = Q[(size_t)(-ro - 2) * K + (-ko - 2)];
     const float h = tc::to_tf32(w);
-    const size_t at = ((size_t)ct * ldr + r) * ldr + k;
-    whi[at] = h;
-    wlo[at] = tc::to_tf32(w - h);
+    unsigned char *ch = blk + (size_t)(k >> 5) * 2 * tile;
+    *(float *)(ch + tc::swz(r, k & 31)) = h;
+    *(float *)(ch + tile + tc::swz(r, k & 31)) = tc::to_tf32(w - h);
   }
 }
 
@@ -1466,7 +1470,7 @@ __global__ void k_tc_pack_raw(const float2 *M, int64_t nrows, int K, int p, int 
 
 struct TJob {
   const float *raw;         // source rows [nsb][ntypes][ldr], unrotated real coordinates
-  const float *whi, *wlo;   // [ncls][ntypes][ldr][ldr]
+  const float *wimg;        // [ncls][ntypes] operator images (k_tc_pack_w)
   const float *rot;         // [NOFF][PMAX+1][2] cos, sin of m phi
   const int32_t *vlist;     // [ntb][NOFF]
   const int32_t *cls_of;    // [NOFF]
@@ -1488,6 +1492,27 @@ __host__ __device__ constexpr int tc_nst(int NC) { return NC <= 5 ? 3 : 2; }
 __host__ __device__ constexpr size_t tc_stage_bytes(int NC) { return (size_t)2 * (TC_ROWS + 32 * NC) * 128; }
 static size_t tc_smem(int NC) { return tc_nst(NC) * tc_stage_bytes(NC) + 1024; }
 
+__device__ __forceinline__ uint64_t to_global(const void *p) {
+  uint64_t g;
+  asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(p));
+  return g;
+}
+// one arrival that also announces tx bytes to come by bulk copies
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                   tc::smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+// bulk copy of bytes (multiple of 16, both addresses 16-byte aligned) global -> shared, completing
+// on mbar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(to_global(src)), "r"(bytes), "r"(tc::smem_u32(mbar))
+               : "memory");
+}
+
 template <int NC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int njobs, int K, int p, int *status) {
   constexpr int N = 32 * NC, NST = tc_nst(NC);
@@ -1503,7 +1528,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   __shared__ unsigned hasmask[HASW];
   // full[b]: the workers have staged buffer b (TC_WORKERS arrivals); empty[b]: its MMAs are done;
   // accbar[a]: a step's MMAs into accumulator a are done; foldbar[a]: the workers have read it
-  __shared__ uint64_t full[NST], empty[NST], accbar[2], foldbar[2];
+  // wfull[b]: the operator chunk of buffer b has landed (one bulk copy, issued by thread 0)
+  __shared__ uint64_t full[NST], empty[NST], accbar[2], foldbar[2], wfull[NST];
   __shared__ uint32_t tbase;
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
@@ -1572,6 +1598,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     for (int b = 0; b < NST; ++b) {
       tc::mbar_init(&full[b], TC_WORKERS);
       tc::mbar_init(&empty[b], 1);
+      tc::mbar_init(&wfull[b], 1);
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(&accbar[a], 1);
@@ -1622,6 +1649,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     return ok;
   };
   bool fail = false;
+  int wl_last = -1;  // last stage whose operator chunk thread 0 requested
   if (worker) {
     int cur_o = -1, my_src = -1;
     // stage s is copied at iteration s and rotated / split at iteration s + 1; the MMA thread takes
@@ -1639,15 +1667,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
           my_src = myt >= 0 ? J.vlist[(size_t)myt * NOFF + o] : -1;
         }
         unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
-        unsigned char *Ah = st, *Bh = st + 2 * SA, *Bl = st + 2 * SA + SB;
-        {
+        unsigned char *Ah = st, *Bh = st + 2 * SA;
+        if (tid == 0) {
+          // the class operator's K-chunk (hi and lo tiles, one contiguous image) by one bulk copy
           const size_t ct = (size_t)J.cls_of[o] * ntypes + tau;
-          const float *wh = J.whi + ct * N * N + kc * 32, *wl = J.wlo + ct * N * N + kc * 32;
-          for (int e = tid; e < N * 8; e += TC_WORKERS) {
-            const int r = e >> 3, u = e & 7;
-            cp_async16(Bh + tc::swz16(r, u), wh + (size_t)r * N + 4 * u, true);
-            cp_async16(Bl + tc::swz16(r, u), wl + (size_t)r * N + 4 * u, true);
-          }
+          const unsigned char *src = (const unsigned char *)(J.wimg + ct * 2 * N * N) + (size_t)kc * 2 * SB;
+          mbar_expect_tx(&wfull[b], (uint32_t)(2 * SB));
+          bulk_g2s(Bh, src, (uint32_t)(2 * SB), &wfull[b]);
+          wl_last = s;
         }
         {
           // this thread's source row chunk, unrotated, into the A-hi slots (rotated next iteration)
@@ -1712,6 +1739,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
       }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
+    // no bulk copy may still be writing this CTA's shared memory when it exits
+    if (tid == 0 && fail && wl_last >= 0)
+      tc::mbar_wait(&wfull[wl_last % NST], (uint32_t)((wl_last / NST) & 1), TC_WAIT);
     if (!fail && !fold(ns - 1)) fail = true;
     if (!fail) {
       const int t = tid_[row];
@@ -1735,7 +1765,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     int last = -1;
     for (int sc = 0; sc < S; ++sc) {
       const int b = sc % NST, si = sc / NC, kc = sc % NC;
-      if (!tc::mbar_wait(&full[b], (uint32_t)((sc / NST) & 1), TC_WAIT)) {
+      if (!tc::mbar_wait(&full[b], (uint32_t)((sc / NST) & 1), TC_WAIT) ||
+          !tc::mbar_wait(&wfull[b], (uint32_t)((sc / NST) & 1), TC_WAIT)) {
         fail = true;
         break;
       }
@@ -1894,9 +1925,9 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
       if (dofree && use_tc) {
         // tensor-core path: the level's class operators as TF32 hi/lo real matrices
         const int N = 32 * tc_nc;
-        float *whi = c.arena.get<float>((size_t)NFREE_CLS * N * N), *wlo = c.arena.get<float>((size_t)NFREE_CLS * N * N);
+        float *wimg = c.arena.get<float>((size_t)NFREE_CLS * 2 * N * N);
         k_tc_pack_w<<<dim3(NFREE_CLS, 4), 256, 0, c.stream>>>((const float *)g.op_free[l], NFREE_CLS, 1, nullptr,
-                                                               c.K, c.p, N, whi, wlo);
+                                                               c.K, c.p, N, wimg);
         LPB_LAUNCH();
         c.launches++;
         float *raw = c.arena.get<float>((size_t)ntb * N);
@@ -1905,7 +1936,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         LPB_LAUNCH();
         c.launches++;
         TJob j;
-        j.raw = raw; j.whi = whi; j.wlo = wlo; j.rot = (const float *)tb.rot;
+        j.raw = raw; j.wimg = wimg; j.rot = (const float *)tb.rot;
         j.vlist = g.vfree[l]; j.cls_of = tb.cls_free; j.tlist = nullptr; j.d_ntl = nullptr;
         j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = 0; j.ntypes = 1;
         const Level *par = l >= 3 ? &g.T.lev[l - 1] : nullptr;
@@ -1924,9 +1955,9 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         // tensor-core reaction path: class operators per (class, source type)
         const int N = 32 * tc_nc;
         const int nct = NREACT_CLS * g.ntypes;
-        float *whi = c.arena.get<float>((size_t)nct * N * N), *wlo = c.arena.get<float>((size_t)nct * N * N);
+        float *wimg = c.arena.get<float>((size_t)nct * 2 * N * N);
         k_tc_pack_w<<<dim3(nct, 4), 256, 0, c.stream>>>((const float *)g.op_react[l], nct, g.ntypes, g.used[l], c.K,
-                                                        c.p, N, whi, wlo);
+                                                        c.p, N, wimg);
         LPB_LAUNCH();
         c.launches++;
         const int64_t nir = g.I.lev[l].n * g.ntypes;
@@ -1937,7 +1968,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         c.launches++;
         for (int kt = 0; kt < 2 * c.ws + 1; ++kt) {
           TJob j;
-          j.raw = raw; j.whi = whi; j.wlo = wlo; j.rot = (const float *)tb.rot;
+          j.raw = raw; j.wimg = wimg; j.rot = (const float *)tb.rot;
           j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * NKT + kt) * NOFF;
           j.tlist = g.rows[l] + (size_t)kt * ntb; j.d_ntl = g.nrows[l] + kt;
           j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = M2L_NSLICE; j.ntypes = g.ntypes;
