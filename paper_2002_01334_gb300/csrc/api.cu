@@ -585,6 +585,7 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (h->tpoly) cudaFree(h->tpoly);
   if (h->sfac) cudaFree(h->sfac);
   if (h->phat_dir) cudaFree(h->phat_dir);
+  if (h->rotcol) cudaFree(h->rotcol);
   if (h->status) cudaFree(h->status);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int k = 0; k < 64; ++k)

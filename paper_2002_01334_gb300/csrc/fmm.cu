@@ -1365,6 +1365,7 @@ static void make_tables(Ctx &c) {
 
 void upload_gl16();
 void upload_an();
+void make_rotcol(Ctx &c);
 void init_fmm_tables(Ctx &c) {
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
@@ -1372,6 +1373,7 @@ void init_fmm_tables(Ctx &c) {
   upload_an();
   make_tables(c);
   upload_consts(c.stream);
+  make_rotcol(c);
 }
 
 template <typename T, int PT>
@@ -1429,6 +1431,37 @@ __host__ __device__ __forceinline__ int tc_remap(int c, int K, int p) {
   return n <= p ? n * (n + 1) / 2 : -1;
 }
 
+// (cos m phi, sin m phi) of every far offset's azimuth phi for each real coordinate pair of the
+// tensor-core layout: entry [o][c], [o][c + 1] for the (Re, Im) columns c, c + 1 of a coefficient
+// of order m; (1, 0) for the columns of m = 0 real parts and padding, which no rotation changes.
+// Per context (the layout depends on p); built once in lpbfmm_create.
+void make_rotcol(Ctx &c) {
+  const int R = 2 * c.K - (c.p + 1), NC = (R + 31) / 32, N = 32 * NC;
+  if (NC > 4) return;  // only the tensor-core path (p <= 10) uses it
+  const int NI2 = 2 * (c.K - (c.p + 1));
+  std::vector<float> t((size_t)NOFF * N);
+  for (int o = 0; o < NOFF; ++o) {
+    int dx, dy, dz;
+    off_decode(o, dx, dy, dz);
+    const double ph = (dx == 0 && dy == 0) ? 0.0 : atan2(-(double)dy, -(double)dx);
+    for (int col = 0; col < N; col += 2) {
+      double cs = 1.0, sn = 0.0;
+      if (col < NI2) {
+        const int h = tc_remap(col, c.K, c.p);  // real part of half index h
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= h) ++n;
+        const int m = h - n * (n + 1) / 2;
+        cs = cos(m * ph);
+        sn = sin(m * ph);
+      }
+      t[(size_t)o * N + col] = (float)cs;
+      t[(size_t)o * N + col + 1] = (float)sn;
+    }
+  }
+  LPB_CUDA(cudaMalloc(&c.rotcol, sizeof(float) * t.size()));
+  LPB_CUDA(cudaMemcpy(c.rotcol, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice));
+}
+
 // W_c of every class and source type as the shared-memory image the MMA reads: per (class, type)
 // a block of NC K-chunks, each [hi: ldr rows x 128 bytes][lo: ldr rows x 128 bytes] in the
 // 128-byte swizzled K-major layout (tc::swz), so that one bulk copy moves a class's operator into
@@ -1471,7 +1504,7 @@ __global__ void k_tc_pack_raw(const float2 *M, int64_t nrows, int K, int p, int 
 struct TJob {
   const float *raw;         // source rows [nsb][ntypes][ldr], unrotated real coordinates
   const float *wimg;        // [ncls][ntypes] operator images (k_tc_pack_w)
-  const float *rot;         // [NOFF][PMAX+1][2] cos, sin of m phi
+  const float *rotcol;      // [NOFF][ldr] (cos, sin) of m phi per real column pair (make_rotcol)
   const int32_t *vlist;     // [ntb][NOFF]
   const int32_t *cls_of;    // [NOFF]
   const int32_t *tlist;     // target boxes (nullptr: octant or plain tiles over 0..ntb-1)
@@ -1513,6 +1546,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                : "memory");
 }
 
+// x rounded to TF32 (10 stored significand bits), to nearest with ties away from zero, in integer
+// arithmetic on the FP32 bits: the rounding of cvt.rna.tf32.f32 for the finite values here, on
+// the integer pipes (the split of every staged source row runs once per step)
+__device__ __forceinline__ float tf32i(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
 template <int NC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int njobs, int K, int p, int *status) {
   constexpr int N = 32 * NC, NST = tc_nst(NC);
@@ -1613,7 +1652,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   const uint32_t tmem = tbase, lanebase = (uint32_t)((warp & 3) * 32) << 16;
   const int S = ns * NC;  // stages: (step, K-chunk)
   const int myt = worker ? tid_[row] : -1;
-  const int NI2 = 2 * (K - (p + 1));  // columns holding (Re, Im) pairs
   constexpr uint32_t IDESC = tc::idesc_tf32(TC_ROWS, N);
   constexpr int NH = N / 2;  // accumulator columns per thread
   float racc[NH];
@@ -1624,23 +1662,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     const bool ok = tc::mbar_wait(&accbar[i & 1], (uint32_t)((i >> 1) & 1), TC_WAIT);
     if (ok) {
       tc::fence_after();
-      const float *rc = J.rot + (size_t)(steps[i] >> 4) * (PMAX + 1) * 2;
+      const float4 *rr = (const float4 *)(J.rotcol + (size_t)(steps[i] >> 4) * N + hf * NH);
       const uint32_t col = (uint32_t)((i & 1) * N + hf * NH);
 #pragma unroll
-      for (int c0 = 0; c0 < NH; c0 += 8) {
-        float v[8];
-        tc::tmem_ld8(tmem + lanebase + col + (uint32_t)c0, v);
+      for (int c1 = 0; c1 < NH; c1 += 32) {
+        uint32_t v[4][8];
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          const int c = hf * NH + c0 + j;
-          if (c < NI2) {
-            const int m = mcol[c];
-            const float cm = __ldg(rc + 2 * m), sm = __ldg(rc + 2 * m + 1);
-            racc[c0 + j] += cm * v[j] + sm * v[j + 1];
-            racc[c0 + j + 1] += cm * v[j + 1] - sm * v[j];
-          } else {
-            racc[c0 + j] += v[j];
-            racc[c0 + j + 1] += v[j + 1];
+        for (int q = 0; q < 4; ++q) tc::tmem_ld8_nw(tmem + lanebase + col + (uint32_t)(c1 + 8 * q), v[q]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c0 = c1 + 8 * q;
+          const float4 ra = __ldg(rr + c0 / 4), rb = __ldg(rr + c0 / 4 + 1);
+          const float cs[4] = {ra.x, ra.z, rb.x, rb.z}, sn[4] = {ra.y, ra.w, rb.y, rb.w};
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            const float vr = __uint_as_float(v[q][j]), vi = __uint_as_float(v[q][j + 1]);
+            racc[c0 + j] += cs[j / 2] * vr + sn[j / 2] * vi;
+            racc[c0 + j + 1] += cs[j / 2] * vi - sn[j / 2] * vr;
           }
         }
       }
@@ -1693,35 +1732,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
         // rotate this thread's half row by e^{i mu phi} and split it into TF32 hi (in place) + lo
         unsigned char *st = sbase + (size_t)(sc % NST) * tc_stage_bytes(NC);
         unsigned char *Ah = st, *Al = st + SA;
-        const float *rc = J.rot + (size_t)(steps[si] >> 4) * (PMAX + 1) * 2;
+        const float4 *rr = (const float4 *)(J.rotcol + (size_t)(steps[si] >> 4) * N + kc * 32);
 #pragma unroll
         for (int uu = 0; uu < 4; ++uu) {
           const int u = hf * 4 + uu;
           float4 x = *(float4 *)(Ah + tc::swz16(row, u));
-          const int c = kc * 32 + 4 * u;
-          if (c < NI2) {
-            const int m0 = mcol[c];
-            const float c0 = __ldg(rc + 2 * m0), s0 = __ldg(rc + 2 * m0 + 1);
-            const float xr = c0 * x.x - s0 * x.y, xi = s0 * x.x + c0 * x.y;
-            x.x = xr;
-            x.y = xi;
-          }
-          if (c + 2 < NI2) {
-            const int m1 = mcol[c + 2];
-            const float c1 = __ldg(rc + 2 * m1), s1 = __ldg(rc + 2 * m1 + 1);
-            const float xr = c1 * x.z - s1 * x.w, xi = s1 * x.z + c1 * x.w;
-            x.z = xr;
-            x.w = xi;
-          }
+          const float4 r = __ldg(rr + u);  // (cos, sin) of the unit's two column pairs
+          const float xr0 = r.x * x.x - r.y * x.y, xi0 = r.y * x.x + r.x * x.y;
+          const float xr1 = r.z * x.z - r.w * x.w, xi1 = r.w * x.z + r.z * x.w;
+          x = make_float4(xr0, xi0, xr1, xi1);
           float4 h4v, l4v;
-          h4v.x = tc::to_tf32(x.x);
-          h4v.y = tc::to_tf32(x.y);
-          h4v.z = tc::to_tf32(x.z);
-          h4v.w = tc::to_tf32(x.w);
-          l4v.x = tc::to_tf32(x.x - h4v.x);
-          l4v.y = tc::to_tf32(x.y - h4v.y);
-          l4v.z = tc::to_tf32(x.z - h4v.z);
-          l4v.w = tc::to_tf32(x.w - h4v.w);
+          h4v.x = tf32i(x.x);
+          h4v.y = tf32i(x.y);
+          h4v.z = tf32i(x.z);
+          h4v.w = tf32i(x.w);
+          l4v.x = tf32i(x.x - h4v.x);
+          l4v.y = tf32i(x.y - h4v.y);
+          l4v.z = tf32i(x.z - h4v.z);
+          l4v.w = tf32i(x.w - h4v.w);
           *(float4 *)(Ah + tc::swz16(row, u)) = h4v;
           *(float4 *)(Al + tc::swz16(row, u)) = l4v;
         }
@@ -1936,7 +1964,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         LPB_LAUNCH();
         c.launches++;
         TJob j;
-        j.raw = raw; j.wimg = wimg; j.rot = (const float *)tb.rot;
+        j.raw = raw; j.wimg = wimg; j.rotcol = c.rotcol;
         j.vlist = g.vfree[l]; j.cls_of = tb.cls_free; j.tlist = nullptr; j.d_ntl = nullptr;
         j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = 0; j.ntypes = 1;
         const Level *par = l >= 3 ? &g.T.lev[l - 1] : nullptr;
@@ -1968,7 +1996,7 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         c.launches++;
         for (int kt = 0; kt < 2 * c.ws + 1; ++kt) {
           TJob j;
-          j.raw = raw; j.wimg = wimg; j.rot = (const float *)tb.rot;
+          j.raw = raw; j.wimg = wimg; j.rotcol = c.rotcol;
           j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * NKT + kt) * NOFF;
           j.tlist = g.rows[l] + (size_t)kt * ntb; j.d_ntl = g.nrows[l] + kt;
           j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = M2L_NSLICE; j.ntypes = g.ntypes;

@@ -204,7 +204,8 @@ struct Ctx {
   double *gaunt = nullptr;   // [(p+1)^2 in][(p+1)^2 out][2p+1]
   double *tpoly = nullptr;   // [K][TPK] Legendre-product coefficients
   double *sfac = nullptr;    // [KMAX_TAB+1][KMAX_TAB+1]: sqrt((K+d)! (K-d)!) for d <= K
-  double *phat_dir = nullptr;  // [72][(2p+1)(2p+2)/2]: Phat_q^k(cos theta) of the operator directions
+  double *phat_dir = nullptr;  // [NDIR][(2p+1)(2p+2)/2]: Phat_q^k(cos theta) of the operator directions
+  float *rotcol = nullptr;     // tensor-core M2L: [NOFF][32 NC] (cos, sin) of m phi per real column pair
   // per evaluation: grading of the shared Sommerfeld node set and its Bessel columns
   double stab_lmin = 0.0;
   double *stab_bes = nullptr;
