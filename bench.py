@@ -35,10 +35,12 @@ METRIC = "targets/sec (potential+field) N=1M 3-layer @relL2<=1e-6: mixed vs FP64
 # the paper's own workload (Sec. 4: charges in three irregular bodies, eps = (1, 8.6, 20.5),
 # lambda = (1.2, 0.5, 2.1)), for context beside its CPU timings; not the headline metric
 METRIC_PAPER = "targets/sec (potential+field) paper irregular-body 3-layer workload: mixed FMM"
+# the batching form: 256 independent systems in random 2- to 4-layer media, one batched call
+METRIC_BATCH = "targets/sec (potential+field) 256 independent systems N=1e3..6.4e4, p=8: batched mixed FMM"
 
 
 def metric_of(workload):
-    return METRIC if workload == "three_layer" else METRIC_PAPER
+    return {"three_layer": METRIC, "paper_irregular": METRIC_PAPER, "batch": METRIC_BATCH}[workload]
 N_DEFAULT = 1000000
 P_DEFAULT = 10
 
@@ -143,7 +145,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="three_layer", choices=["three_layer", "paper_irregular"])
+    ap.add_argument("--workload", default="three_layer", choices=["three_layer", "paper_irregular", "batch"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--p", type=int, default=P_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -481,6 +483,50 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_batch(args, rank, world, local_rank):
+    """The batching form (one lpbfmm_eval_batched call per step over 256 systems, p = 8, mixed):
+    targets of all systems per second.  Context measurement beside the headline workload."""
+    import torch
+    from paper_2002_01334_gb300 import build as B
+    B.build()
+    from paper_2002_01334_gb300 import inputs
+    from paper_2002_01334_gb300 import lpbfmm as F
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    systems = inputs.batch(nsys=256, nmin=1000, nmax=64000, seed=inputs.BASE_SEED + 3 + 1000 * rank)
+    stream = torch.cuda.current_stream(dev)
+    ctxs, offs = [], [0]
+    for s in systems:
+        m = s["medium"]
+        ctxs.append(F.Context(m["d"], m["eps"], m["lam"], 8, precision=F.MIXED, stream=stream))
+        offs.append(offs[-1] + len(s["q"]))
+    n = offs[-1]
+    q = torch.tensor(np.concatenate([s["q"] for s in systems]), device=dev)
+    x = torch.tensor(np.concatenate([s["xyz"] for s in systems]), device=dev)
+    l = torch.tensor(np.concatenate([s["layer"] for s in systems]), dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        F.eval_batched(ctxs, offs, q, x, l)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            F.eval_batched(ctxs, offs, q, x, l)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    value = n * args.steps / (ms / 1e3)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC_BATCH, "value": value, "unit": "targets/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                          "data": "synthetic",
+                          "config": {"workload": "256 systems, N log-uniform in [1000, 64000] (total %d), p = 8, "
+                                                 "random 2-4 layer media" % n, "systems": 256, "n": n, "p": 8,
+                                     "precision": "mixed", "separation": "two-box interaction lists"},
+                          "clocks": clk.summary()}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -488,6 +534,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        run_batch(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -66,21 +66,29 @@ typedef struct lpbfmm_ctx *lpbfmm_t;
  * 2 = two-box: one box lies between a box and the nearest box of its far list, so every
  * expansion converges at a faster geometric rate at the same p (more M2L and near-field work). */
 #define LPBFMM_SEPARATION_DEFAULT 2
+#define LPBFMM_REACT_LEVELS_DEFAULT 4
 
 typedef struct {
   int precision;     /* LPBFMM_FP64 or LPBFMM_MIXED                                        */
   int max_per_leaf;  /* automatic depth: the free-space part uses the smallest depth >= 2 whose
                         mean target occupancy of the non-empty leaves is <= max_per_leaf
-                        (default 128); a group's reaction part goes up to two levels deeper,
-                        until no target box and image box are near (Sec. 3.5, Remark 1)     */
+                        (default 128); a group's reaction part goes up to react_levels
+                        levels deeper, until no target box and image box are near (Sec. 3.5,
+                        Remark 1)                                                            */
   int uniform_depth; /* > 0: use this tree depth for every target group and both parts;
                         0: automatic                                                         */
   int separation;    /* 1 or 2 boxes; 0 = LPBFMM_SEPARATION_DEFAULT                        */
+  int react_levels;  /* automatic depth: how many levels below the free-space depth the
+                        reaction part's tree may go to separate every target box from every
+                        image box (0 .. 8; lpbfmm_default_opts sets
+                        LPBFMM_REACT_LEVELS_DEFAULT).  Image pairs still near at that depth
+                        are summed by direct Sommerfeld quadrature, whose cost grows with the
+                        pairs and with the nodes that small target-image distances need      */
   void *stream;      /* cudaStream_t for all work; NULL = the legacy default stream          */
 } lpbfmm_opts;
 
 /* Fill *opts with the defaults (FP64, max_per_leaf 128, automatic depth, default separation,
- * default stream). */
+ * react_levels LPBFMM_REACT_LEVELS_DEFAULT, default stream). */
 void lpbfmm_default_opts(lpbfmm_opts *opts);
 
 /*
@@ -154,7 +162,12 @@ int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, co
 /*
  * Batched evaluation of nsys independent systems, each with its own context (medium and
  * order): system s uses rows offsets[s] .. offsets[s+1]-1 of the concatenated device arrays.
- * offsets is a host array of nsys+1 non-decreasing entries with offsets[0] = 0.
+ * offsets is a host array of nsys+1 non-decreasing entries with offsets[0] = 0.  All contexts live
+ * on the current device.  The systems run concurrently, each distinct context on one of eight
+ * library-owned streams driven by host threads (a context that serves several systems runs them
+ * in turn), heaviest first; the call returns when every system's host-side work is done, and the
+ * stream of ctxs[0] (and every context's own stream) is ordered after all of it.  Not
+ * stream-capturable.  The first error code any system returns is returned.
  */
 int lpbfmm_eval_batched(int nsys, const lpbfmm_t *ctxs, const int64_t *offsets, const double *q,
                         const double *xyz, const int32_t *layer_id, double *phi, double *field);

@@ -1,10 +1,13 @@
 // C-ABI entry points and host orchestration (Algorithm 2 of the paper: the free-space FMM of
 // every layer plus Algorithm 1 for every reaction component, summed per target).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 
 #include "internal.h"
 
@@ -299,7 +302,7 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     }
   };
   // depth: Df of the free-space part by the occupancy rule (or given); the reaction part goes up to
-  // two levels deeper, to the first level whose boxes are small enough that no target box and
+  // react_levels levels deeper, to the first level whose boxes are small enough that no target box and
   // image box are near (k_t + k_s >= ws for the closest rows): its near field, the costly direct
   // Sommerfeld integrals, then vanishes (Sec. 3.5, Remark 1)
   const int G = (int)c.groups.size();
@@ -322,7 +325,7 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
       if (g.parts & 2) {
         double zt, zs;
         z_gaps(g, zt, zs);
-        while (g.D < std::min(DMAX, g.Df + 2)) {
+        while (g.D < std::min(DMAX, g.Df + c.opts.react_levels)) {
           const double h = g.h(g.D);
           if (std::floor(zt / h) + std::floor(zs / h) >= c.ws) break;
           ++g.D;
@@ -383,6 +386,18 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
   prof_mark(c, "end");
 }
 
+// streams on which lpbfmm_eval_batched runs systems concurrently, per device (created on first use,
+// kept for the process)
+constexpr int BATCH_STREAMS = 8;
+static std::mutex g_bs_mu;
+static cudaStream_t g_bs[LPB_MAX_DEVICES][BATCH_STREAMS] = {};
+static cudaStream_t *batch_streams(int dev) {
+  std::lock_guard<std::mutex> lk(g_bs_mu);
+  if (!g_bs[dev][0])
+    for (int t = 0; t < BATCH_STREAMS; ++t) LPB_CUDA(cudaStreamCreateWithFlags(&g_bs[dev][t], cudaStreamNonBlocking));
+  return g_bs[dev];
+}
+
 }  // namespace lpb
 
 using namespace lpb;
@@ -403,6 +418,7 @@ void lpbfmm_default_opts(lpbfmm_opts *o) {
   o->max_per_leaf = 128;
   o->uniform_depth = 0;
   o->separation = 0;
+  o->react_levels = LPBFMM_REACT_LEVELS_DEFAULT;
   o->stream = nullptr;
 }
 
@@ -424,7 +440,8 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
   lpbfmm_default_opts(&o);
   if (opts) o = *opts;
   if ((o.precision != LPBFMM_FP64 && o.precision != LPBFMM_MIXED) || o.max_per_leaf < 0 || o.uniform_depth < 0 ||
-      o.uniform_depth > DMAX || o.separation < 0 || o.separation > WS_MAX)
+      o.uniform_depth > DMAX || o.separation < 0 || o.separation > WS_MAX ||
+      o.react_levels < 0 || o.react_levels > 8)
     return LPBFMM_ERR_ARG;
   lpbfmm_ctx *c = new (std::nothrow) lpbfmm_ctx();
   if (!c) return LPBFMM_ERR_OOM;
@@ -539,15 +556,91 @@ int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, co
 int lpbfmm_eval_batched(int nsys, const lpbfmm_t *ctxs, const int64_t *offsets, const double *q, const double *xyz,
                         const int32_t *layer_id, double *phi, double *field) {
   if (nsys < 0 || (nsys > 0 && (!ctxs || !offsets))) return LPBFMM_ERR_ARG;
-  if (nsys > 0 && offsets[0] != 0) return LPBFMM_ERR_ARG;
+  if (nsys == 0) return LPBFMM_OK;
+  if (offsets[0] != 0) return LPBFMM_ERR_ARG;
   for (int s = 0; s < nsys; ++s)
-    if (!ctxs[s] || offsets[s + 1] < offsets[s]) return LPBFMM_ERR_ARG;
-  for (int s = 0; s < nsys; ++s) {
-    const int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
-    const int rc = lpbfmm_eval(ctxs[s], n, q + o, xyz + 3 * o, layer_id + o, phi + o, field ? field + 3 * o : nullptr);
-    if (rc) return rc;
+    if (!ctxs[s] || offsets[s + 1] < offsets[s] || ctxs[s]->device != ctxs[0]->device) return LPBFMM_ERR_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != ctxs[0]->device) return LPBFMM_ERR_ARG;
+  // units of work: the distinct contexts, each with its systems (a context serves one system at a
+  // time), heaviest first
+  std::vector<lpbfmm_t> uctx;
+  std::vector<std::vector<int>> usys;
+  std::vector<int64_t> ucost;
+  {
+    std::map<lpbfmm_t, int> idx;
+    for (int s = 0; s < nsys; ++s) {
+      auto it = idx.find(ctxs[s]);
+      if (it == idx.end()) {
+        it = idx.emplace(ctxs[s], (int)uctx.size()).first;
+        uctx.push_back(ctxs[s]);
+        usys.emplace_back();
+        ucost.push_back(0);
+      }
+      usys[it->second].push_back(s);
+      ucost[it->second] += offsets[s + 1] - offsets[s];
+    }
   }
-  return LPBFMM_OK;
+  std::vector<int> order(uctx.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ucost[x] > ucost[y]; });
+  const int dev = ctxs[0]->device;
+  const int nthr = (int)std::min<size_t>(BATCH_STREAMS, uctx.size());
+  cudaStream_t caller = ctxs[0]->stream;
+  cudaStream_t *pool = nullptr;
+  std::vector<cudaEvent_t> evs(nthr + 1, nullptr);
+  try {
+    pool = batch_streams(dev);
+    for (auto &e : evs) LPB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // the inputs are written on the caller's stream; a context's earlier work must be complete
+    // before its work space is reused on a pool stream
+    LPB_CUDA(cudaEventRecord(evs[nthr], caller));
+    for (auto ctx : uctx) LPB_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int t = 0; t < nthr; ++t) LPB_CUDA(cudaStreamWaitEvent(pool[t], evs[nthr], 0));
+  } catch (const CudaError &e) {
+    for (auto &ev : evs)
+      if (ev) cudaEventDestroy(ev);
+    return map_error(e);
+  }
+  std::atomic<int> next{0}, err{0};
+  auto work = [&](int t) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      int z = 0;
+      err.compare_exchange_strong(z, LPBFMM_ERR_CUDA);
+      return;
+    }
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= (int)order.size() || err.load()) break;
+      lpbfmm_t ctx = uctx[order[k]];
+      const cudaStream_t own = ctx->stream;
+      ctx->stream = pool[t];
+      for (int s : usys[order[k]]) {
+        const int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
+        const int rc = lpbfmm_eval(ctx, n, q + o, xyz + 3 * o, layer_id + o, phi + o, field ? field + 3 * o : nullptr);
+        if (rc) {
+          int z = 0;
+          err.compare_exchange_strong(z, rc);
+          break;
+        }
+      }
+      ctx->stream = own;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthr; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto &x : th) x.join();
+  // the caller's stream and every context's own stream continue after the pool's work
+  int rc = err.load();
+  for (int t = 0; t < nthr; ++t) {
+    if (cudaEventRecord(evs[t], pool[t]) != cudaSuccess || cudaStreamWaitEvent(caller, evs[t], 0) != cudaSuccess)
+      rc = rc ? rc : LPBFMM_ERR_CUDA;
+    for (auto ctx : uctx)
+      if (ctx->stream != caller && cudaStreamWaitEvent(ctx->stream, evs[t], 0) != cudaSuccess) rc = rc ? rc : LPBFMM_ERR_CUDA;
+  }
+  for (auto &ev : evs) cudaEventDestroy(ev);
+  return rc;
 }
 
 int lpbfmm_status(lpbfmm_t h) {

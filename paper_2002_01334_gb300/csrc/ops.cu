@@ -472,25 +472,39 @@ __device__ __forceinline__ void df_fma(float2 a, float2 b, float2 &acc) {
   acc = make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
 }
 
+// ASM_CC classes per CTA share each entry's decode and coefficient loads
+constexpr int ASM_CC = 4;
 template <typename T>
 __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const double *sfac, T *out) {
   const RDesc D = descs[blockIdx.y];
-  const int cls = blockIdx.x;
-  if (D.used && !D.used[cls]) return;
+  const int cls0 = blockIdx.x * ASM_CC;
   extern __shared__ double asm_sm[];
-  float2 *Sf = (float2 *)asm_sm;  // [(KT+1)^2 * 4]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}, double-float
+  const int TS = (KT + 1) * (KT + 1) * 4;
+  float2 *Sf = (float2 *)asm_sm;  // [ASM_CC][TS]: sqrt((K+d)!(K-d)!) S^K S_{K d, ij}, double-float
   __shared__ double smm[PMAX + 1], rdf[PMAX + 1];
   __shared__ double fa[KHALF_MAX], fb[KHALF_MAX];  // prefactor A(o, i) = fa[o] fb[i]
   __shared__ float faf[KHALF_MAX], fbf[KHALF_MAX];  // the same in FP32 (FP32 operators, p <= 12)
-  const double *S = D.stab + ((size_t)(cls - D.cls0) * D.ntypes + D.tau) * (size_t)((KT + 1) * (KT + 1) * 4);
-  for (int e = threadIdx.x; e < (KT + 1) * (KT + 1) * 4; e += blockDim.x) {
-    const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
-    Sf[e] = df_split((d <= Kk) ? sfac[Kk * (KMAX_TAB + 1) + d] * S[e] : 0.0);
+  bool cuse[ASM_CC];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < ASM_CC; ++k) {
+    const int cls = cls0 + k;
+    cuse[k] = cls < NREACT_CLS && (!D.used || D.used[cls]);
+    any |= cuse[k];
+  }
+  if (!any) return;
+  for (int k = 0; k < ASM_CC; ++k) {
+    if (!cuse[k]) continue;
+    const double *S = D.stab + ((size_t)(cls0 + k - D.cls0) * D.ntypes + D.tau) * (size_t)TS;
+    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
+      const int Kk = e / ((KT + 1) * 4), d = (e / 4) % (KT + 1);
+      Sf[k * TS + e] = df_split((d <= Kk) ? sfac[Kk * (KMAX_TAB + 1) + d] * S[e] : 0.0);
+    }
   }
   if (threadIdx.x == 0) {
-    double s = 1.0;
+    double sg = 1.0;
     smm[0] = 1.0;
-    for (int m = 1; m <= p; ++m) { s *= -sqrt((2.0 * m + 1.0) / (2.0 * m)); smm[m] = s; }
+    for (int m = 1; m <= p; ++m) { sg *= -sqrt((2.0 * m + 1.0) / (2.0 * m)); smm[m] = sg; }
     rdf[0] = 1.0;
     for (int n = 1; n <= p; ++n) rdf[n] = rdf[n - 1] / (2.0 * n + 1.0);  // 1/(2n+1)!!
   }
@@ -510,7 +524,6 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
   const bool f32_out = sizeof(T) == 4 && p <= 12;
   const int NS = p + 2;
   const size_t KK = (size_t)K * K;
-  T *P = out + D.dst + (size_t)cls * D.ntypes * 2 * KK;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int o = e / K, i = e % K;
     int n, m, nu, mu;
@@ -521,37 +534,48 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     const float2 *cf = D.coef + (size_t)e * NS;
     const int dp = mu - m, dm = mu + m;  // |d| for +mu and -mu
     const int adp = dp < 0 ? -dp : dp;
-    float2 ap = make_float2(0.f, 0.f), am = make_float2(0.f, 0.f);
+    float2 ap[ASM_CC], am[ASM_CC];
+#pragma unroll
+    for (int k = 0; k < ASM_CC; ++k) ap[k] = am[k] = make_float2(0.f, 0.f);
     for (int s = 0; s <= smax; ++s) {
       const int Kk = 1 + m + mu + 2 * s;
       if (Kk > KT) break;
       const float2 c = cf[s];
-      df_fma(c, Sf[((Kk * (KT + 1)) + adp) * 4 + ij], ap);
-      df_fma(c, Sf[((Kk * (KT + 1)) + dm) * 4 + ij], am);
+      const int ip = ((Kk * (KT + 1)) + adp) * 4 + ij, im = ((Kk * (KT + 1)) + dm) * 4 + ij;
+#pragma unroll
+      for (int k = 0; k < ASM_CC; ++k) {
+        df_fma(c, Sf[k * TS + ip], ap[k]);
+        df_fma(c, Sf[k * TS + im], am[k]);
+      }
     }
-
     // signs: (-1)^|d| for d = mu - m < 0 and for d = -mu - m < 0; (-1)^mu of the -mu term
     const bool fp = dp < 0 && (adp & 1), fm = ((dm > 0 && (dm & 1)) != ((mu & 1) != 0));
-    const float2 Xd = fp ? make_float2(-ap.x, -ap.y) : ap, Yd = fm ? make_float2(-am.x, -am.y) : am;
-    T *dP = P + (size_t)D.tau * 2 * KK + (size_t)o * K + i, *dQ = dP + KK;
-    if (f32_out) {
-      const float Af = faf[o] * fbf[i];
-      if (mu == 0) {
-        *dP = (T)(Af * df_sum_f(Xd, make_float2(0.f, 0.f)));
-        *dQ = (T)0;
+#pragma unroll
+    for (int k = 0; k < ASM_CC; ++k) {
+      if (!cuse[k]) continue;
+      const float2 Xd = fp ? make_float2(-ap[k].x, -ap[k].y) : ap[k];
+      const float2 Yd = fm ? make_float2(-am[k].x, -am[k].y) : am[k];
+      T *dP = out + D.dst + (size_t)(cls0 + k) * D.ntypes * 2 * KK + (size_t)D.tau * 2 * KK + (size_t)o * K + i;
+      T *dQ = dP + KK;
+      if (f32_out) {
+        const float Af = faf[o] * fbf[i];
+        if (mu == 0) {
+          *dP = (T)(Af * df_sum_f(Xd, make_float2(0.f, 0.f)));
+          *dQ = (T)0;
+        } else {
+          *dP = (T)(Af * df_sum_f(Xd, Yd));
+          *dQ = (T)(Af * df_sum_f(Xd, make_float2(-Yd.x, -Yd.y)));
+        }
       } else {
-        *dP = (T)(Af * df_sum_f(Xd, Yd));
-        *dQ = (T)(Af * df_sum_f(Xd, make_float2(-Yd.x, -Yd.y)));
+        const double A = fa[o] * fb[i];
+        const double X = (double)Xd.x + (double)Xd.y, Y = (double)Yd.x + (double)Yd.y;
+        *dP = (T)(mu == 0 ? A * X : A * (X + Y));
+        *dQ = (T)(mu == 0 ? 0.0 : A * (X - Y));
       }
-    } else {
-      const double A = fa[o] * fb[i];
-      const double X = (double)Xd.x + (double)Xd.y, Y = (double)Yd.x + (double)Yd.y;
-      *dP = (T)(mu == 0 ? A * X : A * (X + Y));
-      *dQ = (T)(mu == 0 ? 0.0 : A * (X - Y));
     }
   }
 }
-static size_t assemble_smem(int KT) { return sizeof(double) * (size_t)(KT + 1) * (KT + 1) * 4; }
+static size_t assemble_smem(int KT) { return ASM_CC * sizeof(double) * (size_t)(KT + 1) * (KT + 1) * 4; }
 
 // near-field reaction quadrature nodes: W = w lr sigma / (4 pi lz_l), lz_l, lz_l'
 __global__ void k_near_nodes(Medium md, int l, int a, int ntypes, double umax, double wmax, double lmin,
@@ -740,7 +764,8 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
       size_t last = first;
       while (last < rd.size() && rd[last].pad == l) ++last;
       LPB_ATTR_ONCE(k_react_assemble<T>, assemble_smem(KMAX_TAB));
-      k_react_assemble<T><<<dim3(NREACT_CLS, (unsigned)(last - first)), 256, assemble_smem(KT), c.stream>>>(
+      k_react_assemble<T><<<dim3((NREACT_CLS + ASM_CC - 1) / ASM_CC, (unsigned)(last - first)), 256,
+                            assemble_smem(KT), c.stream>>>(
           dr + first, p, K, KT, c.sfac, (T *)g.op_react[l]);
       LPB_LAUNCH();
       c.launches++;

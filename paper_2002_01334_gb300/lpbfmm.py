@@ -30,7 +30,7 @@ class LpbfmmError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_per_leaf", C.c_int), ("uniform_depth", C.c_int),
-                ("separation", C.c_int), ("stream", C.c_void_p)]
+                ("separation", C.c_int), ("react_levels", C.c_int), ("stream", C.c_void_p)]
 
 
 def lib():
@@ -92,7 +92,7 @@ class Context:
     separation = 1 (one-box) or 2 (two-box) interaction lists, 0 = the library default (2)."""
 
     def __init__(self, d, eps, lam, p, tol=1e-14, precision=FP64, max_per_leaf=128, uniform_depth=0,
-                 stream=None, separation=0):
+                 stream=None, separation=0, react_levels=None):
         L = lib()
         o = Opts()
         L.lpbfmm_default_opts(C.byref(o))
@@ -100,6 +100,8 @@ class Context:
         o.max_per_leaf = int(max_per_leaf)
         o.uniform_depth = int(uniform_depth or 0)
         o.separation = int(separation or 0)
+        if react_levels is not None:
+            o.react_levels = int(react_levels)
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()
         o.stream = C.c_void_p(stream.cuda_stream if stream is not None else 0)

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_default_opts_and_strerror(L):
     o = F.Opts()
     L.lpbfmm_default_opts(C.byref(o))
-    assert (o.precision, o.max_per_leaf, o.uniform_depth, o.separation) == (0, 128, 0, 0)
+    assert (o.precision, o.max_per_leaf, o.uniform_depth, o.separation, o.react_levels) == (0, 128, 0, 0, 4)
     assert L.lpbfmm_strerror(0) == b"ok"
     assert L.lpbfmm_strerror(4) == b"charge on an interface"
 

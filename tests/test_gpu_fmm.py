@@ -552,6 +552,103 @@ def test_batched_matches_individual():
         assert rel(got, ref[0]) < 2e-5
 
 
+def test_paper_accuracy_experiment_matches_the_cpu_fmm_table():
+    """The paper's accuracy-against-p experiment (Sec. 4, shown there as a figure) on its own
+    workload (912 + 640 + 1296 charges in the irregular bodies, eps = (1, 8.6, 20.5), lambda = (1.2,
+    0.5, 2.1)): the FP64 GPU FMM on uniform depth-4 trees with one-box lists, p = 2..10, has the
+    per-layer Err_2 / Err_max (potential and field, against the oracle's direct sum) that the
+    oracle's CPU FMM of the same trees gives (tests/golden/paper_accuracy_e2.json), to 1e-3 of each
+    value; the errors fall geometrically with p."""
+    import json
+    tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_accuracy_e2.json")))
+    w = inputs.workload("paper_irregular")
+    md = oracle.Medium(**w["medium"])
+    ref_phi, ref_fld = oracle.direct(md, w["q"], w["xyz"], w["layer"])
+    lay = w["layer"]
+
+    def layer_errors(a, ref):
+        out = []
+        for k in range(int(lay.max()) + 1):
+            s = lay == k
+            d, r = np.abs(a[s] - ref[s]), np.abs(ref[s])
+            out.append((float(np.linalg.norm(d) / np.linalg.norm(r)), float(d.max() / r.max())))
+        return out
+    prev = None
+    for row in tab["rows"]:
+        _, phi, fld = run(w, row["p"], depth=tab["depth"], ws=1)
+        for name, a, ref in (("phi", phi, ref_phi), ("field", fld, ref_fld)):
+            got = layer_errors(a, ref)
+            for k, (e2, em) in enumerate(got):
+                want = row[name][k]
+                assert abs(e2 - want["err2"]) <= 1e-3 * want["err2"] + 1e-13, (row["p"], name, k, e2, want)
+                assert abs(em - want["errmax"]) <= 1e-3 * want["errmax"] + 1e-13, (row["p"], name, k, em, want)
+        tot = rel(phi, ref_phi)
+        assert prev is None or tot < prev / 3, (row["p"], tot, prev)
+        prev = tot
+
+
+def test_single_source_example_converges_in_p():
+    """The paper's single-source example (Sec. 3.4, after the M2L operators; geometry in
+    tests/golden/paper_me_example.json): one unit charge in the middle layer and three targets of
+    zero charge.  The FP64 GPU FMM's reaction part at the targets (images through P2M, M2M, M2L,
+    L2L, L2P where they are far; the node-rule integrals where near) converges geometrically in p
+    to the oracle's direct Sommerfeld integrals (field error 5e-3, 1.5e-4, 2.8e-6 at p = 4, 8, 12
+    on the CPU FMM of the same trees), and equals that CPU FMM to rounding."""
+    import json
+    ex = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_me_example.json")))
+    md = oracle.Medium(ex["d"], ex["eps"], ex["lam"])
+    xyz = np.array([ex["source"]] + ex["targets"], float)
+    q = np.array([1.0, 0.0, 0.0, 0.0])
+    layer = np.array([md.layer_of(z) for z in xyz[:, 2]], np.int32)
+    ref = oracle.direct(md, q, xyz, layer, parts=2)
+    w = {"medium": {"d": ex["d"], "eps": ex["eps"], "lam": ex["lam"]}, "q": q, "xyz": xyz, "layer": layer}
+    from oracle import fmm as cfmm
+    errs = []
+    for p in (4, 8, 12, 16):
+        _, phi, fld = run(w, p, parts=2, depth=4, ws=1)
+        errs.append(max(rel(phi[1:], ref[0][1:]), rel(fld[1:], ref[1][1:])))
+        if p == 8:  # the same truncated FMM as the oracle's CPU FMM of these trees
+            cp, cf = cfmm.react_fmm(md, q, xyz, layer, p, 4, 1)
+            assert rel(phi[1:], cp[1:]) < 1e-9 and rel(fld[1:], cf[1:]) < 1e-9
+    assert errs[0] > 10 * errs[1] > 100 * errs[2] > 1000 * errs[3], errs
+    assert errs[3] < 1e-6, errs
+
+
+def test_batching_form_256_systems():
+    """The batching workload: 256 independent systems, N log-uniform in [1000, 64000], each in its
+    own random 2- to 4-layer medium (eps ~ U[1, 10], lambda ~ U[0.2, 2], thicknesses U[0.5, 2]),
+    charges in a unit cube inside one layer, p = 8, mixed precision, evaluated by one
+    lpbfmm_eval_batched call (systems concurrent on the library's streams).  Against the oracle's
+    direct sum at one seeded target per system: relative L2 over the 256 targets <= 1e-6 for the
+    potential and the field; each system equal to its own lpbfmm_eval to rounding."""
+    systems = inputs.batch(nsys=256, nmin=1000, nmax=64000)
+    ctxs, offs = [], [0]
+    for s in systems:
+        m = s["medium"]
+        ctxs.append(F.Context(m["d"], m["eps"], m["lam"], 8, precision=F.MIXED))
+        offs.append(offs[-1] + len(s["q"]))
+    q = torch.tensor(np.concatenate([s["q"] for s in systems]), device=DEV)
+    x = torch.tensor(np.concatenate([s["xyz"] for s in systems]), device=DEV)
+    l = torch.tensor(np.concatenate([s["layer"] for s in systems]), dtype=torch.int32, device=DEV)
+    phi, fld = F.eval_batched(ctxs, offs, q, x, l)
+    torch.cuda.synchronize()
+    assert all(c.status() == 0 for c in ctxs)
+    phi, fld = phi.cpu().numpy(), fld.cpu().numpy()
+    rng = np.random.default_rng(3)
+    got_p, got_f, ref_p, ref_f = [], [], [], []
+    for k, s in enumerate(systems):
+        i = int(rng.integers(len(s["q"])))
+        rp, rf = oracle.direct(oracle.Medium(**s["medium"]), s["q"], s["xyz"], s["layer"], targets=np.array([i]))
+        got_p.append(phi[offs[k] + i]); got_f.append(fld[offs[k] + i])
+        ref_p.append(rp[0]); ref_f.append(rf[0])
+    e = (rel(got_p, ref_p), rel(got_f, ref_f))
+    assert e[0] < 1e-6 and e[1] < 1e-6, e
+    for k in (0, 100, 255):  # the batched call returns what one evaluation of the system returns
+        s = systems[k]
+        _, p1, f1 = run(s, 8, prec=F.MIXED, ctx=ctxs[k])
+        assert rel(phi[offs[k]:offs[k + 1]], p1) < 1e-12 and rel(fld[offs[k]:offs[k + 1]], f1) < 1e-12
+
+
 @pytest.mark.skipif(os.environ.get("LPBFMM_FULL_SIZE", "1") == "0", reason="full-size sample disabled")
 def test_full_size_three_layer_sampled_targets():
     """N = 1,000,000 in three layers, p = 10, automatic depth, default separation: the launch
