@@ -150,8 +150,8 @@ def parse():
     ap.add_argument("--p", type=int, default=P_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick the leaf-size target by timing candidates on the workload first")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the search of leaf size and reaction depth (use the library defaults)")
     return ap.parse_args()
 
 
@@ -282,6 +282,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2002_01334_gb300 import build as B
     B.build()
+    from paper_2002_01334_gb300 import autotune
     from paper_2002_01334_gb300 import inputs
     from paper_2002_01334_gb300 import lpbfmm as F
 
@@ -297,15 +298,16 @@ def run_ours(args, rank, world, local_rank):
     x = torch.tensor(w["xyz"], device=dev)
     l = torch.tensor(w["layer"], dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    leaf, tuned = 128, None
-    if args.autotune:
-        from paper_2002_01334_gb300 import autotune
+    settings, tuned = dict(autotune.DEFAULTS), None
+    if not args.no_autotune:
         measure, close = autotune.cuda_measure(m, args.p, F.MIXED, q, x, l, stream=stream)
-        leaf, table = autotune.choose(autotune.CANDIDATES, measure, repeats=2)
+        settings, rows = autotune.search(autotune.SPACE, measure, start=autotune.DEFAULTS, repeats=2)
         close()
-        tuned = {"parameter": "max_per_leaf", "ms_by_candidate": {str(k): v for k, v in table.items()},
-                 "chosen": leaf}
-    ctx = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.MIXED, max_per_leaf=leaf, stream=stream)
+        tuned = {"method": "coordinate descent over %s in order; median of 2 CUDA-event timings of one evaluation "
+                           "per setting" % ", ".join(nm for nm, _ in autotune.SPACE),
+                 "ms_by_setting": rows, "chosen": settings}
+    leaf = settings["max_per_leaf"]
+    ctx = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.MIXED, stream=stream, **settings)
     n = args.n
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     fld = torch.empty((n, 3), dtype=torch.float64, device=dev)
@@ -364,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
     # accuracy gate and the FP64 comparator (same tree rule, same inputs), untimed by the driver's clock
     accuracy, fp64_value = None, None
     if not args.no_fp64:
-        ctx64 = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.FP64, stream=stream)
+        ctx64 = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.FP64, stream=stream, **settings)
         p64 = torch.empty_like(phi)
         f64 = torch.empty_like(fld)
         ctx64.eval(q, x, l, out=(p64, f64))
@@ -433,7 +435,7 @@ def run_ours(args, rank, world, local_rank):
 
     roofs = []
     if "p2p" in phase_ms:
-        roofs.append(roof("k_p2p_free_f32 (free-space near field; interval includes k_split_points)", "alu",
+        roofs.append(roof("k_p2p_free_f32 (free-space near field of every group, one launch)", "alu",
                           24.0 * counts["p2p_pairs"], per("p2p"), fp32_peak, "24 per pair (+2 SFU)"))
     if "m2l_tc" in phase_ms:
         tr = counts["m2l_free"] + counts["m2l_react"]
@@ -468,7 +470,8 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": dict(workload_config(n, args.p, "mixed", args.workload),
-                               **({"tree": "automatic depth, <=%d mean targets per leaf (autotuned)" % leaf}
+                               **({"tree": "automatic depth, <=%d mean targets per leaf, reaction trees up to %d "
+                                           "levels deeper (autotuned)" % (leaf, settings["react_levels"])}
                                   if tuned else {})),
                 "clocks": clk.summary(), "autotune": tuned,
                 "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
@@ -489,21 +492,31 @@ def run_batch(args, rank, world, local_rank):
     import torch
     from paper_2002_01334_gb300 import build as B
     B.build()
+    from paper_2002_01334_gb300 import autotune
     from paper_2002_01334_gb300 import inputs
     from paper_2002_01334_gb300 import lpbfmm as F
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     systems = inputs.batch(nsys=256, nmin=1000, nmax=64000, seed=inputs.BASE_SEED + 3 + 1000 * rank)
     stream = torch.cuda.current_stream(dev)
-    ctxs, offs = [], [0]
+    offs = [0]
     for s in systems:
-        m = s["medium"]
-        ctxs.append(F.Context(m["d"], m["eps"], m["lam"], 8, precision=F.MIXED, stream=stream))
         offs.append(offs[-1] + len(s["q"]))
     n = offs[-1]
     q = torch.tensor(np.concatenate([s["q"] for s in systems]), device=dev)
     x = torch.tensor(np.concatenate([s["xyz"] for s in systems]), device=dev)
     l = torch.tensor(np.concatenate([s["layer"] for s in systems]), dtype=torch.int32, device=dev)
+    settings, tuned = dict(autotune.DEFAULTS), None
+    if not args.no_autotune:
+        measure, close = autotune.batch_measure(systems, 8, F.MIXED, offs, q, x, l, stream=stream)
+        settings, rows = autotune.search(autotune.SPACE, measure, start=autotune.DEFAULTS, repeats=2)
+        close()
+        tuned = {"method": "coordinate descent over %s in order (one setting for every system); median of 2 "
+                           "CUDA-event timings of one batched evaluation per setting"
+                           % ", ".join(nm for nm, _ in autotune.SPACE),
+                 "ms_by_setting": rows, "chosen": settings}
+    ctxs = [F.Context(s["medium"]["d"], s["medium"]["eps"], s["medium"]["lam"], 8, precision=F.MIXED, stream=stream,
+                      **settings) for s in systems]
     for _ in range(args.warmup):
         F.eval_batched(ctxs, offs, q, x, l)
     torch.cuda.synchronize(dev)
@@ -516,6 +529,7 @@ def run_batch(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
     value = n * args.steps / (ms / 1e3)
+    launches = sum(c.counts()["launches"] for c in ctxs)  # per step: every context's kernels + grouped ones
     if rank == 0:
         print(json.dumps({"metric": METRIC_BATCH, "value": value, "unit": "targets/s", "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -523,8 +537,14 @@ def run_batch(args, rank, world, local_rank):
                           "data": "synthetic",
                           "config": {"workload": "256 systems, N log-uniform in [1000, 64000] (total %d), p = 8, "
                                                  "random 2-4 layer media" % n, "systems": 256, "n": n, "p": 8,
-                                     "precision": "mixed", "separation": "two-box interaction lists"},
-                          "clocks": clk.summary()}), flush=True)
+                                     "precision": "mixed", "separation": "two-box interaction lists",
+                                     "tree": "automatic depth, <=%d mean targets per leaf, reaction trees up to %d "
+                                             "levels deeper%s" % (settings["max_per_leaf"], settings["react_levels"],
+                                                                  " (autotuned)" if tuned else ""),
+                                     "l2": "not flushed: the inputs (%d MB) and each step's work space exceed the "
+                                           "129 MB L2" % (n * 36 // 10**6)},
+                          "gpu_launches": launches * args.steps, "autotune": tuned, "clocks": clk.summary()}),
+              flush=True)
 
 
 def main():

@@ -163,9 +163,16 @@ int lpbfmm_adjoint(lpbfmm_t h, int64_t n, const double *q, const double *xyz, co
  * Batched evaluation of nsys independent systems, each with its own context (medium and
  * order): system s uses rows offsets[s] .. offsets[s+1]-1 of the concatenated device arrays.
  * offsets is a host array of nsys+1 non-decreasing entries with offsets[0] = 0.  All contexts live
- * on the current device.  The systems run concurrently, each distinct context on one of eight
- * library-owned streams driven by host threads (a context that serves several systems runs them
- * in turn), heaviest first; the call returns when every system's host-side work is done, and the
+ * on the current device.  The per-system parts (validation, trees, lists, tables, operators,
+ * upward and downward passes) run concurrently, each distinct context on one of eight
+ * library-owned streams driven by host threads, heaviest first.  For the contexts that serve one
+ * system each, the two heaviest passes run grouped over all of them, on the stream of ctxs[0]:
+ * one tensor-core M2L launch (and one launch of its slot sums) per truncation order, whose work
+ * items span (system, target group, level, row class, far-list slice), and one launch of the FP32
+ * free-space near field, whose blocks span (system, group, leaf).  A context that serves several
+ * systems evaluates them in turn, whole.  Results equal lpbfmm_eval's bit for bit.  A timed-out
+ * wait in a grouped launch is reported on the status word of the first such context (in batch
+ * order, heaviest first).  The call returns when every system's host-side work is done, and the
  * stream of ctxs[0] (and every context's own stream) is ordered after all of it.  Not
  * stream-capturable.  The first error code any system returns is returned.
  */

@@ -212,8 +212,11 @@ static double unord(unsigned long long u) {
 // ---------------------------------------------------------------------------------------
 // parts: bits 0, 1 free-space / reaction part, bits 2, 3 diagnostics (lpbfmm_eval_parts); gmask (host,
 // may be null): per target group (l, a) at index 2 l + a - 1, the parts it computes (bits 0, 1)
-static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, const int32_t *layer, int parts,
-                      const int32_t *gmask, double *phi, double *field) {
+// validation, trees, lists, tables, operators, upward pass and M2L of one evaluation (eval_back
+// finishes it); with c.def.on the tensor-core M2L is only recorded
+static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, const int32_t *layer, int parts,
+                       const int32_t *gmask, double *phi, double *field) {
+  c.def.clear();
   c.arena.reset();
   c.launches = 0;
   c.nev = 0;
@@ -382,13 +385,25 @@ static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, con
     }
   }
   prof_mark(c, "tables+ops");
-  run_fmm_all(c, c.groups, phi, field);
+  run_fmm_front(c, c.groups);
+}
+// the downward pass and near fields of the evaluation eval_front began
+static void eval_back(Ctx &c, double *phi, double *field) {
+  run_fmm_back(c, c.groups, phi, field);
   prof_mark(c, "end");
+}
+static void eval_impl(Ctx &c, int64_t n, const double *q, const double *xyz, const int32_t *layer, int parts,
+                      const int32_t *gmask, double *phi, double *field) {
+  eval_front(c, n, q, xyz, layer, parts, gmask, phi, field);
+  eval_back(c, phi, field);
 }
 
 // streams on which lpbfmm_eval_batched runs systems concurrently, per device (created on first use,
 // kept for the process)
-constexpr int BATCH_STREAMS = 8;
+#ifndef LPB_BATCH_STREAMS
+#define LPB_BATCH_STREAMS 8
+#endif
+constexpr int BATCH_STREAMS = LPB_BATCH_STREAMS;
 static std::mutex g_bs_mu;
 static cudaStream_t g_bs[LPB_MAX_DEVICES][BATCH_STREAMS] = {};
 static cudaStream_t *batch_streams(int dev) {
@@ -602,43 +617,130 @@ int lpbfmm_eval_batched(int nsys, const lpbfmm_t *ctxs, const int64_t *offsets, 
       if (ev) cudaEventDestroy(ev);
     return map_error(e);
   }
-  std::atomic<int> next{0}, err{0};
-  auto work = [&](int t) {
-    if (cudaSetDevice(dev) != cudaSuccess) {
-      int z = 0;
-      err.compare_exchange_strong(z, LPBFMM_ERR_CUDA);
-      return;
+  // a context that serves one system records its tensor-core M2L and FP32 near field for grouped
+  // launches over all such systems; a context that serves several evaluates them in turn, whole
+  std::atomic<int> err{0};
+  auto fail = [&](int rc) {
+    int z = 0;
+    err.compare_exchange_strong(z, rc);
+  };
+  auto guarded = [&](auto &&f) {
+    try {
+      f();
+      return (int)LPBFMM_OK;
+    } catch (const CudaError &e) {
+      return map_error(e);
+    } catch (const StatusError &e) {
+      return e.code;
     }
-    for (;;) {
-      const int k = next.fetch_add(1);
-      if (k >= (int)order.size() || err.load()) break;
-      lpbfmm_t ctx = uctx[order[k]];
-      const cudaStream_t own = ctx->stream;
-      ctx->stream = pool[t];
-      for (int s : usys[order[k]]) {
+  };
+  std::vector<char> deferred(uctx.size(), 0);
+  auto run_threads = [&](auto &&body) {
+    std::atomic<int> next{0};
+    auto work = [&](int t) {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        fail(LPBFMM_ERR_CUDA);
+        return;
+      }
+      for (;;) {
+        const int k = next.fetch_add(1);
+        if (k >= (int)order.size() || err.load()) break;
+        body(order[k], pool[t]);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nthr; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto &x : th) x.join();
+  };
+  // every pool stream after the caller's stream (fork), the caller's stream after every pool
+  // stream (join)
+  auto fork = [&]() {
+    if (cudaEventRecord(evs[nthr], caller) != cudaSuccess) return false;
+    for (int t = 0; t < nthr; ++t)
+      if (cudaStreamWaitEvent(pool[t], evs[nthr], 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&]() {
+    for (int t = 0; t < nthr; ++t)
+      if (cudaEventRecord(evs[t], pool[t]) != cudaSuccess || cudaStreamWaitEvent(caller, evs[t], 0) != cudaSuccess)
+        return false;
+    return true;
+  };
+  // 1: each context's front part (trees, tables, operators, upward pass, M2L preparation)
+  run_threads([&](int u, cudaStream_t st) {
+    lpbfmm_t ctx = uctx[u];
+    const cudaStream_t own = ctx->stream;
+    ctx->stream = st;
+    if (usys[u].size() == 1) {
+      const int s = usys[u][0];
+      const int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
+      ctx->def.on = true;
+      const int rc = guarded([&] {
+        eval_front(*ctx, n, q + o, xyz + 3 * o, layer_id + o, 3, nullptr, phi + o, field ? field + 3 * o : nullptr);
+      });
+      if (rc) {
+        ctx->def.on = false;
+        ctx->def.clear();
+        fail(rc);
+      } else {
+        deferred[u] = 1;
+      }
+    } else {
+      for (int s : usys[u]) {
         const int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
         const int rc = lpbfmm_eval(ctx, n, q + o, xyz + 3 * o, layer_id + o, phi + o, field ? field + 3 * o : nullptr);
         if (rc) {
-          int z = 0;
-          err.compare_exchange_strong(z, rc);
+          fail(rc);
           break;
         }
       }
-      ctx->stream = own;
     }
-  };
-  std::vector<std::thread> th;
-  for (int t = 1; t < nthr; ++t) th.emplace_back(work, t);
-  work(0);
-  for (auto &x : th) x.join();
+    ctx->stream = own;
+  });
+  std::vector<Ctx *> dcs;
+  for (int u : order)
+    if (deferred[u]) dcs.push_back(uctx[u]);
+  // 2: the tensor-core M2L and its slot sums of every deferred context, grouped
+  if (!err.load() && !dcs.empty()) {
+    const int rc = guarded([&] {
+      if (!join()) throw CudaError{cudaErrorUnknown, "batched join"};
+      launch_deferred(dcs, 0, caller);
+      if (!fork()) throw CudaError{cudaErrorUnknown, "batched fork"};
+    });
+    if (rc) fail(rc);
+  }
+  // 3: each deferred context's downward pass and reaction near field
+  if (!err.load() && !dcs.empty())
+    run_threads([&](int u, cudaStream_t st) {
+      if (!deferred[u]) return;
+      lpbfmm_t ctx = uctx[u];
+      const int s = usys[u][0];
+      const int64_t o = offsets[s];
+      const cudaStream_t own = ctx->stream;
+      ctx->stream = st;
+      const int rc = guarded([&] { eval_back(*ctx, phi + o, field ? field + 3 * o : nullptr); });
+      if (rc) fail(rc);
+      ctx->stream = own;
+    });
+  // 4: the FP32 free-space near field of every deferred context, grouped
+  if (!err.load() && !dcs.empty()) {
+    const int rc = guarded([&] {
+      if (!join()) throw CudaError{cudaErrorUnknown, "batched join"};
+      launch_deferred(dcs, 1, caller);
+    });
+    if (rc) fail(rc);
+  }
+  for (Ctx *c : dcs) {
+    c->def.on = false;
+    c->def.clear();
+  }
   // the caller's stream and every context's own stream continue after the pool's work
   int rc = err.load();
-  for (int t = 0; t < nthr; ++t) {
-    if (cudaEventRecord(evs[t], pool[t]) != cudaSuccess || cudaStreamWaitEvent(caller, evs[t], 0) != cudaSuccess)
-      rc = rc ? rc : LPBFMM_ERR_CUDA;
-    for (auto ctx : uctx)
-      if (ctx->stream != caller && cudaStreamWaitEvent(ctx->stream, evs[t], 0) != cudaSuccess) rc = rc ? rc : LPBFMM_ERR_CUDA;
-  }
+  if (!join()) rc = rc ? rc : LPBFMM_ERR_CUDA;
+  if (cudaEventRecord(evs[nthr], caller) != cudaSuccess) rc = rc ? rc : LPBFMM_ERR_CUDA;
+  for (auto ctx : uctx)
+    if (ctx->stream != caller && cudaStreamWaitEvent(ctx->stream, evs[nthr], 0) != cudaSuccess) rc = rc ? rc : LPBFMM_ERR_CUDA;
   for (auto &ev : evs) cudaEventDestroy(ev);
   return rc;
 }

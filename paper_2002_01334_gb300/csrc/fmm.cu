@@ -7,6 +7,7 @@
 #include "internal.h"
 #include "tc.cuh"
 
+#include <algorithm>
 #include <mutex>
 
 namespace lpb {
@@ -685,12 +686,6 @@ __global__ void __launch_bounds__(256, 1) k_m2l_f32(const XJob *jobs, int njobs,
 }
 
 // L[box][k] += sum over the partial slots, in slot order (deterministic)
-struct RJob {
-  const void *part;
-  void *L;
-  int64_t n;     // boxes x K
-  int64_t e0;    // first element of this job in the flattened launch
-};
 template <typename T>
 __global__ void k_m2l_reduce(const RJob *jobs, int njobs, int K) {
   typedef typename C2<T>::t T2;
@@ -1167,19 +1162,26 @@ __device__ __forceinline__ void p2p_warp_pass(int lane, uint32_t t0, uint32_t tc
   }
 }
 
-__global__ void __launch_bounds__(32 * P2P_WARPS, 6) k_p2p_free_f32(const uint32_t *d_nb, const uint64_t *bkey,
-                                                                    const uint32_t *bstart, const uint32_t *bcount,
-                                                                    const int32_t *ulist, const float4 *h4,
-                                                                    const float4 *l4, const uint32_t *src, float hh,
-                                                                    float hl, float lam, double scale, double *phi,
-                                                                    double *field) {
+__global__ void __launch_bounds__(32 * P2P_WARPS, 6) k_p2p_free_f32(const P2PJob *jobs, int njobs) {
   __shared__ __align__(16) float4 sh_[P2P_WARPS][2][P2P_WSRC], sl_[P2P_WARPS][2][P2P_WSRC];
   __shared__ uint32_t nb_start_[P2P_WARPS][NNEAR], nb_cnt_[P2P_WARPS][NNEAR];
   __shared__ int nb_o_[P2P_WARPS][NNEAR];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].block0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const P2PJob &J = jobs[lo];
+  const uint32_t *bstart = J.bstart, *bcount = J.bcount, *src = J.src;
+  const int32_t *ulist = J.ulist;
+  const float4 *h4 = J.h4, *l4 = J.l4;
+  const float hh = J.hh, hl = J.hl, lam = J.lam;
+  const double scale = J.scale;
+  double *phi = J.phi, *field = J.field;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * P2P_WARPS + w;
+  const uint32_t gw = (uint32_t)((int64_t)blockIdx.x - J.block0) * P2P_WARPS + w;
   const uint32_t box = gw >> 1, half = gw & 1;
-  if (box >= *d_nb) return;
+  if (box >= *J.d_nb) return;
   const uint32_t tst = bstart[box], tcnt = bcount[box];
   if (64 * half >= tcnt) return;
   uint32_t *nb_start = nb_start_[w], *nb_cnt = nb_cnt_[w];
@@ -1491,31 +1493,24 @@ __global__ void k_tc_pack_w(const float *ops, int ncls_types, int ntypes, const 
   }
 }
 
-// unrotated source rows in real-coordinate order (FP32), ldr = 32 NC floats per (box, type)
-__global__ void k_tc_pack_raw(const float2 *M, int64_t nrows, int K, int p, int ldr, float *raw) {
-  const int64_t total = nrows * ldr;
+// unrotated source rows in real-coordinate order (FP32), ldr = 32 NC floats per (box, type); with
+// tmask, bit tau of tmask[box] is set when the row of source type tau has a nonzero entry (a zero
+// row adds nothing, so the M2L may skip that type for that box)
+__global__ void k_tc_pack_raw(const float2 *M, int64_t nrows, int K, int p, int ldr, float *raw, int ntypes,
+                              uint32_t *tmask) {
+  const int64_t total = nrows * ldr;  // a multiple of 32: every warp is full and within one row
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = e / ldr;
     const int code = tc_remap((int)(e % ldr), K, p);
-    raw[e] = code >= 0 ? M[b * K + code].x : (code <= -2 ? M[b * K + (-code - 2)].y : 0.f);
+    const float v = code >= 0 ? M[b * K + code].x : (code <= -2 ? M[b * K + (-code - 2)].y : 0.f);
+    raw[e] = v;
+    if (tmask) {
+      const unsigned nz = __ballot_sync(0xffffffffu, v != 0.f);
+      if ((threadIdx.x & 31) == 0 && nz) atomicOr(&tmask[b / ntypes], 1u << (int)(b % ntypes));
+    }
   }
 }
 
-struct TJob {
-  const float *raw;         // source rows [nsb][ntypes][ldr], unrotated real coordinates
-  const float *wimg;        // [ncls][ntypes] operator images (k_tc_pack_w)
-  const float *rotcol;      // [NOFF][ldr] (cos, sin) of m phi per real column pair (make_rotcol)
-  const int32_t *vlist;     // [ntb][NOFF]
-  const int32_t *cls_of;    // [NOFF]
-  const int32_t *tlist;     // target boxes (nullptr: octant or plain tiles over 0..ntb-1)
-  const uint32_t *d_ntl;    // number of entries of tlist (device)
-  float2 *L;                // partial sums [ntb][M2L_NSLOT][K]
-  int64_t ntb, item0;
-  int slot0, ntypes;
-  const uint32_t *pstart, *pcount;  // octant tiles (nullptr: plain tiles of 128)
-  const uint64_t *ckey;
-  int64_t npar;
-};
 constexpr int TC_MAXSTEP = SLICE_OFFS * 2 * (MAXLAYER - 1);
 
 constexpr int TC_ROWS = 128, TC_WORKERS = 256, TC_THREADS = TC_WORKERS + 32;
@@ -1564,7 +1559,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   __shared__ int steps[TC_MAXSTEP];  // (offset << 4) | source type
   __shared__ int remap_s[N], mcol[N];  // coordinate -> half index code; m of that coefficient
   __shared__ int nsteps;
-  __shared__ unsigned hasmask[HASW];
+  __shared__ unsigned tmk[SLICE_OFFS];  // per offset of the slice: the source types some row needs
   // full[b]: the workers have staged buffer b (TC_WORKERS arrivals); empty[b]: its MMAs are done;
   // accbar[a]: a step's MMAs into accumulator a are done; foldbar[a]: the workers have read it
   // wfull[b]: the operator chunk of buffer b has landed (one bulk copy, issued by thread 0)
@@ -1611,22 +1606,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     }
     tid_[tid] = t;
   }
-  if (tid < HASW) hasmask[tid] = 0u;
+  for (int k = tid; k < SLICE_OFFS; k += TC_THREADS) tmk[k] = 0u;
   __syncthreads();
   if (tid < TC_ROWS) {
     const int t = tid_[tid];
     if (t >= 0)
       for (int k = 0; k < SLICE_OFFS; ++k) {
         const int o = slice * SLICE_OFFS + k;
-        if (J.cls_of[o] >= 0 && J.vlist[(size_t)t * NOFF + o] >= 0) atomicOr(&hasmask[k >> 5], 1u << (k & 31));
+        const int sb = J.cls_of[o] >= 0 ? J.vlist[(size_t)t * NOFF + o] : -1;
+        if (sb >= 0) atomicOr(&tmk[k], J.tmask ? J.tmask[sb] : 0xffffffffu);
       }
   }
   __syncthreads();
   if (tid == 0) {
     int n = 0;
     for (int k = 0; k < SLICE_OFFS; ++k)
-      if (hasmask[k >> 5] & (1u << (k & 31)))
-        for (int tau = 0; tau < ntypes; ++tau) steps[n++] = ((slice * SLICE_OFFS + k) << 4) | tau;
+      for (int tau = 0; tau < ntypes; ++tau)
+        if ((tmk[k] >> tau) & 1u) steps[n++] = ((slice * SLICE_OFFS + k) << 4) | tau;
     nsteps = n;
   }
   __syncthreads();
@@ -1960,12 +1956,12 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         c.launches++;
         float *raw = c.arena.get<float>((size_t)ntb * N);
         k_tc_pack_raw<<<(unsigned)std::min<int64_t>(4096, (ntb * N + 255) / 256), 256, 0, c.stream>>>(
-            (const float2 *)g.Mfree[l], ntb, c.K, c.p, N, raw);
+            (const float2 *)g.Mfree[l], ntb, c.K, c.p, N, raw, 1, nullptr);
         LPB_LAUNCH();
         c.launches++;
         TJob j;
         j.raw = raw; j.wimg = wimg; j.rotcol = c.rotcol;
-        j.vlist = g.vfree[l]; j.cls_of = tb.cls_free; j.tlist = nullptr; j.d_ntl = nullptr;
+        j.vlist = g.vfree[l]; j.cls_of = tb.cls_free; j.tmask = nullptr; j.tlist = nullptr; j.d_ntl = nullptr;
         j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = 0; j.ntypes = 1;
         const Level *par = l >= 3 ? &g.T.lev[l - 1] : nullptr;
         j.pstart = par ? par->start : nullptr;
@@ -1990,14 +1986,16 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
         c.launches++;
         const int64_t nir = g.I.lev[l].n * g.ntypes;
         float *raw = c.arena.get<float>((size_t)nir * N);
+        uint32_t *tmask = c.arena.get<uint32_t>((size_t)g.I.lev[l].n);
+        LPB_CUDA(cudaMemsetAsync(tmask, 0, sizeof(uint32_t) * g.I.lev[l].n, c.stream));
         k_tc_pack_raw<<<(unsigned)std::min<int64_t>(4096, (nir * N + 255) / 256), 256, 0, c.stream>>>(
-            (const float2 *)g.Mimg[l], nir, c.K, c.p, N, raw);
+            (const float2 *)g.Mimg[l], nir, c.K, c.p, N, raw, g.ntypes, tmask);
         LPB_LAUNCH();
         c.launches++;
         for (int kt = 0; kt < 2 * c.ws + 1; ++kt) {
           TJob j;
           j.raw = raw; j.wimg = wimg; j.rotcol = c.rotcol;
-          j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * NKT + kt) * NOFF;
+          j.vlist = g.vreact[l]; j.cls_of = tb.cls_react + ((g.a - 1) * NKT + kt) * NOFF; j.tmask = tmask;
           j.tlist = g.rows[l] + (size_t)kt * ntb; j.d_ntl = g.nrows[l] + kt;
           j.L = (float2 *)part; j.ntb = ntb; j.item0 = titems; j.slot0 = M2L_NSLICE; j.ntypes = g.ntypes;
           j.pstart = nullptr; j.pcount = nullptr; j.ckey = nullptr; j.npar = 0;
@@ -2014,6 +2012,15 @@ static void m2l_all_t(Ctx &c, std::vector<Group> &groups) {
   }
   if (jobs.empty() && tjobs.empty()) return;
   prof_mark(c, "m2l_prep");
+  if (c.def.on && !tjobs.empty() && jobs.empty()) {
+    // batched evaluation: the tensor-core M2L and the slot sums join a grouped launch
+    c.def.nc = tc_nc;
+    c.def.tc = tjobs;
+    c.def.tc_items = titems;
+    c.def.red = rjobs;
+    c.def.red_elems = relem;
+    return;
+  }
   if (!tjobs.empty()) {
     TJob *dj = c.arena.get<TJob>(tjobs.size());
     LPB_CUDA(cudaMemcpyAsync(dj, tjobs.data(), sizeof(TJob) * tjobs.size(), cudaMemcpyHostToDevice, c.stream));
@@ -2086,7 +2093,6 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   }
   PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
   if (dofree) {
-    prof_mark(c, "downward");
     // the free-space near field at the free-space leaves (level Df)
     const Level &Lf = g.T.lev[g.Df];
     const int Df = g.Df;
@@ -2097,13 +2103,17 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
       k_split_points<<<nb, 64, 0, c.stream>>>(Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.T.x, g.T.y, g.T.z, g.T.q,
                                                geo_at<T>(g, Df), h4, l4);
       LPB_LAUNCH();
+      c.launches++;
+      // the near field itself joins the evaluation's (or the batch's) one P2P launch
       const double hD = g.h(Df);
-      const float hh = (float)hD, hl = (float)(hD - (double)hh);
-      k_p2p_free_f32<<<(2 * nb + P2P_WARPS - 1) / P2P_WARPS, 32 * P2P_WARPS, 0, c.stream>>>(
-          Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.ufree, h4, l4, g.T.src, hh, hl, (float)c.md.lam[g.l],
-          1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
-      LPB_LAUNCH();
-      c.launches += 2;
+      P2PJob j;
+      j.d_nb = Lf.d_n; j.bkey = Lf.key; j.bstart = Lf.pstart; j.bcount = Lf.pcount; j.ulist = g.ufree;
+      j.h4 = h4; j.l4 = l4; j.src = g.T.src; j.phi = phi; j.field = field;
+      j.scale = 1.0 / (4.0 * PI * c.md.eps[g.l]);
+      j.hh = (float)hD; j.hl = (float)(hD - (double)j.hh); j.lam = (float)c.md.lam[g.l];
+      j.block0 = c.def.p2p_blocks;
+      c.def.p2p.push_back(j);
+      c.def.p2p_blocks += (2 * (int64_t)nb + P2P_WARPS - 1) / P2P_WARPS;
     } else {
       k_p2p_free<T><<<(unsigned)Lf.n, P2P_TPB, 0, c.stream>>>(
           Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q, g.T.src, geo_at<T>(g, Df),
@@ -2111,7 +2121,6 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
       LPB_LAUNCH();
       c.launches++;
     }
-    prof_mark(c, "p2p");
   }
   if (react_near && g.ureact && g.nodes) {
     k_p2p_react<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(
@@ -2123,15 +2132,101 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
   }
 }
 
-void run_fmm_all(Ctx &c, std::vector<Group> &groups, double *phi, double *field) {
+// one launch of the FP32 free-space near field over the jobs (block0 renumbered from 0)
+static void launch_p2p(Ctx &c, const std::vector<P2PJob> &jobs, int64_t blocks, cudaStream_t st) {
+  if (jobs.empty() || blocks <= 0) return;
+  P2PJob *dj = c.arena.get<P2PJob>(jobs.size());
+  LPB_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(P2PJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+  k_p2p_free_f32<<<(unsigned)blocks, 32 * P2P_WARPS, 0, st>>>(dj, (int)jobs.size());
+  LPB_LAUNCH();
+  c.launches++;
+}
+
+void run_fmm_front(Ctx &c, std::vector<Group> &groups) {
+  c.def.clear();
   const bool d = c.opts.precision == LPBFMM_FP64;
   for (auto &g : groups) d ? upward_t<double>(c, g, g.parts) : upward_t<float>(c, g, g.parts);
   prof_mark(c, "upward");
   d ? m2l_all_t<double>(c, groups) : m2l_all_t<float>(c, groups);
   prof_mark(c, "m2l");
+}
+
+void run_fmm_back(Ctx &c, std::vector<Group> &groups, double *phi, double *field) {
+  const bool d = c.opts.precision == LPBFMM_FP64;
+  c.def.p2p.clear();
+  c.def.p2p_blocks = 0;
   for (auto &g : groups)
     d ? downward_t<double>(c, g, g.parts, phi, field) : downward_t<float>(c, g, g.parts, phi, field);
   prof_mark(c, "downward");
+  if (!c.def.on) {
+    launch_p2p(c, c.def.p2p, c.def.p2p_blocks, c.stream);
+    c.def.p2p.clear();
+    c.def.p2p_blocks = 0;
+    prof_mark(c, "p2p");
+  }
+}
+
+void launch_deferred(const std::vector<Ctx *> &cs, int stage, cudaStream_t st) {
+  if (cs.empty()) return;
+  Ctx &c0 = *cs[0];
+  if (stage == 0) {
+    // per truncation order (the kernels take K and p as arguments): one tensor-core M2L launch,
+    // then one launch of the slot sums (FP32 partials: the tensor-core path runs in mixed mode)
+    std::vector<int> orders;
+    for (Ctx *c : cs)
+      if (c->def.nc && std::find(orders.begin(), orders.end(), c->p) == orders.end()) orders.push_back(c->p);
+    for (int p : orders) {
+      std::vector<TJob> tj;
+      std::vector<RJob> red;
+      int64_t items = 0, relem = 0;
+      Ctx *lead = nullptr;
+      for (Ctx *c : cs) {
+        if (!c->def.nc || c->p != p) continue;
+        if (!lead) lead = c;
+        for (TJob j : c->def.tc) {
+          j.item0 += items;
+          tj.push_back(j);
+        }
+        items += c->def.tc_items;
+        for (RJob r : c->def.red) {
+          r.e0 += relem;
+          red.push_back(r);
+        }
+        relem += c->def.red_elems;
+      }
+      TJob *dj = c0.arena.get<TJob>(tj.size());
+      LPB_CUDA(cudaMemcpyAsync(dj, tj.data(), sizeof(TJob) * tj.size(), cudaMemcpyHostToDevice, st));
+      switch (lead->def.nc) {
+#define LPB_TC_GROUP(NCV)                                                                                    \
+  case NCV:                                                                                                 \
+    LPB_ATTR_ONCE(k_m2l_tc<NCV>, tc_smem(NCV));                                                             \
+    k_m2l_tc<NCV><<<(unsigned)items, TC_THREADS, tc_smem(NCV), st>>>(dj, (int)tj.size(), lead->K, p, c0.status); \
+    break;
+        LPB_TC_GROUP(1) LPB_TC_GROUP(2) LPB_TC_GROUP(3) LPB_TC_GROUP(4)
+#undef LPB_TC_GROUP
+      }
+      LPB_LAUNCH();
+      c0.launches++;
+      if (!red.empty()) {
+        RJob *dr = c0.arena.get<RJob>(red.size());
+        LPB_CUDA(cudaMemcpyAsync(dr, red.data(), sizeof(RJob) * red.size(), cudaMemcpyHostToDevice, st));
+        k_m2l_reduce<float><<<(unsigned)((relem + 255) / 256), 256, 0, st>>>(dr, (int)red.size(), lead->K);
+        LPB_LAUNCH();
+        c0.launches++;
+      }
+    }
+  } else {
+    std::vector<P2PJob> pj;
+    int64_t blocks = 0;
+    for (Ctx *c : cs) {
+      for (P2PJob j : c->def.p2p) {
+        j.block0 += blocks;
+        pj.push_back(j);
+      }
+      blocks += c->def.p2p_blocks;
+    }
+    launch_p2p(c0, pj, blocks, st);
+  }
 }
 
 }  // namespace lpb

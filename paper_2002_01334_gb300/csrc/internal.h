@@ -192,6 +192,64 @@ struct Group {
   double h(int lev) const { return 2.0 * root[3] / double(1 << lev); }
 };
 
+// Job records of the grouped launches (one launch runs many jobs; a block finds its job by a
+// binary search on the first work item of each job).
+// Tensor-core M2L (k_m2l_tc): one (group, level, row class) of target boxes against one source tree.
+struct TJob {
+  const float *raw;         // source rows [nsb][ntypes][ldr], unrotated real coordinates
+  const float *wimg;        // [ncls][ntypes] operator images (k_tc_pack_w)
+  const float *rotcol;      // [NOFF][ldr] (cos, sin) of m phi per real column pair (make_rotcol)
+  const int32_t *vlist;     // [ntb][NOFF]
+  const int32_t *cls_of;    // [NOFF]
+  const uint32_t *tmask;    // [nsb] source types with a nonzero row (nullptr: every type)
+  const int32_t *tlist;     // target boxes (nullptr: octant or plain tiles over 0..ntb-1)
+  const uint32_t *d_ntl;    // number of entries of tlist (device)
+  float2 *L;                // partial sums [ntb][M2L_NSLOT][K]
+  int64_t ntb, item0;
+  int slot0, ntypes;
+  const uint32_t *pstart, *pcount;  // octant tiles (nullptr: plain tiles of 128)
+  const uint64_t *ckey;
+  int64_t npar;
+};
+// Sum of a level's M2L partial slots into its local expansions (k_m2l_reduce).
+struct RJob {
+  const void *part;
+  void *L;
+  int64_t n;     // boxes x K
+  int64_t e0;    // first element of this job in the flattened launch
+};
+// FP32 free-space near field of one target group's leaves (k_p2p_free_f32).
+struct P2PJob {
+  const uint32_t *d_nb;     // number of leaves (device)
+  const uint64_t *bkey;     // leaf keys
+  const uint32_t *bstart, *bcount;  // leaf point ranges
+  const int32_t *ulist;     // [nb][NNEAR] near leaves or -1
+  const float4 *h4, *l4;    // points as FP32 hi / lo offsets from their leaf centre, charge in h4.w
+  const uint32_t *src;      // input index of each point
+  double *phi, *field;      // outputs (input order)
+  double scale;             // 1 / (4 pi eps)
+  float hh, hl, lam;        // leaf side as FP32 hi + lo; screening
+  int64_t block0;           // first block of this job in the launch
+};
+
+// launches of one evaluation held back for one grouped launch over several contexts
+// (lpbfmm_eval_batched): the tensor-core M2L, its slot sums, the FP32 free-space near field
+struct Deferred {
+  bool on = false;
+  int nc = 0;                       // column chunks of the tensor-core M2L (0: none recorded)
+  std::vector<TJob> tc;             // item0 relative to this context
+  std::vector<RJob> red;            // e0 relative to this context
+  std::vector<P2PJob> p2p;          // block0 relative to this context
+  int64_t tc_items = 0, red_elems = 0, p2p_blocks = 0;
+  void clear() {
+    nc = 0;
+    tc.clear();
+    red.clear();
+    p2p.clear();
+    tc_items = red_elems = p2p_blocks = 0;
+  }
+};
+
 struct Ctx {
   Medium md;
   int p = 10, K = 66;
@@ -224,6 +282,7 @@ struct Ctx {
   cudaEvent_t ev[64];
   int nev = 0;
   int launches = 0;
+  Deferred def;
 };
 
 // tree.cu
@@ -255,7 +314,15 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
                   double *out);
 
 // fmm.cu
-void run_fmm_all(Ctx &c, std::vector<Group> &groups, double *phi, double *field);
+// upward pass and M2L of every group (with c.def.on the tensor-core M2L and its slot sums are
+// recorded in c.def instead of launched)
+void run_fmm_front(Ctx &c, std::vector<Group> &groups);
+// downward pass and near fields (with c.def.on the FP32 free-space near field is recorded)
+void run_fmm_back(Ctx &c, std::vector<Group> &groups, double *phi, double *field);
+// the recorded jobs of several contexts (all on the current device) as grouped launches on st:
+// stage 0 the tensor-core M2L and the slot sums, stage 1 the free-space near field.  Timeouts of
+// a grouped tensor-core launch are reported on the first context's status word.
+void launch_deferred(const std::vector<Ctx *> &cs, int stage, cudaStream_t st);
 
 // api.cu
 void prof_mark(Ctx &c, const char *name);

@@ -1,4 +1,4 @@
-"""Host logic of the leaf-size autotuner (paper_2002_01334_gb300/autotune.py): the candidate with
+"""Host logic of the autotuner (paper_2002_01334_gb300/autotune.py): the candidate with
 the smallest median time wins, the first on a tie, and every candidate is measured `repeats`
 times.  The CUDA timing harness itself needs a GPU."""
 import itertools
@@ -28,3 +28,27 @@ def test_choose_breaks_ties_by_order_and_rejects_empty():
     assert best == 64
     with pytest.raises(ValueError):
         autotune.choose((), lambda s: 1.0)
+
+
+def test_search_is_coordinate_descent_over_the_parameters_in_order():
+    # a separable cost: leaf 64 and react_levels 3 are best; every setting timed once per repeat
+    cost = {32: 9.0, 64: 4.0, 128: 5.0, 256: 7.0, 512: 8.0}
+    extra = {2: 3.0, 3: 1.0, 4: 2.0, 6: 2.5}
+    calls = []
+
+    def measure(s):
+        calls.append(tuple(sorted(s.items())))
+        return cost[s["max_per_leaf"]] + extra[s["react_levels"]]
+
+    best, rows = autotune.search(autotune.SPACE, measure, start=autotune.DEFAULTS, repeats=2)
+    assert best == {"max_per_leaf": 64, "react_levels": 3}
+    # leaf sizes at the default react_levels, then react_levels at leaf 64 (64, 4 already timed)
+    assert [r[0] for r in rows] == [{"max_per_leaf": c, "react_levels": 4} for c in (32, 64, 128, 256, 512)] + \
+        [{"max_per_leaf": 64, "react_levels": r} for r in (2, 3, 6)]
+    assert len(calls) == 2 * len(rows)
+    assert rows[1][1] == 6.0
+
+
+def test_search_ties_keep_the_first_candidate():
+    best, _ = autotune.search((("a", (3, 1, 2)), ("b", (5, 4))), lambda s: 1.0, repeats=1)
+    assert best == {"a": 3, "b": 5}

@@ -552,6 +552,36 @@ def test_batched_matches_individual():
         assert rel(got, ref[0]) < 2e-5
 
 
+def test_batched_grouped_launches_match_individual_evaluations():
+    """lpbfmm_eval_batched in mixed precision: the tensor-core M2L and slot sums of all systems run
+    as one launch per truncation order, the FP32 near field as one launch over all systems.  Orders
+    8, 9 and 10 (9 and 10 share the tensor-core tile width but not K), and one context serving two
+    systems (evaluated whole, in turn).  Every system equals its own lpbfmm_eval: the same kernels
+    on the same data, so bit for bit."""
+    systems = inputs.batch(nsys=7, nmin=300, nmax=3000, seed=inputs.BASE_SEED + 77)
+    orders = [8, 9, 10, 8, 10, 9, 9]
+    # system 6: the charges of system 5 with the signs flipped, evaluated by system 5's context
+    systems[6] = dict(systems[5], q=-systems[5]["q"])
+    ctxs, offs = [], [0]
+    for k, (s, p) in enumerate(zip(systems, orders)):
+        m = s["medium"]
+        ctxs.append(ctxs[5] if k == 6 else F.Context(m["d"], m["eps"], m["lam"], p, precision=F.MIXED))
+        offs.append(offs[-1] + len(s["q"]))
+    cat = lambda key: np.concatenate([s[key] for s in systems])
+    q = torch.tensor(cat("q"), device=DEV)
+    x = torch.tensor(cat("xyz"), device=DEV)
+    l = torch.tensor(cat("layer"), dtype=torch.int32, device=DEV)
+    phi, fld = F.eval_batched(ctxs, offs, q, x, l)
+    torch.cuda.synchronize()
+    for k in range(len(systems)):
+        a, b = offs[k], offs[k + 1]
+        p1, f1 = ctxs[k].eval(q[a:b], x[a:b], l[a:b])
+        torch.cuda.synchronize()
+        assert torch.equal(phi[a:b], p1) and torch.equal(fld[a:b], f1), k
+    for c in ctxs[:6]:
+        assert c.status() == 0
+
+
 def test_paper_accuracy_experiment_matches_the_cpu_fmm_table():
     """The paper's accuracy-against-p experiment (Sec. 4, shown there as a figure) on its own
     workload (912 + 640 + 1296 charges in the irregular bodies, eps = (1, 8.6, 20.5), lambda = (1.2,
