@@ -64,19 +64,20 @@ def search(space, measure, start=None, repeats=2):
 
 def cuda_measure(medium, p, precision, q, xyz, layer, stream=None, warmup=1):
     """(measure, close): measure(settings) -> ms of one evaluation of these device arrays by a
-    context created with those options (max_per_leaf, react_levels; created once per setting and
-    warmed up), timed with CUDA events; close() releases the contexts.  An int stands for
-    {"max_per_leaf": int}."""
+    context created with those options (max_per_leaf, react_levels; created when the setting
+    changes, the previous setting's context released first, and warmed up), timed with CUDA
+    events; close() releases the context.  An int stands for {"max_per_leaf": int}."""
     import torch
 
     from . import lpbfmm as F
 
-    contexts = {}
+    contexts = {}  # the current setting's context only (the search times one setting at a time)
 
     def measure(s):
         s = {"max_per_leaf": s} if isinstance(s, int) else dict(s)
         key = tuple(sorted(s.items()))
         if key not in contexts:
+            close()
             ctx = F.Context(medium["d"], medium["eps"], medium["lam"], p, precision=precision, stream=stream, **s)
             for _ in range(warmup):
                 ctx.eval(q, xyz, layer)
@@ -101,17 +102,19 @@ def cuda_measure(medium, p, precision, q, xyz, layer, stream=None, warmup=1):
 
 def batch_measure(systems, p, precision, offsets, q, xyz, layer, stream=None, warmup=1):
     """(measure, close) for lpbfmm_eval_batched: measure(settings) -> ms of one batched evaluation
-    of all systems, every context created with those options."""
+    of all systems, every context created with those options (one setting's contexts alive at a
+    time)."""
     import torch
 
     from . import lpbfmm as F
 
-    sets = {}
+    sets = {}  # the current setting's contexts only (the search times one setting at a time)
 
     def measure(s):
         s = dict(s)
         key = tuple(sorted(s.items()))
         if key not in sets:
+            close()
             ctxs = [F.Context(x["medium"]["d"], x["medium"]["eps"], x["medium"]["lam"], p, precision=precision,
                               stream=stream, **s) for x in systems]
             for _ in range(warmup):

@@ -336,6 +336,14 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
       }
     }
   }
+  // the free-space operators on the side stream, concurrently with the image trees and lists
+  LPB_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+  LPB_CUDA(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+  {
+    OnStream on(c, c.side);
+    for (auto &g : c.groups) build_operators(c, g, g.parts, 1);
+    LPB_CUDA(cudaEventRecord(c.ev_free, c.side));
+  }
   for (auto &g : c.groups) build_group_images(c, g, n, q, xyz, layer, rank, cnt);
   for (auto &g : c.groups) build_group_boxes(c, g);
   // box counts to host
@@ -376,13 +384,21 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
     c.stab_lmin = hmin < 1e300 ? lmin * hmin : lmin;
     c.stab_bes = nullptr;
   }
-  for (auto &g : c.groups) {
-    build_operators(c, g, g.parts);
-    if ((g.parts & 2) && g.ureact) {
-      double zt, zs;
-      z_gaps(g, zt, zs);
-      build_near_nodes(c, g, std::max(zt + zs, 1e-12), (c.ws + 1) * std::sqrt(2.0) * g.h(g.D));
+  // reaction tables, operators and near-field nodes on the side stream, after the lists (the M2L
+  // waits for them)
+  LPB_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+  {
+    OnStream on(c, c.side);
+    LPB_CUDA(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+    for (auto &g : c.groups) {
+      build_operators(c, g, g.parts, 2);
+      if ((g.parts & 2) && g.ureact) {
+        double zt, zs;
+        z_gaps(g, zt, zs);
+        build_near_nodes(c, g, std::max(zt + zs, 1e-12), (c.ws + 1) * std::sqrt(2.0) * g.h(g.D));
+      }
     }
+    LPB_CUDA(cudaEventRecord(c.ev_join, c.side));
   }
   prof_mark(c, "tables+ops");
   run_fmm_front(c, c.groups);
@@ -486,6 +502,10 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     LPB_CUDA(cudaMemset(c->status, 0, sizeof(int)));
     LPB_CUDA(cudaMallocHost(&c->h_pinned, 1 << 16));
     for (int k = 0; k < 64; ++k) LPB_CUDA(cudaEventCreate(&c->ev[k]));
+    LPB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    LPB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    LPB_CUDA(cudaEventCreateWithFlags(&c->ev_free, cudaEventDisableTiming));
+    LPB_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     init_fmm_tables(*c);
   } catch (const CudaError &e) {
     int code = map_error(e);
@@ -771,6 +791,7 @@ const char *lpbfmm_strerror(int code) {
 void lpbfmm_destroy(lpbfmm_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
   h->arena.release();
   if (h->adj) cudaFree(h->adj);
   if (h->gaunt) cudaFree(h->gaunt);
@@ -782,6 +803,10 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (int k = 0; k < 64; ++k)
     if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_free) cudaEventDestroy(h->ev_free);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
 }
 

@@ -2145,8 +2145,12 @@ static void launch_p2p(Ctx &c, const std::vector<P2PJob> &jobs, int64_t blocks, 
 void run_fmm_front(Ctx &c, std::vector<Group> &groups) {
   c.def.clear();
   const bool d = c.opts.precision == LPBFMM_FP64;
+  // the free-space operators (side stream) are complete before the upward pass
+  if (c.ev_free) LPB_CUDA(cudaStreamWaitEvent(c.stream, c.ev_free, 0));
   for (auto &g : groups) d ? upward_t<double>(c, g, g.parts) : upward_t<float>(c, g, g.parts);
   prof_mark(c, "upward");
+  // the reaction tables and operators (side stream) are complete before any M2L
+  if (c.ev_join) LPB_CUDA(cudaStreamWaitEvent(c.stream, c.ev_join, 0));
   d ? m2l_all_t<double>(c, groups) : m2l_all_t<float>(c, groups);
   prof_mark(c, "m2l");
 }

@@ -283,6 +283,19 @@ struct Ctx {
   int nev = 0;
   int launches = 0;
   Deferred def;
+  // operators are built on a second stream: the free-space ones concurrently with the image
+  // trees and lists (the upward pass waits for them, ev_free), the reaction ones concurrently
+  // with the upward pass (the M2L waits for them, ev_join)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_free = nullptr, ev_join = nullptr;
+};
+
+// work of one scope on another stream of the context (restored on exit, also by an exception)
+struct OnStream {
+  Ctx &c;
+  cudaStream_t saved;
+  OnStream(Ctx &c_, cudaStream_t s) : c(c_), saved(c_.stream) { c.stream = s; }
+  ~OnStream() { c.stream = saved; }
 };
 
 // tree.cu
@@ -306,7 +319,9 @@ void build_group_lists(Ctx &c, Group &g, int parts);
 void layer_rank(Ctx &c, int64_t n, const int32_t *layer, int lay, uint32_t *rank);
 
 // ops.cu
-void build_operators(Ctx &c, Group &g, int parts);
+// which: 1 the free-space operators (M2M, L2L, free M2L; need only the depths and roots),
+// 2 the reaction tables and operators (need the interaction lists)
+void build_operators(Ctx &c, Group &g, int parts, int which);
 void build_near_nodes(Ctx &c, Group &g, double zeta_min, double rho_max);
 void stable_noalloc(Ctx &c, int l, int a, int lp, int b, double h, double rho, double zt, double zs, int Kmax,
                     double *out);

@@ -537,10 +537,15 @@ __global__ void k_react_assemble(const RDesc *descs, int p, int K, int KT, const
     float2 ap[ASM_CC], am[ASM_CC];
 #pragma unroll
     for (int k = 0; k < ASM_CC; ++k) ap[k] = am[k] = make_float2(0.f, 0.f);
-    for (int s = 0; s <= smax; ++s) {
+    // the entry's coefficients, all loads in flight at once (smax <= p + 1 < PMAX + 2)
+    float2 cv[PMAX + 2];
+#pragma unroll
+    for (int s = 0; s < PMAX + 2; ++s) cv[s] = s <= smax ? cf[s] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < PMAX + 2; ++s) {
       const int Kk = 1 + m + mu + 2 * s;
-      if (Kk > KT) break;
-      const float2 c = cf[s];
+      if (s > smax || Kk > KT) break;
+      const float2 c = cv[s];
       const int ip = ((Kk * (KT + 1)) + adp) * 4 + ij, im = ((Kk * (KT + 1)) + dm) * 4 + ij;
 #pragma unroll
       for (int k = 0; k < ASM_CC; ++k) {
@@ -606,10 +611,11 @@ __global__ void k_near_nodes(Medium md, int l, int a, int ntypes, double umax, d
 }
 
 template <typename T>
-static void build_ops_t(Ctx &c, Group &g, int parts) {
+static void build_ops_t(Ctx &c, Group &g, int parts, int which) {
   const int p = c.p, K = c.K;
   const size_t KK = (size_t)K * K;
   const double lam_t = c.md.lam[g.l];
+  if (which & 1) {
   std::vector<OpDesc> descs;
   size_t total = 0;
   auto add = [&](int kind, int out_inv, int in_inv, double lam, double bx, double by, double bz, double xout,
@@ -692,7 +698,8 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
     LPB_LAUNCH();
     c.launches += 2;
   }
-  if (!(parts & 2) || !g.I.np) return;
+  }
+  if (!(which & 2) || !(parts & 2) || !g.I.np) return;
   // reaction: one descriptor per (level, type)
   const int KT = 2 * p + 3, NS = p + 2;
   const size_t TS = (size_t)(KT + 1) * (KT + 1) * 4;
@@ -775,9 +782,9 @@ static void build_ops_t(Ctx &c, Group &g, int parts) {
   }
 }
 
-void build_operators(Ctx &c, Group &g, int parts) {
-  if (c.opts.precision == LPBFMM_FP64) build_ops_t<double>(c, g, parts);
-  else build_ops_t<float>(c, g, parts);
+void build_operators(Ctx &c, Group &g, int parts, int which) {
+  if (c.opts.precision == LPBFMM_FP64) build_ops_t<double>(c, g, parts, which);
+  else build_ops_t<float>(c, g, parts, which);
 }
 
 void build_near_nodes(Ctx &c, Group &g, double zeta_min, double rho_max) {
