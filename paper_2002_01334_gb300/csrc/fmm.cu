@@ -1572,8 +1572,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   }
   const TJob &J = jobs[lo];
   const int64_t local = (int64_t)blockIdx.x - J.item0;
-  const int slice = (int)(local % M2L_NSLICE);
-  const int64_t ti = local / M2L_NSLICE;
+  // slice-major: the CTAs resident at one time share a dx-slice, hence the operator classes of
+  // its offsets, which then stay in L2 (a level's reaction operators alone exceed it)
+  const int64_t ntiles = J.pstart ? 8 * ((J.npar + TC_ROWS - 1) / TC_ROWS) : (J.ntb + TC_ROWS - 1) / TC_ROWS;
+  const int slice = (int)(local / ntiles);
+  const int64_t ti = local % ntiles;
   const int64_t ntl = J.tlist ? (int64_t)*J.d_ntl : J.ntb;
   if (J.pstart ? (ti >> 3) * TC_ROWS >= J.npar : ti * TC_ROWS >= ntl) return;
   // worker thread (tid < TC_WORKERS) = (row, half): row = target slot and TMEM lane, half = which
