@@ -38,9 +38,10 @@ def choose(candidates, measure, repeats=3):
 
 def search(space, measure, start=None, repeats=2):
     """Coordinate descent: for each (name, candidates) of space in order, time every candidate with
-    the other parameters at their best so far (measure(settings dict) -> ms; each distinct setting
-    timed once, `repeats` times) and keep the fastest.  Returns (best settings, rows), rows being
-    [settings, median ms] for every setting timed, in order."""
+    the other parameters at their best so far (measure(settings dict) -> ms, or None when the
+    setting cannot run, e.g. out of device memory; each distinct setting timed once, `repeats`
+    times) and keep the fastest.  Returns (best settings, rows), rows being [settings, median ms
+    or None] for every setting tried, in order."""
     best = dict(start or {})
     for name, cands in space:
         best.setdefault(name, cands[0])
@@ -50,15 +51,23 @@ def search(space, measure, start=None, repeats=2):
     def timed(settings):
         key = tuple(sorted(settings.items()))
         if key not in seen:
-            seen[key] = statistics.median(measure(dict(settings)) for _ in range(max(1, repeats)))
+            ts = []
+            for _ in range(max(1, repeats)):
+                t = measure(dict(settings))
+                if t is None:
+                    ts = None
+                    break
+                ts.append(t)
+            seen[key] = statistics.median(ts) if ts else None
             rows.append([dict(settings), seen[key]])
         return seen[key]
 
+    inf = float("inf")
     for name, cands in space:
         if not cands:
             raise ValueError("no candidates for %s" % name)
         ms = {c: timed(dict(best, **{name: c})) for c in cands}
-        best[name] = min(cands, key=lambda c: (ms[c], cands.index(c)))
+        best[name] = min(cands, key=lambda c: (inf if ms[c] is None else ms[c], cands.index(c)))
     return best, rows
 
 
@@ -76,21 +85,28 @@ def cuda_measure(medium, p, precision, q, xyz, layer, stream=None, warmup=1):
     def measure(s):
         s = {"max_per_leaf": s} if isinstance(s, int) else dict(s)
         key = tuple(sorted(s.items()))
-        if key not in contexts:
+        try:
+            if key not in contexts:
+                close()
+                ctx = F.Context(medium["d"], medium["eps"], medium["lam"], p, precision=precision, stream=stream,
+                                **s)
+                contexts[key] = ctx
+                for _ in range(warmup):
+                    ctx.eval(q, xyz, layer)
+            ctx = contexts[key]
+            st = stream if stream is not None else torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            ctx.eval(q, xyz, layer)
+            e1.record(st)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        except F.LpbfmmError as e:
+            if e.code != F.ERR_OOM:
+                raise
             close()
-            ctx = F.Context(medium["d"], medium["eps"], medium["lam"], p, precision=precision, stream=stream, **s)
-            for _ in range(warmup):
-                ctx.eval(q, xyz, layer)
-            contexts[key] = ctx
-        ctx = contexts[key]
-        st = stream if stream is not None else torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        ctx.eval(q, xyz, layer)
-        e1.record(st)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+            return None
 
     def close():
         for ctx in contexts.values():
@@ -113,22 +129,29 @@ def batch_measure(systems, p, precision, offsets, q, xyz, layer, stream=None, wa
     def measure(s):
         s = dict(s)
         key = tuple(sorted(s.items()))
-        if key not in sets:
+        try:
+            if key not in sets:
+                close()
+                sets[key] = []
+                for x in systems:
+                    sets[key].append(F.Context(x["medium"]["d"], x["medium"]["eps"], x["medium"]["lam"], p,
+                                               precision=precision, stream=stream, **s))
+                for _ in range(warmup):
+                    F.eval_batched(sets[key], offsets, q, xyz, layer)
+            ctxs = sets[key]
+            st = stream if stream is not None else torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            F.eval_batched(ctxs, offsets, q, xyz, layer)
+            e1.record(st)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        except F.LpbfmmError as e:
+            if e.code != F.ERR_OOM:
+                raise
             close()
-            ctxs = [F.Context(x["medium"]["d"], x["medium"]["eps"], x["medium"]["lam"], p, precision=precision,
-                              stream=stream, **s) for x in systems]
-            for _ in range(warmup):
-                F.eval_batched(ctxs, offsets, q, xyz, layer)
-            sets[key] = ctxs
-        ctxs = sets[key]
-        st = stream if stream is not None else torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        F.eval_batched(ctxs, offsets, q, xyz, layer)
-        e1.record(st)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+            return None
 
     def close():
         for ctxs in sets.values():

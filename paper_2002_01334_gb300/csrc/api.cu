@@ -289,7 +289,37 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
       c.groups.push_back(g);
     }
   }
-  for (auto &g : c.groups) build_group_targets(c, g, n, q, xyz, layer, rank, cnt);
+  // per-group streams (the groups' trees are independent): fork from / join into c.stream; in a
+  // batched evaluation the systems already run concurrently, and the groups stay on c.stream
+  const int NGS = c.def.on ? 0 : std::min<int>(Ctx::GROUP_STREAMS, (int)c.groups.size());
+  auto fork_groups = [&]() {
+    LPB_CUDA(cudaEventRecord(c.ev_gfork, c.stream));
+    for (int k = 0; k < NGS; ++k) LPB_CUDA(cudaStreamWaitEvent(c.gs[k], c.ev_gfork, 0));
+  };
+  auto join_groups = [&]() {
+    for (int k = 0; k < NGS; ++k) {
+      LPB_CUDA(cudaEventRecord(c.ev_gjoin[k], c.gs[k]));
+      LPB_CUDA(cudaStreamWaitEvent(c.stream, c.ev_gjoin[k], 0));
+    }
+  };
+  auto per_group = [&](auto &&f) {
+    fork_groups();
+    for (size_t k = 0; k < c.groups.size(); ++k) {
+      OnStream on(c, NGS ? c.gs[k % NGS] : c.stream);
+      f((int)k, c.groups[k]);
+    }
+    join_groups();
+  };
+  const int G = (int)c.groups.size();
+  uint32_t *dc = nullptr;  // occupied boxes per level and group (automatic depth)
+  if (c.opts.uniform_depth <= 0) {
+    dc = c.arena.get<uint32_t>((size_t)G * (DMAX + 1));
+    LPB_CUDA(cudaMemsetAsync(dc, 0, sizeof(uint32_t) * G * (DMAX + 1), c.stream));
+  }
+  per_group([&](int k, Group &g) {
+    build_group_targets(c, g, n, q, xyz, layer, rank, cnt);
+    if (dc) count_levels(c, g, dc + (size_t)k * (DMAX + 1));
+  });
   // smallest distances of the group's targets and images to its interface (exact extremes of
   // monotone expressions of the z ranges)
   auto z_gaps = [&](const Group &g, double &zt, double &zs) {
@@ -308,13 +338,9 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
   // react_levels levels deeper, to the first level whose boxes are small enough that no target box and
   // image box are near (k_t + k_s >= ws for the closest rows): its near field, the costly direct
   // Sommerfeld integrals, then vanishes (Sec. 3.5, Remark 1)
-  const int G = (int)c.groups.size();
   if (c.opts.uniform_depth > 0) {
     for (auto &g : c.groups) g.D = g.Df = std::min(DMAX, std::max(2, c.opts.uniform_depth));
   } else {
-    uint32_t *dc = c.arena.get<uint32_t>((size_t)G * (DMAX + 1));
-    LPB_CUDA(cudaMemsetAsync(dc, 0, sizeof(uint32_t) * G * (DMAX + 1), c.stream));
-    for (int k = 0; k < G; ++k) count_levels(c, c.groups[k], dc + (size_t)k * (DMAX + 1));
     uint32_t *hc = (uint32_t *)c.h_pinned;
     LPB_CUDA(cudaMemcpyAsync(hc, dc, sizeof(uint32_t) * G * (DMAX + 1), cudaMemcpyDeviceToHost, c.stream));
     LPB_CUDA(cudaStreamSynchronize(c.stream));
@@ -344,8 +370,10 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
     for (auto &g : c.groups) build_operators(c, g, g.parts, 1);
     LPB_CUDA(cudaEventRecord(c.ev_free, c.side));
   }
-  for (auto &g : c.groups) build_group_images(c, g, n, q, xyz, layer, rank, cnt);
-  for (auto &g : c.groups) build_group_boxes(c, g);
+  per_group([&](int, Group &g) {
+    build_group_images(c, g, n, q, xyz, layer, rank, cnt);
+    build_group_boxes(c, g);
+  });
   // box counts to host
   {
     std::vector<const uint32_t *> srcs;
@@ -374,7 +402,7 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
       ++k;
     }
   }
-  for (auto &g : c.groups) build_group_lists(c, g, g.parts);
+  per_group([&](int, Group &g) { build_group_lists(c, g, g.parts); });
   prof_mark(c, "tree");
   {
     double lmin = 1e300, hmin = 1e300;
@@ -505,6 +533,11 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     LPB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     LPB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     LPB_CUDA(cudaEventCreateWithFlags(&c->ev_free, cudaEventDisableTiming));
+    LPB_CUDA(cudaEventCreateWithFlags(&c->ev_gfork, cudaEventDisableTiming));
+    for (int k = 0; k < Ctx::GROUP_STREAMS; ++k) {
+      LPB_CUDA(cudaStreamCreateWithFlags(&c->gs[k], cudaStreamNonBlocking));
+      LPB_CUDA(cudaEventCreateWithFlags(&c->ev_gjoin[k], cudaEventDisableTiming));
+    }
     LPB_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     init_fmm_tables(*c);
   } catch (const CudaError &e) {
@@ -792,6 +825,8 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
+  for (int k = 0; k < Ctx::GROUP_STREAMS; ++k)
+    if (h->gs[k]) cudaStreamSynchronize(h->gs[k]);
   h->arena.release();
   if (h->adj) cudaFree(h->adj);
   if (h->gaunt) cudaFree(h->gaunt);
@@ -805,6 +840,11 @@ void lpbfmm_destroy(lpbfmm_t h) {
     if (h->ev[k]) cudaEventDestroy(h->ev[k]);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_free) cudaEventDestroy(h->ev_free);
+  if (h->ev_gfork) cudaEventDestroy(h->ev_gfork);
+  for (int k = 0; k < Ctx::GROUP_STREAMS; ++k) {
+    if (h->ev_gjoin[k]) cudaEventDestroy(h->ev_gjoin[k]);
+    if (h->gs[k]) cudaStreamDestroy(h->gs[k]);
+  }
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
   delete h;

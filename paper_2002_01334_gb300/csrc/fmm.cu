@@ -1571,6 +1571,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     if (jobs[mid].item0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
   }
   const TJob &J = jobs[lo];
+  // the fields the pipeline reads, in registers: the inline-assembly memory clobbers of the
+  // barrier and copy instructions would otherwise make the compiler reload them from global
+  // memory after every one
+  const float *const Jraw = J.raw, *const Jwimg = J.wimg, *const Jrotcol = J.rotcol;
+  const int32_t *const Jvlist = J.vlist, *const Jcls = J.cls_of;
   const int64_t local = (int64_t)blockIdx.x - J.item0;
   // slice-major: the CTAs resident at one time share a dx-slice, hence the operator classes of
   // its offsets, which then stay in L2 (a level's reaction operators alone exceed it)
@@ -1661,7 +1666,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     const bool ok = tc::mbar_wait(&accbar[i & 1], (uint32_t)((i >> 1) & 1), TC_WAIT);
     if (ok) {
       tc::fence_after();
-      const float4 *rr = (const float4 *)(J.rotcol + (size_t)(steps[i] >> 4) * N + hf * NH);
+      const float4 *rr = (const float4 *)(Jrotcol + (size_t)(steps[i] >> 4) * N + hf * NH);
       const uint32_t col = (uint32_t)((i & 1) * N + hf * NH);
 #pragma unroll
       for (int c1 = 0; c1 < NH; c1 += 32) {
@@ -1702,14 +1707,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
         const int o = steps[s / NC] >> 4, tau = steps[s / NC] & 15, kc = s % NC;
         if (o != cur_o) {
           cur_o = o;
-          my_src = myt >= 0 ? J.vlist[(size_t)myt * NOFF + o] : -1;
+          my_src = myt >= 0 ? Jvlist[(size_t)myt * NOFF + o] : -1;
         }
         unsigned char *st = sbase + (size_t)b * tc_stage_bytes(NC);
         unsigned char *Ah = st, *Bh = st + 2 * SA;
         if (tid == 0) {
           // the class operator's K-chunk (hi and lo tiles, one contiguous image) by one bulk copy
-          const size_t ct = (size_t)J.cls_of[o] * ntypes + tau;
-          const unsigned char *src = (const unsigned char *)(J.wimg + ct * 2 * N * N) + (size_t)kc * 2 * SB;
+          const size_t ct = (size_t)Jcls[o] * ntypes + tau;
+          const unsigned char *src = (const unsigned char *)(Jwimg + ct * 2 * N * N) + (size_t)kc * 2 * SB;
           mbar_expect_tx(&wfull[b], (uint32_t)(2 * SB));
           bulk_g2s(Bh, src, (uint32_t)(2 * SB), &wfull[b]);
           wl_last = s;
@@ -1717,7 +1722,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
         {
           // this thread's source row chunk, unrotated, into the A-hi slots (rotated next iteration)
           const bool v = my_src >= 0;
-          const float *g = J.raw + ((size_t)(v ? my_src : 0) * ntypes + tau) * N + kc * 32;
+          const float *g = Jraw + ((size_t)(v ? my_src : 0) * ntypes + tau) * N + kc * 32;
 #pragma unroll
           for (int u = hf * 4; u < hf * 4 + 4; ++u) cp_async16(Ah + tc::swz16(row, u), g + 4 * u, v);
         }
@@ -1731,7 +1736,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
         // rotate this thread's half row by e^{i mu phi} and split it into TF32 hi (in place) + lo
         unsigned char *st = sbase + (size_t)(sc % NST) * tc_stage_bytes(NC);
         unsigned char *Ah = st, *Al = st + SA;
-        const float4 *rr = (const float4 *)(J.rotcol + (size_t)(steps[si] >> 4) * N + kc * 32);
+        const float4 *rr = (const float4 *)(Jrotcol + (size_t)(steps[si] >> 4) * N + kc * 32);
 #pragma unroll
         for (int uu = 0; uu < 4; ++uu) {
           const int u = hf * 4 + uu;

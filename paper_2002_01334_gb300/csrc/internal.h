@@ -288,6 +288,11 @@ struct Ctx {
   // with the upward pass (the M2L waits for them, ev_join)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_free = nullptr, ev_join = nullptr;
+  // the target groups' trees and lists are independent: built on one stream per group
+  // (group k on gs[k % GROUP_STREAMS]), forked from and joined into the evaluation stream
+  static constexpr int GROUP_STREAMS = 4;
+  cudaStream_t gs[GROUP_STREAMS] = {};
+  cudaEvent_t ev_gfork = nullptr, ev_gjoin[GROUP_STREAMS] = {};
 };
 
 // work of one scope on another stream of the context (restored on exit, also by an exception)

@@ -15,6 +15,7 @@ _lib = None
 
 FP64 = 0
 MIXED = 1
+ERR_OOM = 7
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "invalid medium", 3: "truncation order out of range",
     4: "charge on an interface", 5: "layer_id does not match z", 6: "non-finite input",

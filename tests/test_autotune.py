@@ -52,3 +52,12 @@ def test_search_is_coordinate_descent_over_the_parameters_in_order():
 def test_search_ties_keep_the_first_candidate():
     best, _ = autotune.search((("a", (3, 1, 2)), ("b", (5, 4))), lambda s: 1.0, repeats=1)
     assert best == {"a": 3, "b": 5}
+
+
+def test_search_skips_settings_that_cannot_run():
+    # leaf 32 runs out of memory (None): it is recorded and never chosen
+    cost = {32: None, 64: 4.0, 128: 3.0, 256: 5.0, 512: 6.0}
+    best, rows = autotune.search((("max_per_leaf", (32, 64, 128, 256, 512)),),
+                                 lambda s: cost[s["max_per_leaf"]], repeats=2)
+    assert best == {"max_per_leaf": 128}
+    assert rows[0] == [{"max_per_leaf": 32}, None]
