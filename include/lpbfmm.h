@@ -17,10 +17,11 @@
  *
  * Every entry point returns an lpbfmm status code (0 = success).  Device pointers refer to
  * memory on the context's device; the caller owns all input and output arrays and the
- * library never frees them.  Work is issued on the context's stream; lpbfmm_eval returns
- * after the results are complete on that stream (it synchronizes the stream internally
- * several times to size its work).  A context lives on the device current at lpbfmm_create
- * (ordinal below 64); call its entry points with that device current.  Contexts on several
+ * library never frees them.  Work is issued on the context's stream and on streams the context
+ * owns, forked from it and joined back into it, so the results are complete in the context's
+ * stream order (lpbfmm_eval synchronizes the stream internally several times to size its work,
+ * and returns without waiting for its last kernels).  A context lives on the device current at
+ * lpbfmm_create (ordinal below 64); call its entry points with that device current.  Contexts on several
  * devices may coexist in one process; one context must not be used by two host threads at
  * once.
  */
@@ -271,8 +272,10 @@ void lpbfmm_destroy(lpbfmm_t h);
 
 /*
  * Per-phase device times (ms) of the last lpbfmm_eval, measured with CUDA events on the
- * context's stream, and the number of kernels it launched.  names[i] is a static string.
- * Returns the number of phases written (at most cap).
+ * context's stream, and the number of kernels it launched.  The mixed-precision free-space near
+ * field ("p2p") runs on a stream of its own beside the operators, the upward pass and the M2L,
+ * and is timed there; the operators run on another stream and show only as waits.  names[i] is
+ * a static string.  Returns the number of phases written (at most cap).
  */
 int lpbfmm_last_profile(lpbfmm_t h, int cap, const char **names, float *ms, int *launches);
 

@@ -404,6 +404,18 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
   }
   per_group([&](int, Group &g) { build_group_lists(c, g, g.parts); });
   prof_mark(c, "tree");
+  // the FP32 free-space near field needs only the trees and near lists: on its own stream, beside
+  // the operators, the upward pass and the M2L (the downward pass waits for it).  In a batched
+  // evaluation it is recorded for the batch's grouped launch.
+  c.near_async = !c.def.on && c.opts.precision != LPBFMM_FP64;
+  if (c.near_async) {
+    LPB_CUDA(cudaEventRecord(c.ev_gfork, c.stream));
+    LPB_CUDA(cudaStreamWaitEvent(c.gs[0], c.ev_gfork, 0));
+    run_near_free(c, c.groups, phi, field, c.gs[0]);
+    LPB_CUDA(cudaEventRecord(c.ev_near, c.gs[0]));
+  } else {
+    run_near_free(c, c.groups, phi, field, c.stream);
+  }
   {
     double lmin = 1e300, hmin = 1e300;
     for (int k = 0; k <= L; ++k) lmin = std::min(lmin, c.md.lam[k]);
@@ -429,7 +441,17 @@ static void eval_front(Ctx &c, int64_t n, const double *q, const double *xyz, co
     LPB_CUDA(cudaEventRecord(c.ev_join, c.side));
   }
   prof_mark(c, "tables+ops");
-  run_fmm_front(c, c.groups);
+  c.far_async = c.near_async;
+  if (c.far_async) {
+    // the far field on the high-priority stream, beside the near field
+    LPB_CUDA(cudaEventRecord(c.ev_gfork, c.stream));
+    LPB_CUDA(cudaStreamWaitEvent(c.far, c.ev_gfork, 0));
+    OnStream on(c, c.far);
+    run_fmm_front(c, c.groups);
+    LPB_CUDA(cudaEventRecord(c.ev_far, c.far));
+  } else {
+    run_fmm_front(c, c.groups);
+  }
 }
 // the downward pass and near fields of the evaluation eval_front began
 static void eval_back(Ctx &c, double *phi, double *field) {
@@ -530,10 +552,17 @@ int lpbfmm_create(int n_iface, const double *z_iface, const double *eps, const d
     LPB_CUDA(cudaMemset(c->status, 0, sizeof(int)));
     LPB_CUDA(cudaMallocHost(&c->h_pinned, 1 << 16));
     for (int k = 0; k < 64; ++k) LPB_CUDA(cudaEventCreate(&c->ev[k]));
-    LPB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    int prio_least = 0, prio_greatest = 0;
+    LPB_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    LPB_CUDA(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_greatest));
+    LPB_CUDA(cudaStreamCreateWithPriority(&c->far, cudaStreamNonBlocking, prio_greatest));
+    LPB_CUDA(cudaEventCreateWithFlags(&c->ev_far, cudaEventDisableTiming));
     LPB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     LPB_CUDA(cudaEventCreateWithFlags(&c->ev_free, cudaEventDisableTiming));
     LPB_CUDA(cudaEventCreateWithFlags(&c->ev_gfork, cudaEventDisableTiming));
+    LPB_CUDA(cudaEventCreateWithFlags(&c->ev_near, cudaEventDisableTiming));
+    LPB_CUDA(cudaEventCreate(&c->ev_p2p[0]));
+    LPB_CUDA(cudaEventCreate(&c->ev_p2p[1]));
     for (int k = 0; k < Ctx::GROUP_STREAMS; ++k) {
       LPB_CUDA(cudaStreamCreateWithFlags(&c->gs[k], cudaStreamNonBlocking));
       LPB_CUDA(cudaEventCreateWithFlags(&c->ev_gjoin[k], cudaEventDisableTiming));
@@ -751,11 +780,13 @@ int lpbfmm_eval_batched(int nsys, const lpbfmm_t *ctxs, const int64_t *offsets, 
   std::vector<Ctx *> dcs;
   for (int u : order)
     if (deferred[u]) dcs.push_back(uctx[u]);
-  // 2: the tensor-core M2L and its slot sums of every deferred context, grouped
+  // 2: the tensor-core M2L and its slot sums, then the FP32 free-space near field, of every
+  // deferred context, grouped (the near field first into the outputs, as in lpbfmm_eval)
   if (!err.load() && !dcs.empty()) {
     const int rc = guarded([&] {
       if (!join()) throw CudaError{cudaErrorUnknown, "batched join"};
       launch_deferred(dcs, 0, caller);
+      launch_deferred(dcs, 1, caller);
       if (!fork()) throw CudaError{cudaErrorUnknown, "batched fork"};
     });
     if (rc) fail(rc);
@@ -773,14 +804,6 @@ int lpbfmm_eval_batched(int nsys, const lpbfmm_t *ctxs, const int64_t *offsets, 
       if (rc) fail(rc);
       ctx->stream = own;
     });
-  // 4: the FP32 free-space near field of every deferred context, grouped
-  if (!err.load() && !dcs.empty()) {
-    const int rc = guarded([&] {
-      if (!join()) throw CudaError{cudaErrorUnknown, "batched join"};
-      launch_deferred(dcs, 1, caller);
-    });
-    if (rc) fail(rc);
-  }
   for (Ctx *c : dcs) {
     c->def.on = false;
     c->def.clear();
@@ -825,6 +848,7 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
+  if (h->far) cudaStreamSynchronize(h->far);
   for (int k = 0; k < Ctx::GROUP_STREAMS; ++k)
     if (h->gs[k]) cudaStreamSynchronize(h->gs[k]);
   h->arena.release();
@@ -841,12 +865,17 @@ void lpbfmm_destroy(lpbfmm_t h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_free) cudaEventDestroy(h->ev_free);
   if (h->ev_gfork) cudaEventDestroy(h->ev_gfork);
+  if (h->ev_near) cudaEventDestroy(h->ev_near);
+  for (int k = 0; k < 2; ++k)
+    if (h->ev_p2p[k]) cudaEventDestroy(h->ev_p2p[k]);
   for (int k = 0; k < Ctx::GROUP_STREAMS; ++k) {
     if (h->ev_gjoin[k]) cudaEventDestroy(h->ev_gjoin[k]);
     if (h->gs[k]) cudaStreamDestroy(h->gs[k]);
   }
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->far) cudaStreamDestroy(h->far);
+  if (h->ev_far) cudaEventDestroy(h->ev_far);
   delete h;
 }
 
@@ -865,6 +894,13 @@ int lpbfmm_last_profile(lpbfmm_t h, int cap, const char **names, float *ms, int 
     if (!acc.count(nm)) order.push_back(nm);
     acc[nm] += t;
     lc[nm] += h->prof_launch[k] - h->prof_launch[k - 1];
+  }
+  if (h->p2p_timed) {  // the free-space near field, timed on its own stream
+    float t = 0;
+    cudaEventElapsedTime(&t, h->ev_p2p[0], h->ev_p2p[1]);
+    if (!acc.count("p2p")) order.push_back("p2p");
+    acc["p2p"] += t;
+    lc["p2p"] += 1;
   }
   int w = 0;
   static std::vector<std::string> keep;

@@ -2100,35 +2100,15 @@ static void downward_t(Ctx &c, Group &g, int parts, double *phi, double *field) 
     c.launches++;
   }
   PT_DISPATCH(launch_l2p, c, g.T.lev[D], g.T.lev[D].n, g.T, geo_at<T>(g, D), c.md.lam[g.l], g.Lt[D], phi, field);
-  if (dofree) {
-    // the free-space near field at the free-space leaves (level Df)
+  if (dofree && sizeof(T) == 8) {
+    // the FP64 free-space near field at the free-space leaves (level Df); the FP32 one runs in
+    // run_near_free, beside the far field
     const Level &Lf = g.T.lev[g.Df];
-    const int Df = g.Df;
-    if (sizeof(T) == 4) {
-      const unsigned nb = (unsigned)Lf.n;
-      const int64_t np = g.T.np;
-      float4 *h4 = c.arena.get<float4>((size_t)np), *l4 = c.arena.get<float4>((size_t)np);
-      k_split_points<<<nb, 64, 0, c.stream>>>(Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.T.x, g.T.y, g.T.z, g.T.q,
-                                               geo_at<T>(g, Df), h4, l4);
-      LPB_LAUNCH();
-      c.launches++;
-      // the near field itself joins the evaluation's (or the batch's) one P2P launch
-      const double hD = g.h(Df);
-      P2PJob j;
-      j.d_nb = Lf.d_n; j.bkey = Lf.key; j.bstart = Lf.pstart; j.bcount = Lf.pcount; j.ulist = g.ufree;
-      j.h4 = h4; j.l4 = l4; j.src = g.T.src; j.phi = phi; j.field = field;
-      j.scale = 1.0 / (4.0 * PI * c.md.eps[g.l]);
-      j.hh = (float)hD; j.hl = (float)(hD - (double)j.hh); j.lam = (float)c.md.lam[g.l];
-      j.block0 = c.def.p2p_blocks;
-      c.def.p2p.push_back(j);
-      c.def.p2p_blocks += (2 * (int64_t)nb + P2P_WARPS - 1) / P2P_WARPS;
-    } else {
-      k_p2p_free<T><<<(unsigned)Lf.n, P2P_TPB, 0, c.stream>>>(
-          Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q, g.T.src, geo_at<T>(g, Df),
-          c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
-      LPB_LAUNCH();
-      c.launches++;
-    }
+    k_p2p_free<T><<<(unsigned)Lf.n, P2P_TPB, 0, c.stream>>>(
+        Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.ufree, g.T.x, g.T.y, g.T.z, g.T.q, g.T.src, geo_at<T>(g, g.Df),
+        c.md.lam[g.l], 1.0 / (4.0 * PI * c.md.eps[g.l]), phi, field);
+    LPB_LAUNCH();
+    c.launches++;
   }
   if (react_near && g.ureact && g.nodes) {
     k_p2p_react<T><<<(unsigned)g.T.lev[D].n, P2P_THREADS, 0, c.stream>>>(
@@ -2151,7 +2131,10 @@ static void launch_p2p(Ctx &c, const std::vector<P2PJob> &jobs, int64_t blocks, 
 }
 
 void run_fmm_front(Ctx &c, std::vector<Group> &groups) {
-  c.def.clear();
+  c.def.nc = 0;
+  c.def.tc.clear();
+  c.def.red.clear();
+  c.def.tc_items = c.def.red_elems = 0;
   const bool d = c.opts.precision == LPBFMM_FP64;
   // the free-space operators (side stream) are complete before the upward pass
   if (c.ev_free) LPB_CUDA(cudaStreamWaitEvent(c.stream, c.ev_free, 0));
@@ -2163,19 +2146,52 @@ void run_fmm_front(Ctx &c, std::vector<Group> &groups) {
   prof_mark(c, "m2l");
 }
 
-void run_fmm_back(Ctx &c, std::vector<Group> &groups, double *phi, double *field) {
-  const bool d = c.opts.precision == LPBFMM_FP64;
+void run_near_free(Ctx &c, std::vector<Group> &groups, double *phi, double *field, cudaStream_t st) {
   c.def.p2p.clear();
   c.def.p2p_blocks = 0;
+  c.p2p_timed = false;
+  if (c.opts.precision == LPBFMM_FP64) return;
+  OnStream on(c, st);
+  for (auto &g : groups) {
+    if (!(g.is_free && (g.parts & 1))) continue;
+    const Level &Lf = g.T.lev[g.Df];
+    const unsigned nb = (unsigned)Lf.n;
+    if (!nb) continue;
+    const int64_t np = g.T.np;
+    float4 *h4 = c.arena.get<float4>((size_t)np), *l4 = c.arena.get<float4>((size_t)np);
+    k_split_points<<<nb, 64, 0, c.stream>>>(Lf.d_n, Lf.key, Lf.pstart, Lf.pcount, g.T.x, g.T.y, g.T.z, g.T.q,
+                                             geo_at<float>(g, g.Df), h4, l4);
+    LPB_LAUNCH();
+    c.launches++;
+    const double hD = g.h(g.Df);
+    P2PJob j;
+    j.d_nb = Lf.d_n; j.bkey = Lf.key; j.bstart = Lf.pstart; j.bcount = Lf.pcount; j.ulist = g.ufree;
+    j.h4 = h4; j.l4 = l4; j.src = g.T.src; j.phi = phi; j.field = field;
+    j.scale = 1.0 / (4.0 * PI * c.md.eps[g.l]);
+    j.hh = (float)hD; j.hl = (float)(hD - (double)j.hh); j.lam = (float)c.md.lam[g.l];
+    j.block0 = c.def.p2p_blocks;
+    c.def.p2p.push_back(j);
+    c.def.p2p_blocks += (2 * (int64_t)nb + P2P_WARPS - 1) / P2P_WARPS;
+  }
+  if (!c.def.on && !c.def.p2p.empty()) {
+    LPB_CUDA(cudaEventRecord(c.ev_p2p[0], c.stream));
+    launch_p2p(c, c.def.p2p, c.def.p2p_blocks, c.stream);
+    LPB_CUDA(cudaEventRecord(c.ev_p2p[1], c.stream));
+    c.p2p_timed = true;
+    c.def.p2p.clear();
+    c.def.p2p_blocks = 0;
+  }
+}
+
+void run_fmm_back(Ctx &c, std::vector<Group> &groups, double *phi, double *field) {
+  const bool d = c.opts.precision == LPBFMM_FP64;
+  // the far field (its own stream) and the free-space near field, which adds into the same
+  // outputs, are complete first
+  if (c.far_async) LPB_CUDA(cudaStreamWaitEvent(c.stream, c.ev_far, 0));
+  if (c.near_async) LPB_CUDA(cudaStreamWaitEvent(c.stream, c.ev_near, 0));
   for (auto &g : groups)
     d ? downward_t<double>(c, g, g.parts, phi, field) : downward_t<float>(c, g, g.parts, phi, field);
   prof_mark(c, "downward");
-  if (!c.def.on) {
-    launch_p2p(c, c.def.p2p, c.def.p2p_blocks, c.stream);
-    c.def.p2p.clear();
-    c.def.p2p_blocks = 0;
-    prof_mark(c, "p2p");
-  }
 }
 
 void launch_deferred(const std::vector<Ctx *> &cs, int stage, cudaStream_t st) {

@@ -293,6 +293,15 @@ struct Ctx {
   static constexpr int GROUP_STREAMS = 4;
   cudaStream_t gs[GROUP_STREAMS] = {};
   cudaEvent_t ev_gfork = nullptr, ev_gjoin[GROUP_STREAMS] = {};
+  // the FP32 free-space near field runs on gs[0] beside the upward pass and the M2L; the downward
+  // pass (which also adds into the outputs) waits for ev_near.  ev_p2p[2] time its launch.
+  cudaEvent_t ev_near = nullptr, ev_p2p[2] = {};
+  bool near_async = false, p2p_timed = false;
+  // beside it, the upward pass and the M2L run on a high-priority stream (far), so that their
+  // blocks are scheduled ahead of the near field's; the downward pass waits for ev_far
+  cudaStream_t far = nullptr;
+  cudaEvent_t ev_far = nullptr;
+  bool far_async = false;
 };
 
 // work of one scope on another stream of the context (restored on exit, also by an exception)
@@ -337,7 +346,10 @@ void debug_stable(Ctx &c, int l, int a, int lp, int b, double h, double rho, dou
 // upward pass and M2L of every group (with c.def.on the tensor-core M2L and its slot sums are
 // recorded in c.def instead of launched)
 void run_fmm_front(Ctx &c, std::vector<Group> &groups);
-// downward pass and near fields (with c.def.on the FP32 free-space near field is recorded)
+// the FP32 free-space near field of every group (mixed precision): point splitting and one P2P
+// launch on stream st, or, with c.def.on, the launch recorded in c.def for a grouped one
+void run_near_free(Ctx &c, std::vector<Group> &groups, double *phi, double *field, cudaStream_t st);
+// downward pass and the remaining near fields
 void run_fmm_back(Ctx &c, std::vector<Group> &groups, double *phi, double *field);
 // the recorded jobs of several contexts (all on the current device) as grouped launches on st:
 // stage 0 the tensor-core M2L and the slot sums, stage 1 the free-space near field.  Timeouts of
