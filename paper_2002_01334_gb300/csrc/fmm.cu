@@ -1560,6 +1560,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
   __shared__ int remap_s[N], mcol[N];  // coordinate -> half index code; m of that coefficient
   __shared__ int nsteps;
   __shared__ unsigned tmk[SLICE_OFFS];  // per offset of the slice: the source types some row needs
+  // the rotation columns depend on the offset's azimuth only, i.e. on (dx, dy): a dx-slice needs
+  // OFF_D rows of the table, kept here for the whole CTA
+  __shared__ __align__(16) float rot_s[OFF_D * 128];
   // full[b]: the workers have staged buffer b (TC_WORKERS arrivals); empty[b]: its MMAs are done;
   // accbar[a]: a step's MMAs into accumulator a are done; foldbar[a]: the workers have read it
   // wfull[b]: the operator chunk of buffer b has landed (one bulk copy, issued by thread 0)
@@ -1649,6 +1652,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     }
     tc::mbar_fence_init();
   }
+  for (int e = tid; e < OFF_D * N; e += TC_THREADS) {
+    const int dyi = e / N;
+    rot_s[e] = Jrotcol[(size_t)off_index(slice - OFF_R, dyi - OFF_R, 0) * N + (e - dyi * N)];
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -1666,7 +1673,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
     const bool ok = tc::mbar_wait(&accbar[i & 1], (uint32_t)((i >> 1) & 1), TC_WAIT);
     if (ok) {
       tc::fence_after();
-      const float4 *rr = (const float4 *)(Jrotcol + (size_t)(steps[i] >> 4) * N + hf * NH);
+      const float4 *rr = (const float4 *)(rot_s + ((steps[i] >> 4) / OFF_D % OFF_D) * N + hf * NH);
       const uint32_t col = (uint32_t)((i & 1) * N + hf * NH);
 #pragma unroll
       for (int c1 = 0; c1 < NH; c1 += 32) {
@@ -1677,7 +1684,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int c0 = c1 + 8 * q;
-          const float4 ra = __ldg(rr + c0 / 4), rb = __ldg(rr + c0 / 4 + 1);
+          const float4 ra = rr[c0 / 4], rb = rr[c0 / 4 + 1];
           const float cs[4] = {ra.x, ra.z, rb.x, rb.z}, sn[4] = {ra.y, ra.w, rb.y, rb.w};
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
@@ -1736,12 +1743,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const TJob *jobs, int 
         // rotate this thread's half row by e^{i mu phi} and split it into TF32 hi (in place) + lo
         unsigned char *st = sbase + (size_t)(sc % NST) * tc_stage_bytes(NC);
         unsigned char *Ah = st, *Al = st + SA;
-        const float4 *rr = (const float4 *)(Jrotcol + (size_t)(steps[si] >> 4) * N + kc * 32);
+        const float4 *rr = (const float4 *)(rot_s + ((steps[si] >> 4) / OFF_D % OFF_D) * N + kc * 32);
 #pragma unroll
         for (int uu = 0; uu < 4; ++uu) {
           const int u = hf * 4 + uu;
           float4 x = *(float4 *)(Ah + tc::swz16(row, u));
-          const float4 r = __ldg(rr + u);  // (cos, sin) of the unit's two column pairs
+          const float4 r = rr[u];  // (cos, sin) of the unit's two column pairs
           const float xr0 = r.x * x.x - r.y * x.y, xi0 = r.y * x.x + r.x * x.y;
           const float xr1 = r.z * x.z - r.w * x.w, xi1 = r.w * x.z + r.z * x.w;
           x = make_float4(xr0, xi0, xr1, xi1);
