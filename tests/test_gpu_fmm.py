@@ -379,16 +379,21 @@ def test_four_layer_medium_all_layers(w3000):
     md = oracle.Medium(**w["medium"])
     ref = oracle.direct(md, w["q"], w["xyz"], w["layer"])
     _, phi, fld = run(w, 10, depth=4)
-    assert rel(phi, ref[0]) < 1e-5 and rel(fld, ref[1]) < 5e-5
+    assert rel(phi, ref[0]) < 1e-6 and rel(fld, ref[1]) < 1e-6, (rel(phi, ref[0]), rel(fld, ref[1]))
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 37, 129])
 def test_ragged_and_tiny_inputs(n):
+    """Tiny and ragged systems at a forced depth 3 against the oracle: the 1e-6 gate from three
+    charges on.  With one or two charges the error is that of a handful of single translations
+    (a charge's own image through the M2L), not an average over many pairs: measured up to
+    7.6e-7 (potential) and 2.2e-5 (field, whose value is small there), bounded at 5e-5."""
     w = inputs.workload("three_layer", n=n, seed=100 + n)
     md = oracle.Medium(**w["medium"])
     ref = oracle.direct(md, w["q"], w["xyz"], w["layer"])
     _, phi, fld = run(w, 10, depth=3)
-    assert rel(phi, ref[0]) < 1e-5 and rel(fld, ref[1]) < 5e-5
+    tol = 1e-6 if n >= 3 else 5e-5
+    assert rel(phi, ref[0]) < tol and rel(fld, ref[1]) < tol, (rel(phi, ref[0]), rel(fld, ref[1]))
 
 
 def test_empty_input_is_noop():
@@ -434,7 +439,7 @@ def test_adjoint_forces_and_dEdq_match_oracle_and_finite_differences():
     ref_phi, ref_fld = oracle.direct(md, w["q"], w["xyz"], w["layer"])
     assert rel(gq.cpu().numpy(), ref_phi) < 1e-6
     force = -gx.cpu().numpy()
-    assert rel(force, w["q"][:, None] * ref_fld) < 3e-6
+    assert rel(force, w["q"][:, None] * ref_fld) < 1e-6
 
     def energy(xx):
         phi, _ = ctx.eval(q, torch.tensor(xx, device=DEV), l, field=False)
@@ -549,7 +554,7 @@ def test_batched_matches_individual():
         sel = np.arange(0, len(s["q"]), 37)
         ref = oracle.direct(md, s["q"], s["xyz"], s["layer"], targets=sel)
         got = phi[offs[k]:offs[k + 1]].cpu().numpy()[sel]
-        assert rel(got, ref[0]) < 2e-5
+        assert rel(got, ref[0]) < 1e-6, (k, rel(got, ref[0]))
 
 
 def test_batched_grouped_launches_match_individual_evaluations():
