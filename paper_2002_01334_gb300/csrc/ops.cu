@@ -207,19 +207,22 @@ __global__ void k_stab_bessel(NDesc N, double *bes) {
   __shared__ int npan;
   if (threadIdx.x == 0) make_panels(N.umax, N.wmax, N.lmin, pu, pw, &npan);
   __syncthreads();
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N.nq; j += gridDim.x * blockDim.x) {
+  // one thread per (node, rho value): the node set is short, so a thread per node alone would
+  // leave most of the GPU idle
+  const int64_t total = (int64_t)N.nq * NRHO;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / NRHO), r = (int)(e % NRHO);
     double *o = bes + (size_t)j * 2 * NRHO;
     if (j >= npan * 16) {
-      for (int k = 0; k < 2 * NRHO; ++k) o[k] = 0.0;
+      o[r] = 0.0;
+      o[NRHO + r] = 0.0;
       continue;
     }
     const int pi_ = j >> 4, gi = 15 - (j & 15);  // ascending abscissae
     const double u = pu[pi_] + 0.5 * pw[pi_] * (c_glx[gi] + 1.0);
-    for (int r = 0; r < NRHO; ++r) {
-      const double x = u * sqrt((double)rho2_of(r));
-      o[r] = j0(x);
-      o[NRHO + r] = j1(x);
-    }
+    const double x = u * sqrt((double)rho2_of(r));
+    o[r] = j0(x);
+    o[NRHO + r] = j1(x);
   }
 }
 
@@ -737,7 +740,7 @@ static void build_ops_t(Ctx &c, Group &g, int parts, int which) {
     if (!c.stab_bes) {
       const NDesc N0 = node_desc(KT, tol, c.stab_lmin, c.stab_lmin);
       c.stab_bes = c.arena.get<double>((size_t)N0.nq * 2 * NRHO);
-      k_stab_bessel<<<(unsigned)((N0.nq + 255) / 256), 256, 0, c.stream>>>(N0, c.stab_bes);
+      k_stab_bessel<<<(unsigned)(((int64_t)N0.nq * NRHO + 255) / 256), 256, 0, c.stream>>>(N0, c.stab_bes);
       LPB_LAUNCH();
       c.launches++;
     }
