@@ -163,11 +163,14 @@ def workload_config(n, p, precision, workload="three_layer"):
                 "charges": "q~U[-1,1], uniform in the bodies r(theta) = 0.5 - a + (a/8)(35 cos^4 - 30 cos^2 + 3), "
                            "a = 0.1, 0.15, 0.05, centres z = 0.6, -0.6, -1.8, counts in the ratio 912:640:1296",
                 "precision": precision, "l2": "flushed between steps (256 MB write)",
-                "tree": "automatic depth, <=128 mean targets per leaf", "separation": "two-box interaction lists"}
+                "tree": "automatic depth by mean leaf occupancy (library default 128; the autotune object gives "
+                        "the setting timed)", "separation": "two-box interaction lists"}
     return {"workload": "three-layer screened Coulomb, N=%d, p=%d" % (n, p), "n": n, "p": p, "layers": 3,
             "interfaces": [0.0, -1.2], "eps": [1.0, 2.0, 5.0], "lambda": [0.5, 1.0, 0.8],
             "charges": "q~U[-1,1], uniform in three unit cubes (one per layer)", "precision": precision,
-            "l2": "flushed between steps (256 MB write)", "tree": "automatic depth, <=128 mean targets per leaf",
+            "l2": "flushed between steps (256 MB write)",
+            "tree": "automatic depth by mean leaf occupancy (library default 128; the autotune object gives the "
+                    "setting timed)",
             "separation": "two-box interaction lists"}
 
 
@@ -306,7 +309,6 @@ def run_ours(args, rank, world, local_rank):
         tuned = {"method": "coordinate descent over %s in order; median of 2 CUDA-event timings of one evaluation "
                            "per setting" % ", ".join(nm for nm, _ in autotune.SPACE),
                  "ms_by_setting": rows, "chosen": settings}
-    leaf = settings["max_per_leaf"]
     ctx = F.Context(m["d"], m["eps"], m["lam"], args.p, precision=F.MIXED, stream=stream, **settings)
     n = args.n
     phi = torch.empty(n, dtype=torch.float64, device=dev)
@@ -469,10 +471,7 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": metric_of(args.workload), "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": dict(workload_config(n, args.p, "mixed", args.workload),
-                               **({"tree": "automatic depth, <=%d mean targets per leaf, reaction trees up to %d "
-                                           "levels deeper (autotuned)" % (leaf, settings["react_levels"])}
-                                  if tuned else {})),
+                "config": workload_config(n, args.p, "mixed", args.workload),
                 "clocks": clk.summary(), "autotune": tuned,
                 "e2e": {"value": e2e_val, "unit": "targets/s", "h2d_bytes_per_step": n * (8 + 24 + 4),
                         "d2h_bytes_per_step": n * (8 + 24)},
