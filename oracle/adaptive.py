@@ -17,7 +17,9 @@ refined: both boxes when both have children, else the one that has.  Far pairs a
     V  same level                 (multipole-to-local),
     W  B a leaf, C finer than B   (multipole at B's targets; direct in a first version),
     X  C a leaf, B finer than C   (C's sources into B's local expansion; direct at first),
-and an adjacent pair of two leaves is U (direct).  Every (target, source) pair of points then lies
+and an adjacent pair of two leaves is U (direct).  With a separation of ws boxes, "adjacent"
+is "near": the coarser box grown by ws - 1 of its sides meets the finer one (ws = 1: the closed
+cubes meet; at one level, indices within ws).  Every (target, source) pair of points then lies
 in exactly one listed box pair: the traversal partitions B x C at every refinement.  For a tree of
 uniform depth the lists are the uniform ones: V at every level is the same-level boxes whose
 parents are adjacent but which are not, and U at the leaf level the adjacent leaves.
@@ -39,15 +41,21 @@ def _decode(key):
     return x, y, z
 
 
-def adjacent(la, ka, lb, kb):
-    """Whether the closed cubes of box (la, ka) and box (lb, kb) intersect (levels may differ)."""
+def adjacent(la, ka, lb, kb, ws=1):
+    """Whether box (la, ka) and box (lb, kb) are near for a separation of ws boxes (levels may
+    differ): the closed cube of the coarser box, grown by ws - 1 of its own sides in every
+    direction, intersects the closed cube of the finer one.  ws = 1: the closed cubes intersect;
+    for two boxes of one level: their indices differ by at most ws in every coordinate (the near
+    rule of the uniform lists, Sec. 3.5 reading R22)."""
     ax, ay, az = _decode(ka)
     bx, by, bz = _decode(kb)
     L = max(la, lb)
     sa, sb = 1 << (L - la), 1 << (L - lb)
+    ga = (ws - 1) * sa if la <= lb else 0  # the growth of the coarser cube, in units of level L
+    gb = (ws - 1) * sb if lb < la else 0
     for u, v in ((ax, bx), (ay, by), (az, bz)):
-        # [u sa, (u + 1) sa] and [v sb, (v + 1) sb] in units of the finer level
-        if (u + 1) * sa < v * sb or (v + 1) * sb < u * sa:
+        # [u sa - ga, (u + 1) sa + ga] and [v sb - gb, (v + 1) sb + gb] in units of level L
+        if (u + 1) * sa + ga < v * sb - gb or (v + 1) * sb + gb < u * sa - ga:
             return False
     return True
 
@@ -94,16 +102,17 @@ class Tree:
         return (lev, key) in self.leaves
 
 
-def dual_lists(T, S):
-    """The lists of the dual traversal of target tree T and source tree S: a dict with keys
-    'V', 'U', 'W', 'X', each a sorted list of ((lt, kt), (ls, ks)) box pairs."""
+def dual_lists(T, S, ws=1):
+    """The lists of the dual traversal of target tree T and source tree S for a separation of ws
+    boxes (adjacent(..., ws) decides near): a dict with keys 'V', 'U', 'W', 'X', each a sorted
+    list of ((lt, kt), (ls, ks)) box pairs."""
     out = {"V": [], "U": [], "W": [], "X": []}
     if not T.boxes or not S.boxes:
         return out
     stack = [((0, 0), (0, 0))]
     while stack:
         (lt, kt), (ls, ks) = stack.pop()
-        if not adjacent(lt, kt, ls, ks):
+        if not adjacent(lt, kt, ls, ks, ws):
             kind = "V" if lt == ls else ("W" if ls > lt else "X")
             out[kind].append(((lt, kt), (ls, ks)))
             continue

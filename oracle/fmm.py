@@ -401,10 +401,11 @@ def fmm(md, q, xyz, layer, p, D, ws=1):
     return a + b, fa + fb
 
 
-def free_fmm_adaptive(md, q, xyz, layer, p, s):
+def free_fmm_adaptive(md, q, xyz, layer, p, s, ws=1):
     """Free-space part of phi and field on adaptive trees: each layer's tree (the group root of the
     uniform case, keys at depth 21) split while a box holds more than s charges
-    (oracle/adaptive.py).  Lists from the dual traversal of the tree with itself: V pairs by M2L
+    (oracle/adaptive.py).  Lists from the dual traversal of the tree with itself for a separation of
+    ws boxes: V pairs by M2L
     (Thm. 3), U, W and X pairs summed directly (closed form, j != i).  Expansions exist for the
     boxes of level >= 2: P2M at leaves, M2M to parents, L2L to children, L2P at target leaves.
     Returns (phi[n], field[n, 3])."""
@@ -425,7 +426,7 @@ def free_fmm_adaptive(md, q, xyz, layer, p, s):
         root = tree_root(md, xyz, layer, l, a)
         keys, src, _ = tree_keys(md, xyz, layer, l, a, A.DMAX, root, 0)
         T = A.Tree(keys, s)
-        lists_ = A.dual_lists(T, T)
+        lists_ = A.dual_lists(T, T, ws)
         H = root[3]
         x0 = np.array([root[0] - H, root[1] - H, root[2] - H])
 
@@ -487,10 +488,10 @@ def free_fmm_adaptive(md, q, xyz, layer, p, s):
     return phi, field
 
 
-def react_fmm_adaptive(md, q, xyz, layer, p, s):
+def react_fmm_adaptive(md, q, xyz, layer, p, s, ws=1):
     """Reaction part of phi and field on adaptive dual trees (oracle/adaptive.py): per target
     group (l, a) the target tree of its charges and the source tree of its images, each split
-    while a box holds more than s of its points.  V pairs by M2L (T of eqs. metoleimage1-2, one
+    while a box holds more than s of its points, lists for a separation of ws boxes.  V pairs by M2L (T of eqs. metoleimage1-2, one
     ME per source type), U, W and X pairs by the component integral directly; expansions for the
     boxes of level >= 2 (P2M at image leaves, M2M with lam_l', L2L and L2P with lam_l).
     Returns (phi[n], field[n, 3])."""
@@ -525,7 +526,7 @@ def react_fmm_adaptive(md, q, xyz, layer, p, s):
                 lp, b = divmod(int(ityp[j]), 2)
                 ipos[j, 2] = image_z(md, l, a, lp, b + 1, xyz[isrc[j], 2])
             types = sorted(set(int(t) for t in ityp))
-            Ls = A.dual_lists(T, S)
+            Ls = A.dual_lists(T, S, ws)
             # upward pass on the image tree, one expansion per source type
             M = {}
             for lev in sorted(S.boxes, reverse=True):
@@ -556,7 +557,9 @@ def react_fmm_adaptive(md, q, xyz, layer, p, s):
                     if not np.any(M[bs][ti]):
                         continue
                     if (lev, t) not in ops:
-                        ops[(lev, t)] = ReactionM2L(md, l, t // 2, a, t % 2 + 1, p, h, math.sqrt(18.0) * h)
+                        # V pairs lie within (2 ws + 1) boxes in x and y: rho <= (2 ws + 1) sqrt(2) h
+                        ops[(lev, t)] = ReactionM2L(md, l, t // 2, a, t % 2 + 1, p, h,
+                                                   (2 * ws + 1) * math.sqrt(2.0) * h)
                     L[bt] = L.get(bt, np.zeros(K, complex)) + ops[(lev, t)].apply(centre(*bt), centre(*bs), M[bs][ti])
             for lev in sorted(T.boxes):
                 if lev < 2:

@@ -89,3 +89,54 @@ def test_uniform_tree_lists_equal_the_uniform_oracle_lists(D):
             ref = {(int(tb[t]), int(sb[j])) for t in range(len(tb)) for j in idx[off[t]:off[t + 1]]}
             got = {(bt[1], bs[1]) for (bt, bs) in L[name] if bt[0] == lev}
             assert got == ref, (lev, name)
+
+
+@pytest.mark.parametrize("n,s,seed", [(300, 4, 1), (900, 16, 2)])
+@pytest.mark.parametrize("swap", [False, True])
+def test_two_box_lists_cover_every_pair_exactly_once(n, s, seed, swap):
+    """With a separation of two boxes (the GPU's default, reading R22) the dual traversal still
+    partitions every (target, source) pair: each lies in exactly one U, V, W or X box pair."""
+    w, md, root = _group(n, seed)
+    T, S, (tsrc, ssrc, _) = A.group_trees(md, w["xyz"], w["layer"], 1, 1, root, s)
+    if swap:
+        T, S, tsrc, ssrc = S, T, ssrc, tsrc
+    L = A.dual_lists(T, S, ws=2)
+    cnt = _coverage(T, S, L, len(tsrc), len(ssrc))
+    assert cnt.min() == 1 and cnt.max() == 1
+    assert all(len(L[k]) > 0 for k in ("U", "V", "X" if swap else "W"))
+
+
+def test_two_box_near_rule():
+    """adjacent(..., ws): at one level, indices within ws in every coordinate; across levels, the
+    coarser cube grown by ws - 1 of its sides meets the finer one; ws = 1 is closed-cube contact."""
+    key = lambda x, y, z: sum(((x >> k) & 1) << (3 * k + 2) | ((y >> k) & 1) << (3 * k + 1) | ((z >> k) & 1) << (3 * k)
+                             for k in range(A.DMAX))
+    for d in range(-4, 5):
+        for ws in (1, 2):
+            assert A.adjacent(4, key(8, 8, 8), 4, key(8 + d, 8, 8), ws) == (abs(d) <= ws)
+            assert A.adjacent(4, key(8, 8, 8), 4, key(8 + d, 8 - d, 8 + d), ws) == (abs(d) <= ws)
+    # level-3 box [4, 5) and level-5 boxes (units of 1/4 of it): grown by one side it spans [12, 24)
+    for v in range(8, 28):
+        near = 12 - 1 <= v <= 24  # closed cubes: the fine box [v, v + 1] meets [12, 24]
+        assert A.adjacent(3, key(4, 4, 4), 5, key(v, 16, 16), 2) == near, v
+        assert A.adjacent(5, key(v, 16, 16), 3, key(4, 4, 4), 2) == near, v
+        assert A.adjacent(3, key(4, 4, 4), 5, key(v, 16, 16), 1) == (15 <= v <= 20), v
+
+
+@pytest.mark.parametrize("D", [3, 4])
+def test_uniform_tree_two_box_lists_equal_the_uniform_oracle_lists(D):
+    w, md, root = _group(2000, 6)
+    T, S, _ = A.group_trees(md, w["xyz"], w["layer"], 1, 1, root, 0, uniform=D)
+    L = A.dual_lists(T, S, ws=2)
+    assert not L["W"] and not L["X"]
+    tk, _, _ = oracle.tree_keys(md, w["xyz"], w["layer"], 1, 1, D, root, 0)
+    sk, _, _ = oracle.tree_keys(md, w["xyz"], w["layer"], 1, 1, D, root, 1)
+    for lev in range(2, D + 1):
+        tb, sb = oracle.level_boxes(tk, D, lev), oracle.level_boxes(sk, D, lev)
+        for kind, name in ((0, "V"), (1, "U")):
+            if kind == 1 and lev != D:
+                continue
+            off, idx = oracle.lists(tb, sb, lev, kind, ws=2)
+            ref = {(int(tb[t]), int(sb[j])) for t in range(len(tb)) for j in idx[off[t]:off[t + 1]]}
+            got = {(bt[1], bs[1]) for (bt, bs) in L[name] if bt[0] == lev}
+            assert got == ref, (lev, name)
