@@ -401,11 +401,35 @@ def fmm(md, q, xyz, layer, p, D, ws=1):
     return a + b, fa + fb
 
 
-def free_fmm_adaptive(md, q, xyz, layer, p, s, ws=1):
+def _m2p(lam, M, c, pts, p):
+    """Value and gradient at each point of the ME M (degree p) about c: the ME translated (Thm. 3)
+    into a degree-1 LE about the point itself, whose n <= 1 coefficients give both exactly."""
+    val = np.zeros(len(pts))
+    grad = np.zeros((len(pts), 3))
+    for i, r in enumerate(pts):
+        Lr = E.free_m2l(lam, M, c, r, p, 1)
+        v, g = _le_at_points(lam, Lr, r, r[None, :], 1)
+        val[i], grad[i] = v[0], g[0]
+    return val, grad
+
+
+def _p2l(lam, pts, q, c, p):
+    """LE about c (degree p) of the point sources (eq. melecoeffree, conjugate reading):
+    sum_j q_j 4 pi k_n(lam |r_j - c|) conj Y_n^m of r_j - c."""
+    R, T, P = E.sph(pts - c)
+    rows = np.array([special.spherical_kn(n, lam * R) for n, _ in E._nm(p)])
+    return 4 * math.pi * (rows * np.conj(E.ylm_all(p, T, P))) @ q
+
+
+def free_fmm_adaptive(md, q, xyz, layer, p, s, ws=1, wx="direct"):
     """Free-space part of phi and field on adaptive trees: each layer's tree (the group root of the
     uniform case, keys at depth 21) split while a box holds more than s charges
     (oracle/adaptive.py).  Lists from the dual traversal of the tree with itself for a separation of
-    ws boxes: V pairs by M2L
+    ws boxes.  wx = "direct": W and X pairs summed directly; wx = "expansion": a W pair (target
+    leaf B, finer source box C) by C's multipole expansion evaluated at B's targets (M2P), an X
+    pair (target box B, coarser source leaf C) by C's charges expanded about B's centre and added
+    to B's local expansion before it is shifted down (P2L); boxes above level 2 keep the direct
+    sum.  V pairs by M2L
     (Thm. 3), U, W and X pairs summed directly (closed form, j != i).  Expansions exist for the
     boxes of level >= 2: P2M at leaves, M2M to parents, L2L to children, L2P at target leaves.
     Returns (phi[n], field[n, 3])."""
@@ -459,6 +483,25 @@ def free_fmm_adaptive(md, q, xyz, layer, p, s, ws=1):
             if kb not in ops:
                 ops[kb] = E.free_s(lam, b, p, p).T
             L[bt] = L.get(bt, np.zeros(K, complex)) + ops[kb] @ M[bs]
+        # the pairs summed directly: U, and W / X unless expanded
+        direct = list(lists_["U"])
+        if wx == "expansion":
+            for (bt, bs) in lists_["X"]:
+                if bt[0] < 2:
+                    direct.append((bt, bs))
+                    continue
+                sm = pts(*bs)
+                L[bt] = L.get(bt, np.zeros(K, complex)) + _p2l(lam, xyz[sm], q[sm], centre(*bt), p)
+            for (bt, bs) in lists_["W"]:
+                if bs not in M:
+                    direct.append((bt, bs))
+                    continue
+                tm = pts(*bt)
+                v, g = _m2p(lam, M[bs], centre(*bs), xyz[tm], p)
+                phi[tm] += cfac * v
+                field[tm] -= cfac * g
+        else:
+            direct += lists_["W"] + lists_["X"]
         for lev in levels:
             if lev < 2:
                 continue
@@ -475,16 +518,15 @@ def free_fmm_adaptive(md, q, xyz, layer, p, s, ws=1):
                 v, g = _le_at_points(lam, L[(lev, key)], centre(lev, key), xyz[mem], p)
                 phi[mem] += cfac * v
                 field[mem] -= cfac * g
-        for kind in ("U", "W", "X"):
-            for (bt, bs) in lists_[kind]:
-                tm, sm = pts(*bt), pts(*bs)
-                for i in tm:
-                    js = sm[sm != i]
-                    d = xyz[i] - xyz[js]
-                    r = np.sqrt((d * d).sum(1))
-                    e = q[js] * np.exp(-lam * r) / (4 * math.pi * eps * r)
-                    phi[i] += e.sum()
-                    field[i] += ((e * (1 + lam * r) / (r * r))[:, None] * d).sum(0)
+        for (bt, bs) in direct:
+            tm, sm = pts(*bt), pts(*bs)
+            for i in tm:
+                js = sm[sm != i]
+                d = xyz[i] - xyz[js]
+                r = np.sqrt((d * d).sum(1))
+                e = q[js] * np.exp(-lam * r) / (4 * math.pi * eps * r)
+                phi[i] += e.sum()
+                field[i] += ((e * (1 + lam * r) / (r * r))[:, None] * d).sum(0)
     return phi, field
 
 
