@@ -194,6 +194,22 @@ int lpbfmm_debug_tree(lpbfmm_t h, int l, int a, double *root, int64_t *n_targets
                       int32_t *type_i);
 
 /*
+ * Diagnostics: after an lpbfmm_eval, the interaction lists of the adaptive dual tree of target
+ * group (l, a)'s free-space tree with itself (Sec. 3.5 builds the method on the adaptive FMM
+ * framework; built on the device by a level-synchronous traversal over frontiers of box pairs;
+ * the evaluation itself uses uniform trees).  A box of level l >= 3 exists when its parent exists
+ * and holds more than s targets (every box of level 2 exists); it is a leaf when it holds at most
+ * s or sits at the group's free-space depth.  Two boxes are near for separation ws (1 or 2) when
+ * the coarser one, grown by ws - 1 of its sides, meets the finer one.  Records of 5 int64 (host):
+ * kind (0 = V: far, same level; 1 = U: near leaves; 2 = W: target leaf, finer far source box;
+ * 3 = X: source leaf, finer far target box), target level, target box's Morton key at that level,
+ * source level, source key; in no particular order.  *nrec receives their number; at most cap
+ * are copied to rec (rec may be NULL).  The group must carry the free-space part.
+ */
+int lpbfmm_debug_adaptive_lists(lpbfmm_t h, int l, int a, int s, int ws, int64_t *nrec, int64_t *rec,
+                                int64_t cap);
+
+/*
  * Diagnostics: after an lpbfmm_eval, the interaction lists of group (l, a) at level lev:
  * kind 0 = far (multipole-to-local) list, kind 1 = near list at the leaf level; src 0 = the
  * group's free-space sources (its own targets; leaf level = the free-space depth), src 1 = its

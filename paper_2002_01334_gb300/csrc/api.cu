@@ -997,6 +997,25 @@ int lpbfmm_debug_lists(lpbfmm_t h, int l, int a, int lev, int kind, int src, int
   return LPBFMM_OK;
 }
 
+int lpbfmm_debug_adaptive_lists(lpbfmm_t h, int l, int a, int s, int ws, int64_t *nrec, int64_t *rec,
+                                int64_t cap) {
+  if (!h || !nrec || s < 0 || ws < 1 || ws > WS_MAX || cap < 0) return LPBFMM_ERR_ARG;
+  Group *g = find_group(h, l, a);
+  if (!g || !g->is_free || !(g->parts & 1)) return LPBFMM_ERR_ARG;
+  std::vector<int64_t> r;
+  try {
+    LPB_CUDA(cudaStreamSynchronize(h->stream));
+    adaptive_lists(*h, *g, s, ws, r);
+  } catch (const CudaError &e) {
+    return map_error(e);
+  } catch (const StatusError &e) {
+    return e.code;
+  }
+  *nrec = (int64_t)(r.size() / 5);
+  if (rec) std::memcpy(rec, r.data(), sizeof(int64_t) * 5 * (size_t)std::min<int64_t>(cap, *nrec));
+  return LPBFMM_OK;
+}
+
 int lpbfmm_debug_array(lpbfmm_t h, int l, int a, const char *name, int lev, void *dst, int64_t cap,
                        int64_t *bytes) {
   if (!h || !name || !bytes) return LPBFMM_ERR_ARG;

@@ -331,6 +331,9 @@ void count_levels(Ctx &c, Group &g, uint32_t *d_counts);
 void build_group_boxes(Ctx &c, Group &g);
 void build_group_lists(Ctx &c, Group &g, int parts);
 void layer_rank(Ctx &c, int64_t n, const int32_t *layer, int lay, uint32_t *rank);
+// adaptive dual-tree lists of group g's free-space target tree with itself (diagnostic): records
+// of 5 int64 (kind 0 V / 1 U / 2 W / 3 X, target level, target key, source level, source key)
+void adaptive_lists(Ctx &c, Group &g, int s, int ws, std::vector<int64_t> &rec);
 
 // ops.cu
 // which: 1 the free-space operators (M2M, L2L, free M2L; need only the depths and roots),

@@ -671,3 +671,157 @@ void build_group_lists(Ctx &c, Group &g, int parts) {
 }
 
 }  // namespace lpb
+
+namespace lpb {
+
+// ---------------------------------------------------------------------------------------
+// Adaptive dual-tree lists of a group's free-space target tree with itself (Sec. 3.5 builds the
+// method on the adaptive FMM framework; diagnostic for now, the evaluation uses uniform trees).
+// A box of level l >= 3 exists in the adaptive tree when its parent exists and holds more than s
+// targets (every box of level 2 exists); a box is a leaf when it holds at most s or l = D.  The
+// dual traversal starts from every pair of level-2 boxes and runs level-synchronously over
+// frontiers of box pairs: a pair that is not near (separation ws: the coarser box grown by ws - 1
+// of its sides meets the finer one) is V (same level), W (target leaf, finer source) or X (source
+// leaf, finer target); a near pair of two leaves is U; any other near pair is replaced by its
+// child pairs (both boxes refined when both have children, else the one that has).
+// ---------------------------------------------------------------------------------------
+struct APair {
+  uint32_t bt, bs;  // box indices in their levels
+  int32_t lt, ls;   // levels
+};
+struct ALevel {
+  const uint64_t *key;
+  const uint32_t *start, *count, *pcount, *parent;
+  const uint8_t *flag;  // bit 0: the box exists in the adaptive tree; bit 1: it is a leaf
+  uint32_t n;
+};
+
+__global__ void k_adapt_flags(int l, int D, int s, ALevel cur, const uint8_t *pflag, uint8_t *flag) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cur.n) return;
+  bool present = true;
+  if (l > 2) {
+    const uint8_t pf = pflag[cur.parent[b]];
+    present = (pf & 1) && !(pf & 2);
+  }
+  const bool leaf = present && (cur.pcount[b] <= (uint32_t)s || l == D);
+  flag[b] = (uint8_t)((present ? 1 : 0) | (leaf ? 2 : 0));
+}
+
+__global__ void k_adapt_init(uint32_t n2, APair *pairs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n2 * n2) return;
+  pairs[i] = APair{(uint32_t)(i / n2), (uint32_t)(i % n2), 2, 2};
+}
+
+// boxes (la, ka) and (lb, kb) near for separation ws (integer geometry at the finer level)
+__device__ bool adapt_near(int la, uint64_t ka, int lb, uint64_t kb, int ws) {
+  const int L = max(la, lb);
+  const int64_t sa = (int64_t)1 << (L - la), sb = (int64_t)1 << (L - lb);
+  const int64_t ga = la <= lb ? (ws - 1) * sa : 0, gb = lb < la ? (ws - 1) * sb : 0;
+  for (int d = 0; d < 3; ++d) {
+    const int64_t u = compact3(ka >> (2 - d)), v = compact3(kb >> (2 - d));
+    if ((u + 1) * sa + ga < v * sb - gb || (v + 1) * sb + gb < u * sa - ga) return false;
+  }
+  return true;
+}
+
+// classify every frontier pair; nchild[i] = its child pairs (0 when classified).  Records of
+// 5 int64: kind (0 V, 1 U, 2 W, 3 X), lt, key t, ls, key s; at most one per pair
+__global__ void k_adapt_step(const APair *pairs, uint32_t np, const ALevel *lv, int ws, uint32_t *nchild,
+                             int64_t *rec, uint32_t *nrec) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const APair P = pairs[i];
+  const ALevel &T = lv[P.lt], &S = lv[P.ls];
+  if (P.bt >= T.n || P.bs >= S.n) {  // cannot happen for pairs built below; checked all the same
+    nchild[i] = 0;
+    return;
+  }
+  const uint64_t kt = T.key[P.bt], ks = S.key[P.bs];
+  const bool tl = T.flag[P.bt] & 2, sl = S.flag[P.bs] & 2;
+  int kind = -1;
+  uint32_t nc = 0;
+  if (!adapt_near(P.lt, kt, P.ls, ks, ws)) kind = P.lt == P.ls ? 0 : (P.ls > P.lt ? 2 : 3);
+  else if (tl && sl) kind = 1;
+  else nc = (tl ? 1u : T.count[P.bt]) * (sl ? 1u : S.count[P.bs]);
+  nchild[i] = nc;
+  if (kind >= 0) {
+    const uint32_t r = atomicAdd(nrec, 1u);
+    if (r < np) {
+      int64_t *o = rec + (size_t)r * 5;
+      o[0] = kind; o[1] = P.lt; o[2] = (int64_t)kt; o[3] = P.ls; o[4] = (int64_t)ks;
+    }
+  }
+}
+
+__global__ void k_adapt_children(const APair *pairs, uint32_t np, const ALevel *lv, const uint32_t *nchild,
+                                 const uint32_t *off, APair *next, uint32_t cap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np || !nchild[i]) return;
+  const APair P = pairs[i];
+  const ALevel &T = lv[P.lt], &S = lv[P.ls];
+  const bool tl = T.flag[P.bt] & 2, sl = S.flag[P.bs] & 2;
+  const uint32_t nt = tl ? 1u : T.count[P.bt], ns = sl ? 1u : S.count[P.bs];
+  for (uint32_t a = 0; a < nt; ++a)
+    for (uint32_t b = 0; b < ns; ++b) {
+      const uint64_t o = (uint64_t)off[i] + (uint64_t)a * ns + b;
+      if (o >= cap) continue;
+      next[o] = APair{tl ? P.bt : T.start[P.bt] + a, sl ? P.bs : S.start[P.bs] + b, tl ? P.lt : P.lt + 1,
+                      sl ? P.ls : P.ls + 1};
+    }
+}
+
+void adaptive_lists(Ctx &c, Group &g, int s, int ws, std::vector<int64_t> &rec) {
+  rec.clear();
+  PointSet &P = g.T;
+  const int D = g.Df;
+  if (!P.np || D < 2) return;
+  // flags, top down
+  std::vector<ALevel> hl(DMAX + 1);
+  for (int l = 2; l <= D; ++l) {
+    const Level &L = P.lev[l];
+    uint8_t *f = c.arena.get<uint8_t>((size_t)std::max<int64_t>(L.n, 1));
+    hl[l] = ALevel{L.key, L.start, L.count, L.pcount, L.parent, f, (uint32_t)L.n};
+    if (L.n)
+      k_adapt_flags<<<(unsigned)((L.n + 255) / 256), 256, 0, c.stream>>>(l, D, s, hl[l], l > 2 ? hl[l - 1].flag : nullptr,
+                                                                         f);
+    LPB_LAUNCH();
+  }
+  ALevel *dl = c.arena.get<ALevel>(DMAX + 1);
+  LPB_CUDA(cudaMemcpyAsync(dl, hl.data(), sizeof(ALevel) * (DMAX + 1), cudaMemcpyHostToDevice, c.stream));
+  const uint32_t n2 = (uint32_t)P.lev[2].n;
+  uint64_t F = (uint64_t)n2 * n2;
+  constexpr uint64_t FMAX = (uint64_t)1 << 26;  // frontier pairs this diagnostic handles
+  if (F > FMAX) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+  APair *pairs = c.arena.get<APair>((size_t)std::max<uint64_t>(F, 1));
+  if (F) k_adapt_init<<<(unsigned)((F + 255) / 256), 256, 0, c.stream>>>(n2, pairs);
+  LPB_LAUNCH();
+  uint32_t *hp = (uint32_t *)c.h_pinned;
+  for (int step = 0; F > 0; ++step) {
+    if (step > 4 * DMAX) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+    uint32_t *nchild = c.arena.get<uint32_t>(F), *off = c.arena.get<uint32_t>(F), *d2 = c.arena.get<uint32_t>(2);
+    int64_t *drec = c.arena.get<int64_t>((size_t)F * 5);
+    LPB_CUDA(cudaMemsetAsync(d2, 0, 2 * sizeof(uint32_t), c.stream));
+    k_adapt_step<<<(unsigned)((F + 255) / 256), 256, 0, c.stream>>>(pairs, (uint32_t)F, dl, ws, nchild, drec, d2);
+    LPB_LAUNCH();
+    scan_u32(c, nchild, off, (int64_t)F, d2 + 1);
+    LPB_CUDA(cudaMemcpyAsync(hp, d2, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    LPB_CUDA(cudaStreamSynchronize(c.stream));
+    const uint32_t nr = std::min<uint64_t>(hp[0], F), nnext = hp[1];
+    const size_t base = rec.size();
+    rec.resize(base + (size_t)nr * 5);
+    if (nr) LPB_CUDA(cudaMemcpy(rec.data() + base, drec, sizeof(int64_t) * nr * 5, cudaMemcpyDeviceToHost));
+    if (nnext > FMAX) throw StatusError{LPBFMM_ERR_UNSUPPORTED};
+    APair *next = nnext ? c.arena.get<APair>(nnext) : nullptr;
+    if (nnext)
+      k_adapt_children<<<(unsigned)((F + 255) / 256), 256, 0, c.stream>>>(pairs, (uint32_t)F, dl, nchild, off, next,
+                                                                         nnext);
+    LPB_LAUNCH();
+    pairs = next;
+    F = nnext;
+  }
+  LPB_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+}  // namespace lpb

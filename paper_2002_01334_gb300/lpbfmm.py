@@ -51,6 +51,7 @@ def lib():
         L.lpbfmm_eval_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(i64), vp, vp, vp, vp, vp]
         L.lpbfmm_debug_tree.argtypes = [vp, C.c_int, C.c_int, dp, C.POINTER(i64), C.POINTER(i64),
                                         C.POINTER(C.c_int), vp, vp, vp, vp, vp]
+        L.lpbfmm_debug_adaptive_lists.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(i64), vp, i64]
         L.lpbfmm_debug_lists.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(i64),
                                          C.POINTER(i64), vp, vp]
         L.lpbfmm_debug_stable.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -208,6 +209,20 @@ class Context:
                                         C.c_void_p(off.ctypes.data), C.c_void_p(idx.ctypes.data)),
                "lpbfmm_debug_lists")
         return off, idx[:ne.value]
+
+    def debug_adaptive_lists(self, l, a, s, ws=1):
+        """Adaptive dual-tree lists of group (l, a)'s free-space tree (lpbfmm_debug_adaptive_lists):
+        {'V', 'U', 'W', 'X'} -> set of ((target level, key), (source level, key))."""
+        import numpy as np
+        n = C.c_int64()
+        _check(lib().lpbfmm_debug_adaptive_lists(self.h, l, a, s, ws, C.byref(n), None, 0), "debug_adaptive_lists")
+        rec = np.zeros((max(n.value, 1), 5), np.int64)
+        _check(lib().lpbfmm_debug_adaptive_lists(self.h, l, a, s, ws, C.byref(n), C.c_void_p(rec.ctypes.data),
+                                                 n.value), "debug_adaptive_lists")
+        out = {k: set() for k in "VUWX"}
+        for kind, lt, kt, ls, ks in rec[:n.value].tolist():
+            out["VUWX"[kind]].add(((lt, kt), (ls, ks)))
+        return out
 
     def debug_array(self, l, a, name, lev, dtype):
         import numpy as np

@@ -338,6 +338,27 @@ def test_tree_and_lists_bit_exact(ws):
                     assert np.array_equal(off, goff) and np.array_equal(idx, gidx), (l, a, lev, kind)
 
 
+@pytest.mark.parametrize("n,s,ws,D", [(3000, 16, 1, 5), (3000, 16, 2, 5), (3000, 40, 2, 5), (6000, 8, 2, 6)])
+def test_adaptive_lists_on_the_gpu_equal_the_oracle(n, s, ws, D):
+    """The adaptive dual-tree lists of a free-space tree, built on the device by the level-
+    synchronous traversal (lpbfmm_debug_adaptive_lists), equal the oracle's dual traversal
+    (oracle/adaptive.py, split while a box holds more than s points, at most depth D) box pair for
+    box pair: U, V, W and X, for one- and two-box separation."""
+    from oracle import adaptive as A
+    w = inputs.workload("three_layer", n=n, seed=31)
+    md = oracle.Medium(**w["medium"])
+    ctx, _, _ = run(w, 6, depth=D)
+    got = ctx.debug_adaptive_lists(1, 1, s, ws)
+    root = oracle.tree_root(md, w["xyz"], w["layer"], 1, 1)
+    k21, _, _ = oracle.tree_keys(md, w["xyz"], w["layer"], 1, 1, A.DMAX, root, 0)
+    T = A.Tree(k21, s, dmax=D)
+    assert not [b for b in T.leaves if b[0] < 2]  # the device tree starts at level 2
+    ref = A.dual_lists(T, T, ws)
+    for k in "VUWX":
+        assert got[k] == set(ref[k]), (k, len(got[k]), len(ref[k]))
+    assert ref["V"] and ref["U"] and (s >= 40 or (ref["W"] and ref["X"]))
+
+
 @pytest.mark.parametrize("cls", [(1, 2, 1, 2, 5, 0, 1), (1, 1, 0, 1, 0, 1, 1), (0, 1, 2, 2, 18, 0, 0),
                                  (2, 2, 1, 1, 2, 0, 2), (1, 1, 1, 1, 1, 0, 0)])
 def test_sommerfeld_tables_quadrature_and_recurrence(cls):
